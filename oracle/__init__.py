@@ -1,0 +1,217 @@
+"""ctypes view of the plain FP64 C oracle (``pf_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg are the only callers.  The GPU library never
+imports this package and this package never imports the GPU library.
+
+Arrays are numpy float64 (int8 for boundary masks); P is (3, nz, ny, nx),
+scalar fields are (nz, ny, nx), face masks are (ny, nx).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class _Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double),
+                ("periodic_z", C.c_int),
+                ("type_lo", C.c_void_p), ("volt_lo", C.c_void_p),
+                ("type_hi", C.c_void_p), ("volt_hi", C.c_void_p),
+                ("eps", C.c_void_p)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("a1", C.c_double), ("a11", C.c_double), ("a12", C.c_double),
+                ("g", C.c_double), ("L", C.c_double), ("dt", C.c_double),
+                ("rtol", C.c_double), ("maxit", C.c_int)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("steps_done", C.c_int), ("last_iters", C.c_int), ("total_iters", C.c_long),
+                ("last_relres", C.c_double), ("nonconverged", C.c_int)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        vp, d, i, l = C.c_void_p, C.c_double, C.c_int, C.c_long
+        L.or_landau_energy.restype = d
+        L.or_landau_energy.argtypes = [vp, l, d, d, d]
+        L.or_landau_force.argtypes = [vp, l, d, d, d, vp]
+        for f in (L.or_laplacian, L.or_rhs, L.or_apply, L.or_field):
+            f.argtypes = [vp, vp, vp]
+        L.or_diag.argtypes = [vp, vp]
+        L.or_has_dirichlet.argtypes = [vp]
+        L.or_solve.argtypes = [vp, vp, vp, d, i, vp, vp]
+        L.or_solve_potential.argtypes = [vp, vp, vp, d, i, vp, vp]
+        L.or_step.argtypes = [vp, vp, vp, vp, i, vp]
+        L.or_energy.restype = d
+        L.or_energy.argtypes = [vp, vp, vp, d]
+        _lib = L
+    return _lib
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+@dataclass
+class Grid:
+    """Grid, boundary masks and permittivity (the oracle's own description)."""
+    nx: int
+    ny: int
+    nz: int
+    dx: float = 1.0
+    periodic_z: bool = False
+    type_lo: np.ndarray | None = None
+    volt_lo: np.ndarray | None = None
+    type_hi: np.ndarray | None = None
+    volt_hi: np.ndarray | None = None
+    eps: np.ndarray | None = None
+
+    def __post_init__(self):
+        m = (self.ny, self.nx)
+        def mask(a):
+            return np.zeros(m, np.int8) if a is None else np.ascontiguousarray(a, np.int8).reshape(m)
+        def volt(a):
+            return np.zeros(m) if a is None else _f64(a).reshape(m)
+        self.type_lo, self.type_hi = mask(self.type_lo), mask(self.type_hi)
+        self.volt_lo, self.volt_hi = volt(self.volt_lo), volt(self.volt_hi)
+        if self.eps is not None:
+            self.eps = _f64(self.eps).reshape(self.shape)
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def n(self):
+        return self.nx * self.ny * self.nz
+
+    def _c(self):
+        g = _Grid(self.nx, self.ny, self.nz, float(self.dx), int(bool(self.periodic_z)),
+                  _ptr(self.type_lo), _ptr(self.volt_lo), _ptr(self.type_hi), _ptr(self.volt_hi),
+                  _ptr(self.eps))
+        return g
+
+
+@dataclass
+class Params:
+    a1: float = -1.0
+    a11: float = 0.5
+    a12: float = 0.8
+    g: float = 0.5
+    L: float = 1.0
+    dt: float = 0.01
+    rtol: float = 1e-12
+    maxit: int = 100000
+
+    def _c(self):
+        return _Params(self.a1, self.a11, self.a12, self.g, self.L, self.dt, self.rtol, int(self.maxit))
+
+
+def landau_energy(P, prm: Params) -> float:
+    P = _f64(P)
+    n = P.size // 3
+    return lib().or_landau_energy(_ptr(P), n, prm.a1, prm.a11, prm.a12)
+
+
+def landau_force(P, prm: Params):
+    P = _f64(P)
+    out = np.empty_like(P)
+    lib().or_landau_force(_ptr(P), P.size // 3, prm.a1, prm.a11, prm.a12, _ptr(out))
+    return out
+
+
+def _unary(fn, G: Grid, a, out_shape):
+    a = _f64(a)
+    out = np.empty(out_shape)
+    g = G._c()
+    fn(C.byref(g), _ptr(a), _ptr(out))
+    return out
+
+
+def laplacian(G: Grid, f):
+    return _unary(lib().or_laplacian, G, _f64(f).reshape(G.shape), G.shape)
+
+
+def rhs(G: Grid, P):
+    return _unary(lib().or_rhs, G, _f64(P).reshape((3,) + G.shape), G.shape)
+
+
+def apply(G: Grid, phi):
+    return _unary(lib().or_apply, G, _f64(phi).reshape(G.shape), G.shape)
+
+
+def field(G: Grid, phi):
+    return _unary(lib().or_field, G, _f64(phi).reshape(G.shape), (3,) + G.shape)
+
+
+def diag(G: Grid):
+    out = np.empty(G.shape)
+    g = G._c()
+    lib().or_diag(C.byref(g), _ptr(out))
+    return out
+
+
+def has_dirichlet(G: Grid) -> bool:
+    g = G._c()
+    return bool(lib().or_has_dirichlet(C.byref(g)))
+
+
+def solve(G: Grid, b, phi0=None, rtol=1e-14, maxit=100000):
+    """Jacobi-PCG solve of A phi = b.  Returns (phi, status, iters, relres)."""
+    b = _f64(b).reshape(G.shape)
+    phi = np.zeros(G.shape) if phi0 is None else _f64(phi0).reshape(G.shape).copy()
+    it, rel = C.c_int(0), C.c_double(0.0)
+    g = G._c()
+    st = lib().or_solve(C.byref(g), _ptr(b), _ptr(phi), float(rtol), int(maxit),
+                        C.byref(it), C.byref(rel))
+    return phi, st, it.value, rel.value
+
+
+def solve_potential(G: Grid, P, phi0=None, rtol=1e-14, maxit=100000):
+    P = _f64(P).reshape((3,) + G.shape)
+    phi = np.zeros(G.shape) if phi0 is None else _f64(phi0).reshape(G.shape).copy()
+    it, rel = C.c_int(0), C.c_double(0.0)
+    g = G._c()
+    st = lib().or_solve_potential(C.byref(g), _ptr(P), _ptr(phi), float(rtol), int(maxit),
+                                  C.byref(it), C.byref(rel))
+    return phi, st, it.value, rel.value
+
+
+def step(G: Grid, prm: Params, P, phi=None, nsteps=1):
+    """nsteps forward-Euler steps.  Returns (P, phi, status, info dict)."""
+    P = _f64(P).reshape((3,) + G.shape).copy()
+    phi = np.zeros(G.shape) if phi is None else _f64(phi).reshape(G.shape).copy()
+    info = _Info()
+    g, p = G._c(), prm._c()
+    st = lib().or_step(C.byref(g), C.byref(p), _ptr(P), _ptr(phi), int(nsteps), C.byref(info))
+    d = dict(steps_done=info.steps_done, last_iters=info.last_iters,
+             total_iters=info.total_iters, last_relres=info.last_relres,
+             nonconverged=info.nonconverged)
+    return P, phi, st, d
+
+
+def energy(G: Grid, prm: Params, P, rtol=1e-14) -> float:
+    P = _f64(P).reshape((3,) + G.shape)
+    g, p = G._c(), prm._c()
+    return lib().or_energy(C.byref(g), C.byref(p), _ptr(P), float(rtol))
+
+
+OK, NOCONV = 0, 3

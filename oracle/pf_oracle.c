@@ -1,0 +1,390 @@
+/*
+ * Plain FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY (see pf_oracle.h).
+ *
+ * Serial loops, no blocking, no fusion: every operator is written cell by
+ * cell, face by face, the way the equations read.  Citations are to the
+ * paper's sections and equations:
+ *   Eq. F_bulk            Landau bulk energy (Section Theory)
+ *   Eqs. F_grad, dF_grad  domain-wall gradient energy and its force
+ *   Eqs. F_elec           E = -dF_elec/dP
+ *   Eq. TDGL              dP/dt = -dF/dP (+ noise, not used here)
+ *   Eqs. rho, Poisson     rho = div P,  eps Lap phi = rho  (Section
+ *                         Electrostatics Calculation), boundary kinds listed
+ *                         in the same section
+ *   Section Time Integration: explicit forward Euler
+ *   Section Numerical Performance: the Krylov solve is warm-started from the
+ *                         previous step's potential
+ */
+#include "pf_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+static long ncells(const or_grid* G) { return (long)G->nx * G->ny * G->nz; }
+
+static long cell_index(const or_grid* G, int x, int y, int z) {
+  return ((long)z * G->ny + y) * G->nx + x;
+}
+
+/* Periodic wrap of an index that is at most one step outside [0, n). */
+static int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+static double eps_of(const or_grid* G, long c) { return G->eps ? G->eps[c] : 1.0; }
+
+/* Face of cell (x,y,z) in direction d (0=x,1=y,2=z) on side s (-1 or +1).
+ * Returns 1 for an interior face (neighbour index in *nb) and 0 for a z
+ * boundary face (its mask type in *btype, voltage in *bvolt). */
+static int face_of(const or_grid* G, int x, int y, int z, int d, int s,
+                   long* nb, int* btype, double* bvolt) {
+  int q[3] = {x, y, z};
+  int n[3] = {G->nx, G->ny, G->nz};
+  int t = q[d] + s;
+  if (d < 2 || G->periodic_z) {
+    q[d] = wrap(t, n[d]);
+    *nb = cell_index(G, q[0], q[1], q[2]);
+    return 1;
+  }
+  if (t >= 0 && t < n[2]) {
+    q[2] = t;
+    *nb = cell_index(G, q[0], q[1], q[2]);
+    return 1;
+  }
+  long m = (long)y * G->nx + x;
+  if (s < 0) {
+    *btype = G->type_lo[m];
+    *bvolt = G->volt_lo[m];
+  } else {
+    *btype = G->type_hi[m];
+    *bvolt = G->volt_hi[m];
+  }
+  return 0;
+}
+
+/* Eq. F_bulk: f = a1 sum P_i^2 + a11 sum P_i^4 + a12 (Px^2 Py^2 + Py^2 Pz^2 + Pz^2 Px^2). */
+double or_landau_energy(const double* P, long n, double a1, double a11, double a12) {
+  double F = 0.0;
+  for (long c = 0; c < n; ++c) {
+    double x2 = P[c] * P[c], y2 = P[n + c] * P[n + c], z2 = P[2 * n + c] * P[2 * n + c];
+    F += a1 * (x2 + y2 + z2) + a11 * (x2 * x2 + y2 * y2 + z2 * z2) +
+         a12 * (x2 * y2 + y2 * z2 + z2 * x2);
+  }
+  return F;
+}
+
+/* df/dP_i = 2 a1 P_i + 4 a11 P_i^3 + 2 a12 P_i (P_j^2 + P_k^2), from Eq. F_bulk. */
+void or_landau_force(const double* P, long n, double a1, double a11, double a12, double* out) {
+  for (long c = 0; c < n; ++c) {
+    double p[3] = {P[c], P[n + c], P[2 * n + c]};
+    for (int i = 0; i < 3; ++i) {
+      int j = (i + 1) % 3, k = (i + 2) % 3;
+      out[i * n + c] = 2.0 * a1 * p[i] + 4.0 * a11 * p[i] * p[i] * p[i] +
+                       2.0 * a12 * p[i] * (p[j] * p[j] + p[k] * p[k]);
+    }
+  }
+}
+
+/* Eq. dF_grad/dP: Lap f as the sum over the cell's interior faces of
+ * (f_nb - f_c)/dx^2.  A non-periodic z face is dropped (zero normal flux). */
+void or_laplacian(const or_grid* G, const double* f, double* out) {
+  double h2 = 1.0 / (G->dx * G->dx);
+  for (int z = 0; z < G->nz; ++z)
+    for (int y = 0; y < G->ny; ++y)
+      for (int x = 0; x < G->nx; ++x) {
+        long c = cell_index(G, x, y, z);
+        double acc = 0.0;
+        for (int d = 0; d < 3; ++d)
+          for (int s = -1; s <= 1; s += 2) {
+            long nb;
+            int bt;
+            double bv;
+            if (face_of(G, x, y, z, d, s, &nb, &bt, &bv)) acc += f[nb] - f[c];
+          }
+        out[c] = acc * h2;
+      }
+}
+
+/* Face permittivity between cells c and nb: the harmonic mean of the two
+ * cell values (reading R4); 1 when no permittivity field is given. */
+static double eps_face(const or_grid* G, long c, long nb) {
+  if (!G->eps) return 1.0;
+  double a = G->eps[c], b = G->eps[nb];
+  return 2.0 * a * b / (a + b);
+}
+
+/* Eqs. rho, Poisson: div(eps grad phi) = div P.  In SPD form A phi = b with
+ * b = -div P + (Dirichlet terms).  div P is the sum of outward normal face
+ * values of P divided by dx; face values per reading R3. */
+void or_rhs(const or_grid* G, const double* P, double* b) {
+  long n = ncells(G);
+  double ih = 1.0 / G->dx, ih2 = ih * ih;
+  for (int z = 0; z < G->nz; ++z)
+    for (int y = 0; y < G->ny; ++y)
+      for (int x = 0; x < G->nx; ++x) {
+        long c = cell_index(G, x, y, z);
+        double div = 0.0, dir = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          const double* Pd = P + (long)d * n;
+          for (int s = -1; s <= 1; s += 2) {
+            long nb;
+            int bt;
+            double bv, Pf;
+            if (face_of(G, x, y, z, d, s, &nb, &bt, &bv)) {
+              Pf = 0.5 * (Pd[c] + Pd[nb]);
+            } else if (bt == 1) {
+              Pf = Pd[c];                              /* electrode: surface charge screened */
+              dir += 2.0 * eps_of(G, c) * bv;          /* ghost 2V - phi_c moved to the rhs */
+            } else {
+              Pf = 0.0;                                /* open surface */
+            }
+            div += s * Pf;
+          }
+        }
+        b[c] = -div * ih + dir * ih2;
+      }
+}
+
+/* A phi = sum over faces of eps_f (phi_c - phi_nb)/dx^2, with the Dirichlet
+ * ghost 2V - phi_c taken at V = 0 (flux 2 eps_c phi_c) and Neumann faces
+ * contributing nothing (Section Electrostatics Calculation, R4). */
+void or_apply(const or_grid* G, const double* phi, double* out) {
+  double ih2 = 1.0 / (G->dx * G->dx);
+  for (int z = 0; z < G->nz; ++z)
+    for (int y = 0; y < G->ny; ++y)
+      for (int x = 0; x < G->nx; ++x) {
+        long c = cell_index(G, x, y, z);
+        double acc = 0.0;
+        for (int d = 0; d < 3; ++d)
+          for (int s = -1; s <= 1; s += 2) {
+            long nb;
+            int bt;
+            double bv;
+            if (face_of(G, x, y, z, d, s, &nb, &bt, &bv))
+              acc += eps_face(G, c, nb) * (phi[c] - phi[nb]);
+            else if (bt == 1)
+              acc += 2.0 * eps_of(G, c) * phi[c];
+          }
+        out[c] = acc * ih2;
+      }
+}
+
+void or_diag(const or_grid* G, double* dg) {
+  double ih2 = 1.0 / (G->dx * G->dx);
+  for (int z = 0; z < G->nz; ++z)
+    for (int y = 0; y < G->ny; ++y)
+      for (int x = 0; x < G->nx; ++x) {
+        long c = cell_index(G, x, y, z);
+        double acc = 0.0;
+        for (int d = 0; d < 3; ++d)
+          for (int s = -1; s <= 1; s += 2) {
+            long nb;
+            int bt;
+            double bv;
+            if (face_of(G, x, y, z, d, s, &nb, &bt, &bv))
+              acc += eps_face(G, c, nb);
+            else if (bt == 1)
+              acc += 2.0 * eps_of(G, c);
+          }
+        dg[c] = acc * ih2;
+      }
+}
+
+/* Eqs. F_elec: E = -grad phi, per component the difference of the two face
+ * values of phi divided by dx; face values per reading R3. */
+void or_field(const or_grid* G, const double* phi, double* E) {
+  long n = ncells(G);
+  double ih = 1.0 / G->dx;
+  for (int z = 0; z < G->nz; ++z)
+    for (int y = 0; y < G->ny; ++y)
+      for (int x = 0; x < G->nx; ++x) {
+        long c = cell_index(G, x, y, z);
+        for (int d = 0; d < 3; ++d) {
+          double f[2];
+          for (int s = -1; s <= 1; s += 2) {
+            long nb;
+            int bt;
+            double bv;
+            if (face_of(G, x, y, z, d, s, &nb, &bt, &bv))
+              f[(s + 1) / 2] = 0.5 * (phi[c] + phi[nb]);
+            else
+              f[(s + 1) / 2] = (bt == 1) ? bv : phi[c];
+          }
+          E[(long)d * n + c] = -(f[1] - f[0]) * ih;
+        }
+      }
+}
+
+int or_has_dirichlet(const or_grid* G) {
+  if (G->periodic_z) return 0;
+  long m = (long)G->nx * G->ny;
+  for (long i = 0; i < m; ++i)
+    if (G->type_lo[i] == 1 || G->type_hi[i] == 1) return 1;
+  return 0;
+}
+
+static double dot(const double* a, const double* b, long n) {
+  double s = 0.0;
+  for (long i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+static double mean(const double* a, long n) {
+  double s = 0.0;
+  for (long i = 0; i < n; ++i) s += a[i];
+  return s / (double)n;
+}
+
+/* Reading R6: Jacobi-preconditioned conjugate gradients (the paper uses a
+ * PETSc Krylov solver, Section Numerical Performance, warm-started from the
+ * previous potential).  Textbook Hestenes-Stiefel PCG; stop when the
+ * recursive residual satisfies ||r||/||b|| < rtol. */
+int or_solve(const or_grid* G, const double* b_in, double* phi, double rtol, int maxit,
+             int* iters, double* relres) {
+  long n = ncells(G);
+  int singular = !or_has_dirichlet(G);
+  double* b = (double*)malloc(sizeof(double) * n);
+  double* r = (double*)malloc(sizeof(double) * n);
+  double* z = (double*)malloc(sizeof(double) * n);
+  double* p = (double*)malloc(sizeof(double) * n);
+  double* q = (double*)malloc(sizeof(double) * n);
+  double* dg = (double*)malloc(sizeof(double) * n);
+  memcpy(b, b_in, sizeof(double) * n);
+  if (singular) {
+    double m = mean(b, n);
+    for (long i = 0; i < n; ++i) b[i] -= m;
+  }
+  or_diag(G, dg);
+  int status = OR_OK, k = 0;
+  double bnorm = sqrt(dot(b, b, n)), rel = 0.0;
+  if (bnorm == 0.0) {
+    memset(phi, 0, sizeof(double) * n);
+    goto done;
+  }
+  or_apply(G, phi, q);
+  for (long i = 0; i < n; ++i) r[i] = b[i] - q[i];
+  rel = sqrt(dot(r, r, n)) / bnorm;
+  if (rel < rtol) goto finish;
+  for (long i = 0; i < n; ++i) z[i] = r[i] / dg[i];
+  for (long i = 0; i < n; ++i) p[i] = z[i];
+  double rz = dot(r, z, n);
+  status = OR_NOCONV;
+  for (k = 1; k <= maxit; ++k) {
+    or_apply(G, p, q);
+    double pq = dot(p, q, n);
+    if (!(pq > 0.0)) break;                 /* breakdown: keep the current iterate */
+    double alpha = rz / pq;
+    for (long i = 0; i < n; ++i) phi[i] += alpha * p[i];
+    for (long i = 0; i < n; ++i) r[i] -= alpha * q[i];
+    rel = sqrt(dot(r, r, n)) / bnorm;
+    if (rel < rtol) {
+      status = OR_OK;
+      break;
+    }
+    for (long i = 0; i < n; ++i) z[i] = r[i] / dg[i];
+    double rz_new = dot(r, z, n);
+    double beta = rz_new / rz;
+    rz = rz_new;
+    for (long i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+  }
+  if (k > maxit) k = maxit;
+finish:
+  if (singular) {
+    double m = mean(phi, n);
+    for (long i = 0; i < n; ++i) phi[i] -= m;
+  }
+done:
+  if (iters) *iters = k;
+  if (relres) *relres = rel;
+  free(b); free(r); free(z); free(p); free(q); free(dg);
+  return status;
+}
+
+int or_solve_potential(const or_grid* G, const double* P, double* phi, double rtol, int maxit,
+                       int* iters, double* relres) {
+  long n = ncells(G);
+  double* b = (double*)malloc(sizeof(double) * n);
+  or_rhs(G, P, b);
+  int st = or_solve(G, b, phi, rtol, maxit, iters, relres);
+  free(b);
+  return st;
+}
+
+/* Eq. TDGL with the deterministic driving force
+ *   -dF/dP_i = -(df/dP_i) + g Lap P_i + E_i      (Eqs. F_bulk, dF_grad, F_elec)
+ * advanced by forward Euler (Section Time Integration):
+ *   P_{n+1} = P_n + dt L (-df/dP + g Lap P + E),   E from the potential of P_n. */
+int or_step(const or_grid* G, const or_params* prm, double* P, double* phi, int nsteps,
+            or_info* info) {
+  long n = ncells(G);
+  double* b = (double*)malloc(sizeof(double) * n);
+  double* h = (double*)malloc(sizeof(double) * 3 * n);
+  double* lap = (double*)malloc(sizeof(double) * 3 * n);
+  double* E = (double*)malloc(sizeof(double) * 3 * n);
+  or_info inf;
+  memset(&inf, 0, sizeof(inf));
+  int status = OR_OK;
+  for (int s = 0; s < nsteps; ++s) {
+    int it = 0;
+    double rel = 0.0;
+    or_rhs(G, P, b);
+    int st = or_solve(G, b, phi, prm->rtol, prm->maxit, &it, &rel);
+    if (st != OR_OK) {
+      status = st;
+      inf.nonconverged++;
+    }
+    inf.last_iters = it;
+    inf.total_iters += it;
+    inf.last_relres = rel;
+    or_field(G, phi, E);
+    or_landau_force(P, n, prm->a1, prm->a11, prm->a12, h);
+    for (int c = 0; c < 3; ++c) or_laplacian(G, P + (long)c * n, lap + (long)c * n);
+    for (long i = 0; i < 3 * n; ++i)
+      P[i] = P[i] + prm->dt * prm->L * (-h[i] + prm->g * lap[i] + E[i]);
+    inf.steps_done = s + 1;
+  }
+  if (info) *info = inf;
+  free(b); free(h); free(lap); free(E);
+  return status;
+}
+
+/* Discrete free energy whose gradient is the force used in or_step:
+ *   F = sum_c f(P_c) + (g/2) sum_{interior faces} |P_c - P_nb|^2 / dx^2
+ *       - 1/2 sum_c P_c . (E_c + E_ext,c)
+ * E is the field of P (with electrodes); E_ext the field of the electrodes
+ * alone (P = 0).  -dF/dP_c then equals the driving force of Eq. TDGL. */
+double or_energy(const or_grid* G, const or_params* prm, const double* P, double rtol) {
+  long n = ncells(G);
+  double F = or_landau_energy(P, n, prm->a1, prm->a11, prm->a12);
+  double ih2 = 1.0 / (G->dx * G->dx), fg = 0.0;
+  for (int z = 0; z < G->nz; ++z)
+    for (int y = 0; y < G->ny; ++y)
+      for (int x = 0; x < G->nx; ++x) {
+        long c = cell_index(G, x, y, z);
+        for (int d = 0; d < 3; ++d) {
+          long nb;
+          int bt;
+          double bv;
+          if (!face_of(G, x, y, z, d, +1, &nb, &bt, &bv)) continue;
+          for (int i = 0; i < 3; ++i) {
+            double dp = P[(long)i * n + nb] - P[(long)i * n + c];
+            fg += dp * dp;
+          }
+        }
+      }
+  F += 0.5 * prm->g * fg * ih2;
+
+  double* phi = (double*)calloc(n, sizeof(double));
+  double* E = (double*)malloc(sizeof(double) * 3 * n);
+  double* zero = (double*)calloc(3 * n, sizeof(double));
+  or_solve_potential(G, P, phi, rtol, 100000, NULL, NULL);
+  or_field(G, phi, E);
+  double fe = 0.0;
+  for (long i = 0; i < 3 * n; ++i) fe += P[i] * E[i];
+  memset(phi, 0, sizeof(double) * n);
+  or_solve_potential(G, zero, phi, rtol, 100000, NULL, NULL);
+  or_field(G, phi, E);
+  for (long i = 0; i < 3 * n; ++i) fe += P[i] * E[i];
+  F -= 0.5 * fe;
+  free(phi); free(E); free(zero);
+  return F;
+}
