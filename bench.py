@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Throughput of the TDGL + Poisson step in cell-steps/s on GB300.
+
+One "step" is one forward-Euler time step of a whole film: the warm-started
+Poisson solve (to the workload's tolerance) followed by the TDGL update, all
+in the CUDA library behind include/pf.h.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank advances its own film
+(independent replicas, no collective on the data path); value = all ranks'
+cell-steps / max over ranks of the timed device time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TDGL cell-steps/s incl. Poisson solve"
+UNIT = "cell-steps/s"
+L2_BYTES = 129 * 2 ** 20
+WORKLOADS = ("strips", "tip", "grounded")
+
+
+def make_workload(name, seed_offset=0):
+    from paper_1202_6116_gb300 import workloads as W
+    if name == "strips":
+        return W.film_strip_fp32(seed=1 + seed_offset)
+    if name == "tip":
+        return W.film_tip_fp32(seed=2 + seed_offset)
+    if name == "grounded":
+        return W.film_fp64_grounded(seed=0 + seed_offset)
+    raise ValueError(name)
+
+
+def sample_workload(name):
+    """Bounded CPU sample of a workload: same recipe, each dimension / 4."""
+    from paper_1202_6116_gb300 import workloads as W
+    if name == "strips":
+        return W.film_strip_fp32(64, 64, 16, seed=1), "64x64x16 film of the strip-electrode recipe"
+    if name == "tip":
+        return W.film_tip_fp32(256, 256, 32, seed=2), "256x256x32 film of the tip-electrode recipe"
+    return W.film_fp64_grounded(32, 32, 32, seed=0), "the full 32x32x32 grounded film"
+
+
+def workload_config(w, name, flush):
+    return {"workload": "%s %dx%dx%d %s %s rtol=%g dt=%g" % (name, w.nx, w.ny, w.nz, w.precision,
+                                                             "MG-PCG" if w.solver == "mg" else "Jacobi-PCG",
+                                                             w.rtol, w.dt),
+            "cells": w.n, "precision": w.precision, "solver": w.solver, "poisson_rtol": w.rtol,
+            "dt": w.dt, "l2": flush}
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ roofline
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1202_6116_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload, cells):
+    """DRAM bytes per launch of a kernel family from the committed ncu summary,
+    scaled to this workload's cell count; None if absent or taken on other code."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    e = d.get("kernels", {}).get(kernel)
+    if not e or e.get("workload") != workload:
+        return None
+    return e["dram_bytes_per_cell"] * cells
+
+
+# ------------------------------------------------------------------ our impl
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1202_6116_gb300 import build as B
+    from paper_1202_6116_gb300 import pf
+    from paper_1202_6116_gb300.film import Film
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = make_workload(args.workload, seed_offset=rank)
+    film = Film(w, device=dev)
+    stream = film.stream
+    flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = "flushed (a %d MiB buffer is written between timed steps)" % (2 * L2_BYTES // 2 ** 20)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        film.step(1)
+    pf.pf_profile_enable(film.ctx, 1)
+    clocks = ClockSampler(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches = 0
+    iters = 0
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        flush_buf.zero_()
+        starts[k].record(stream)
+        st, info = film.step(1)
+        ends[k].record(stream)
+        launches += info["kernel_launches"]
+        iters += info["total_iters"]
+    barrier()
+    clk = clocks.stop()
+    stats = pf.pf_profile_read(film.ctx)
+    pf.pf_profile_enable(film.ctx, 0)
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    ms_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = w.n * args.steps * world / (ms_max / 1e3)
+
+    # end to end: host-resident state, copies inside the timed region
+    w_bytes = 4 if w.precision == "fp32" else 8
+    tdt = torch.float32 if w.precision == "fp32" else torch.float64
+    Ph = film.P.detach().to("cpu").pin_memory()
+    phih = film.phi.detach().to("cpu").pin_memory()
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    barrier()
+    t0 = time.perf_counter()
+    pf.pf_step_host(film.ctx, Ph, phih, e2e_steps)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": w.n * e2e_steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 4 * w.n * w_bytes, "d2h_bytes_per_step": 4 * w.n * w_bytes,
+           "steps": e2e_steps}
+
+    # roofline of the dominant kernel family (live CUDA-event times)
+    work = [s for s in stats if s["launches"] > 0]
+    dom = max(work, key=lambda s: s["total_ms"])
+    total_kernel_ms = sum(s["total_ms"] for s in work)
+    peak, peak_kind = measured_peak_hbm()
+    achieved = dom["bytes"] / (dom["total_ms"] / 1e3) / 1e9
+    traffic = ncu_traffic(dom["name"], args.workload, w.n)
+    roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic,
+                "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
+                "avg_launch_us": 1e3 * dom["total_ms"] / dom["launches"],
+                "share_of_kernel_time": round(dom["total_ms"] / total_kernel_ms, 3),
+                "step_achieved_gbs": round(sum(s["bytes"] for s in work) / (total_kernel_ms / 1e3) / 1e9, 1),
+                "kernels": {s["name"]: {"launches": s["launches"], "idle": s["idle_launches"],
+                                        "ms": round(s["total_ms"], 3),
+                                        "gbs": round(s["bytes"] / (s["total_ms"] / 1e3) / 1e9, 1)}
+                            for s in work}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, args.cpu_seconds)
+    film.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w.precision == "fp32" else "f64",
+                "data": "synthetic (seeded SplitMix64 initial state, electrode masks of the workload)",
+                "config": workload_config(w, args.workload, flush),
+                "poisson_iters_per_step": iters / args.steps,
+                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+                "clocks": clk, "impl": "ours"}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+def oracle_timed(w, warm, steps):
+    import oracle as O
+    G = O.Grid(w.nx, w.ny, w.nz, w.dx, w.periodic_z, w.type_lo, w.volt_lo, w.type_hi, w.volt_hi, w.eps)
+    prm = O.Params(w.a1, w.a11, w.a12, w.g, w.L, w.dt, w.rtol, w.maxit)
+    P, phi, _, _ = O.step(G, prm, w.P0, None, warm)
+    t0 = time.perf_counter()
+    P, phi, st, info = O.step(G, prm, P, phi, steps)
+    return time.perf_counter() - t0, info
+
+
+def cpu_baseline(name, budget_s):
+    """The FP64 oracle as it stands, serial, on a bounded sample of the workload."""
+    import oracle.build
+    oracle.build.build()
+    w, desc = sample_workload(name)
+    dt1, _ = oracle_timed(w, 2, 1)
+    steps = max(1, min(50, int(budget_s / max(dt1, 1e-3))))
+    secs, info = oracle_timed(w, 2, steps)
+    return {"value": w.n * steps / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%s, FP64, %d timed steps after 3 warm-up steps (%.1f s, %d CG iterations)" %
+                      (desc, steps, secs, info["total_iters"])}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    import oracle.build
+    oracle.build.build()
+    w, desc = sample_workload(args.workload)
+    secs, info = oracle_timed(w, args.warmup, args.steps)
+    value = w.n * args.steps / secs
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SplitMix64 initial state, electrode masks of the workload)",
+            "config": workload_config(make_workload(args.workload), args.workload, "n/a (CPU)"),
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%s, FP64 serial oracle, %d steps after %d warm-up steps" %
+                                       (desc, args.steps, args.warmup)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
+    ap.add_argument("--workload", choices=WORKLOADS, default="strips")
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        args.steps = 5 if args.steps is None else args.steps
+        args.warmup = 3 if args.warmup is None else args.warmup
+        run_reference(args)
+    else:
+        args.steps = 200 if args.steps is None else args.steps
+        args.warmup = 10 if args.warmup is None else max(3, args.warmup)
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

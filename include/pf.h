@@ -1,0 +1,180 @@
+/*
+ * pf.h -- C ABI of the GB300 time-domain ferroelectric phase-field step.
+ *
+ * The library advances the polarization field P of a ferroelectric film by
+ * the time-dependent Ginzburg-Landau equation (Eq. TDGL of Ashraf &
+ * Salahuddin, "A Massively Parallel Time Domain Phase Field Model for
+ * Multi-domain Ferroelectric Device Simulation"), with the driving force made
+ * of
+ *   - the Landau bulk term (Eq. F_bulk),
+ *   - the domain-wall gradient term G11 Lap P (Eqs. F_grad, dF_grad/dP),
+ *   - the electric field E = -grad phi (Eqs. F_elec),
+ * where phi solves the electrostatic Poisson problem div(eps grad phi) =
+ * div P (Eqs. rho, Poisson) with periodic x/y and per-cell Dirichlet
+ * (electrode) or Neumann (open surface) z faces (Section Electrostatics
+ * Calculation).  Time stepping is explicit forward Euler (Section Time
+ * Integration); each Poisson solve is warm-started from the previous
+ * potential (Section Numerical Performance).  The paper's finite-element
+ * elastic solve is not part of this library: a fixed homogeneous misfit
+ * strain is assumed folded into a1, a11, a12.
+ *
+ * Discretisation: cell-centred unknowns on an nx*ny*nz grid of spacing dx,
+ * linear index (z*ny + y)*nx + x (x fastest, the paper's natural ordering).
+ * Interior face values are the mean of the two cells; at a Dirichlet face
+ * phi_f = V and P_f = P_cell; at a Neumann face phi_f = phi_cell and P_f = 0;
+ * P has zero normal flux at non-periodic z faces for the gradient term;
+ * interior face permittivity is the harmonic mean of the two cells.
+ *
+ * Memory: every device buffer is owned by the caller (for example torch
+ * tensors).  The library allocates no device memory and keeps only a small
+ * pinned host mirror of its solver scalars.  All calls are issued on the CUDA
+ * stream given to pf_create.  Calls return a pf_status and never abort; the
+ * message of the last failure is available from pf_last_error.
+ */
+#ifndef PF_H
+#define PF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pf_ctx pf_ctx;
+
+typedef enum {
+  PF_OK = 0,
+  PF_ERR_ARG = 1,        /* invalid argument (sizes, pointers, enum values) */
+  PF_ERR_CUDA = 2,       /* a CUDA runtime call failed; see pf_last_error */
+  PF_ERR_NOCONV = 3,     /* a Poisson solve hit poisson_maxit (state stays valid) */
+  PF_ERR_NONFINITE = 4,  /* NaN or Inf detected in the solver scalars */
+  PF_ERR_TIMEOUT = 5,    /* reserved: a bounded device wait gave up */
+  PF_ERR_STATE = 6,      /* call out of order (e.g. pf_step before pf_bind) */
+  PF_ERR_NOTIMPL = 7     /* entry point declared but not available */
+} pf_status;
+
+enum { PF_FP64 = 0, PF_FP32 = 1 };              /* storage and arithmetic type of fields */
+enum { PF_PCG_JACOBI = 0, PF_PCG_MG = 1 };      /* Poisson preconditioner */
+enum { PF_ZLO = 0, PF_ZHI = 1 };                /* z faces: z = -1/2 and z = nz - 1/2 */
+enum { PF_NEUMANN = 0, PF_DIRICHLET = 1 };      /* per-(x,y) face type */
+
+typedef struct {
+  int32_t nx, ny, nz;        /* grid cells (Section Grid); each >= 1 */
+  double dx;                 /* grid spacing (reduced units) */
+  double a1, a11, a12;       /* Landau coefficients, Eq. F_bulk */
+  double g;                  /* gradient coefficient G11, Eq. dF_grad/dP */
+  double L;                  /* mobility multiplying -dF/dP in Eq. TDGL */
+  double dt;                 /* forward-Euler time step */
+  int32_t precision;         /* PF_FP64 or PF_FP32 (FP32 fields, FP64-accurate dots) */
+  int32_t solver;            /* PF_PCG_JACOBI or PF_PCG_MG */
+  double poisson_rtol;       /* stop when ||b - A phi||_2 / ||b||_2 < rtol (recursive residual) */
+  int32_t poisson_maxit;     /* iteration cap per solve (>= 1) */
+  int32_t periodic_z;        /* 1: z periodic too (masks ignored; zero-mean potential) */
+  int32_t has_eps;           /* 1: a cell permittivity field is bound; 0: eps = 1 */
+  int32_t reserved[7];       /* must be zero */
+} pf_params;
+
+typedef struct {
+  int32_t steps_done;        /* steps completed by this call */
+  int32_t last_iters;        /* Poisson iterations of the last solve */
+  int64_t total_iters;       /* Poisson iterations summed over this call */
+  double last_relres;        /* recursive ||r||/||b|| at the end of the last solve */
+  int32_t nonconverged;      /* solves of this call that hit poisson_maxit */
+  int32_t status;            /* pf_status of this call */
+  int64_t kernel_launches;   /* kernels this call launched (including ones that
+                                returned at entry because the solve had finished) */
+} pf_step_info;
+
+/* Per-kernel device-time statistics collected while profiling is on (see
+ * pf_profile_enable).  Times come from CUDA events recorded on the context's
+ * stream between consecutive launches; bytes are the algorithmic bytes each
+ * kernel must move (reads + writes of whole fields, halos and masks not
+ * counted), summed over the launches that did work. */
+typedef struct {
+  char name[32];             /* kernel family, e.g. "cg_p", "tdgl" */
+  int64_t launches;          /* launches that did work */
+  int64_t idle_launches;     /* launches that returned at entry */
+  double total_ms;           /* device time of the working launches */
+  double bytes;              /* algorithmic bytes of the working launches */
+} pf_kernel_stat;
+
+/* Bytes of device workspace needed for these parameters (0 on invalid
+ * parameters).  The workspace holds the second polarization buffer, the
+ * Krylov vectors, the multigrid hierarchy, the boundary masks and the
+ * reduction scratch. */
+size_t pf_workspace_bytes(const pf_params* params);
+
+/* Validate params and create a context bound to a CUDA stream (a
+ * cudaStream_t, or NULL for the legacy default stream).  Host only: no
+ * kernel is launched and no device memory is allocated.  The context must be
+ * used from one host thread at a time. */
+pf_status pf_create(const pf_params* params, void* cuda_stream, pf_ctx** out);
+
+/* Attach caller-owned device buffers (borrowed, never freed by the library):
+ *   P         3*N elements, component-major (Px block, Py block, Pz block),
+ *             each block in the linear cell order; double for PF_FP64,
+ *             float for PF_FP32.  Read and updated in place by pf_step.
+ *   phi       N elements of the same type: the potential.  Its contents are
+ *             the initial guess of the first solve (zero is a valid start).
+ *   eps       N elements of the same type (cell permittivity, > 0) when
+ *             params.has_eps = 1, else ignored and may be NULL.
+ *   workspace at least pf_workspace_bytes(params) bytes, 256-byte aligned.
+ * All pointers must be device pointers of the current device, with P, phi
+ * and eps 16-byte aligned.  Resets both z faces to Neumann at 0 V. */
+pf_status pf_bind(pf_ctx* ctx, void* P, void* phi, const void* eps, void* workspace,
+                  size_t workspace_bytes);
+
+/* Set the electrical boundary of one z face (Section Electrostatics
+ * Calculation): type_xy[y*nx + x] is PF_DIRICHLET (electrode held at
+ * volts_xy[y*nx + x]) or PF_NEUMANN (open surface, zero normal field).
+ * Host arrays of nx*ny entries, copied before the call returns.  volts_xy
+ * may be NULL (0 V).  Ignored when periodic_z = 1. */
+pf_status pf_set_bc(pf_ctx* ctx, int32_t face, const int8_t* type_xy, const double* volts_xy);
+
+/* Advance nsteps forward-Euler steps.  Step n solves A phi = b(P_n) with the
+ * current phi as initial guess, then updates
+ *   P <- P - dt L (df/dP - g Lap P - E),  E = -grad phi.
+ * On return P = P_nsteps and phi is the potential of P_{nsteps-1}.  Blocks
+ * the host until the work is done.  A solve that hits poisson_maxit does not
+ * stop the run: the step completes with the unconverged potential and the
+ * call returns PF_ERR_NOCONV with info->nonconverged counting such solves.
+ * info may be NULL. */
+pf_status pf_step(pf_ctx* ctx, int32_t nsteps, pf_step_info* info);
+
+/* Same as pf_step but P and phi live in host memory: both are copied to the
+ * bound device buffers before every step and copied back after it (pinned
+ * host memory makes the copies asynchronous).  This is the end-to-end entry
+ * for callers that keep the state on the host. */
+pf_status pf_step_host(pf_ctx* ctx, void* P_host, void* phi_host, int32_t nsteps,
+                       pf_step_info* info);
+
+/* Solve the Poisson problem for the current P only (no P update). */
+pf_status pf_solve_potential(pf_ctx* ctx, pf_step_info* info);
+
+/* Reverse-mode step of the discrete TDGL + Poisson map; not available in
+ * this version (returns PF_ERR_NOTIMPL). */
+pf_status pf_adjoint_step(pf_ctx* ctx, const void* lam_in, void* lam_out, double* grad_params,
+                          double* grad_volts);
+
+/* Turn per-kernel timing on (1) or off (0); turning it on clears the
+ * counters.  While on, every launch is bracketed by CUDA events on the
+ * context's stream (no extra synchronisation: the events are read at the
+ * points where the host already waits). */
+pf_status pf_profile_enable(pf_ctx* ctx, int32_t enable);
+
+/* Copy up to max kernel statistics into out; returns how many families
+ * exist (may exceed max), or -1 on a NULL context. */
+int32_t pf_profile_read(const pf_ctx* ctx, pf_kernel_stat* out, int32_t max);
+
+/* Release the context (not the bound buffers).  Safe on NULL. */
+pf_status pf_destroy(pf_ctx* ctx);
+
+/* Message of the last failing call on this context ("" if none); with
+ * ctx = NULL, the message of the last failing pf_create in this process. */
+const char* pf_last_error(const pf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF_H */

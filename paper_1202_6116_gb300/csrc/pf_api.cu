@@ -1,0 +1,586 @@
+// C ABI of the TDGL + Poisson library (declared in include/pf.h).
+//
+// Host-side driver: argument checks, workspace layout, boundary masks, and
+// the time loop.  Per step: r0 = b(P_n) - A phi (warm start, Section
+// Numerical Performance), Jacobi-PCG iterations until the on-device
+// convergence flag is set, the deferred last x update, then the
+// forward-Euler TDGL update into the second polarization buffer (Section
+// Time Integration).  The host never sees alpha/beta; it only polls the flag
+// once per batch of iterations to stop issuing more.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pf.h"
+#include "pf_internal.h"
+
+using pf::Geo;
+using pf::Scalars;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr size_t ALIGN = 256;
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+  size_t P_alt, r, p0, p1, q, invd, tlo, thi, vlo, vhi, part, S, total;
+};
+
+bool params_valid(const pf_params* p, std::string* why) {
+  auto fail = [&](const char* m) {
+    if (why) *why = m;
+    return false;
+  };
+  if (!p) return fail("params is NULL");
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail("nx, ny, nz must be >= 1");
+  if ((double)p->nx * p->ny * p->nz > 4.0e10) return fail("grid too large");
+  if (!(p->dx > 0.0) || !std::isfinite(p->dx)) return fail("dx must be finite and > 0");
+  if (p->precision != PF_FP64 && p->precision != PF_FP32) return fail("precision must be PF_FP64 or PF_FP32");
+  if (p->solver != PF_PCG_JACOBI && p->solver != PF_PCG_MG) return fail("solver must be PF_PCG_JACOBI or PF_PCG_MG");
+  if (!(p->poisson_rtol > 0.0) || !std::isfinite(p->poisson_rtol)) return fail("poisson_rtol must be > 0");
+  if (p->poisson_maxit < 1) return fail("poisson_maxit must be >= 1");
+  if (p->periodic_z != 0 && p->periodic_z != 1) return fail("periodic_z must be 0 or 1");
+  if (p->has_eps != 0 && p->has_eps != 1) return fail("has_eps must be 0 or 1");
+  for (double v : {p->a1, p->a11, p->a12, p->g, p->L, p->dt})
+    if (!std::isfinite(v)) return fail("coefficients must be finite");
+  for (int i = 0; i < 7; ++i)
+    if (p->reserved[i] != 0) return fail("reserved fields must be zero");
+  return true;
+}
+
+Layout layout_of(const pf_params* p) {
+  const size_t w = p->precision == PF_FP32 ? 4 : 8;
+  const size_t n = (size_t)p->nx * p->ny * p->nz, nxy = (size_t)p->nx * p->ny;
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align_up(bytes);
+    return o;
+  };
+  L.P_alt = take(3 * n * w);
+  L.r = take(n * w);
+  L.p0 = take(n * w);
+  L.p1 = take(n * w);
+  L.q = take(n * w);
+  L.invd = take(p->has_eps ? n * w : 0);
+  L.tlo = take(nxy);
+  L.thi = take(nxy);
+  L.vlo = take(nxy * w);
+  L.vhi = take(nxy * w);
+  L.part = take(sizeof(double) * pf::MAX_GRID * pf::MAX_NV);
+  L.S = take(sizeof(Scalars));
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+struct pf_ctx {
+  pf_params prm;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int nsm = 0;
+  Geo geo{};
+  pf::LaunchCfg L{};
+  Layout lay{};
+  bool bound = false;
+  void* P_user = nullptr;
+  void* phi = nullptr;
+  const void* eps = nullptr;
+  char* ws = nullptr;
+  int cur = 0;                    // 0: state in P_user, 1: in the workspace copy
+  int singular = 1;               // no Dirichlet face anywhere (or periodic z)
+  bool invd_dirty = true;
+  int est_iters = 8;              // iterations issued before the first poll
+  std::vector<int8_t> tlo_h, thi_h;
+  Scalars* S_tmpl = nullptr;      // pinned host: template written at each call
+  Scalars* S_host = nullptr;      // pinned host: mirror read back
+  std::string err;
+  int64_t launches = 0;           // kernels launched by the current call
+
+  // Profiling: events recorded between consecutive launches; each record
+  // says which kernel family ran in the interval and what it moved.
+  struct Rec {
+    int fam;
+    double bytes;
+    int iter_no;                  // CG launches: iteration number in its solve, else 0
+    int first_bytes_alt;          // 1: cg_p, first iteration moves bytes_first
+    double bytes_first;
+  };
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<Rec> recs;
+  bool have_base = false;
+  std::vector<pf_kernel_stat> stats;
+
+  pf_status fail(pf_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    err = buf;
+    return st;
+  }
+  pf_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(PF_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+  }
+};
+
+#define PF_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return ctx->cuda_fail(e_, #call); \
+  } while (0)
+
+namespace {
+
+enum Fam { F_RHS_MEAN, F_RHS, F_CG_P, F_CG_R, F_FINISH, F_SUB_MEAN, F_TDGL, F_INVDIAG, F_COUNT };
+const char* const FAM_NAMES[F_COUNT] = {"rhs_mean", "rhs", "cg_p", "cg_r", "cg_finish", "sub_mean", "tdgl",
+                                        "invdiag"};
+
+void prof_reset(pf_ctx* ctx) {
+  ctx->stats.assign(F_COUNT, pf_kernel_stat{});
+  for (int f = 0; f < F_COUNT; ++f) std::snprintf(ctx->stats[f].name, sizeof(ctx->stats[f].name), "%s", FAM_NAMES[f]);
+  ctx->recs.clear();
+  ctx->have_base = false;
+}
+
+cudaError_t prof_event(pf_ctx* ctx, size_t i) {
+  while (ctx->ev.size() <= i) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    ctx->ev.push_back(e);
+  }
+  return cudaEventRecord(ctx->ev[i], ctx->stream);
+}
+
+// Call before a launch: records the interval's opening event once.
+void before_launch(pf_ctx* ctx) {
+  if (ctx->prof && !ctx->have_base) {
+    prof_event(ctx, 0);
+    ctx->have_base = true;
+  }
+}
+
+// Call after a launch: counts it and closes its timing interval.
+void after_launch(pf_ctx* ctx, int fam, double bytes, int iter_no = 0, double bytes_first = -1.0) {
+  ctx->launches += 1;
+  if (!ctx->prof) return;
+  pf_ctx::Rec r{fam, bytes, iter_no, bytes_first >= 0.0 ? 1 : 0, bytes_first};
+  ctx->recs.push_back(r);
+  prof_event(ctx, ctx->recs.size());
+}
+
+// After a host wait on the stream: turn the recorded intervals into stats.
+// CG launches numbered beyond the solve's executed iteration count returned
+// at entry and are booked as idle.
+void prof_harvest(pf_ctx* ctx, int executed_iters) {
+  if (!ctx->prof || !ctx->have_base) return;
+  for (size_t i = 0; i < ctx->recs.size(); ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]);
+    const pf_ctx::Rec& r = ctx->recs[i];
+    pf_kernel_stat& st = ctx->stats[r.fam];
+    if (r.iter_no > 0 && r.iter_no > executed_iters) {
+      st.idle_launches += 1;
+      continue;
+    }
+    st.launches += 1;
+    st.total_ms += ms;
+    st.bytes += (r.first_bytes_alt && r.iter_no == 1) ? r.bytes_first : r.bytes;
+  }
+  ctx->recs.clear();
+  ctx->have_base = false;
+}
+
+template <typename T>
+pf::Dev<T> dev_view(pf_ctx* ctx) {
+  pf::Dev<T> d{};
+  char* ws = ctx->ws;
+  const Layout& L = ctx->lay;
+  d.phi = (T*)ctx->phi;
+  d.eps = ctx->prm.has_eps ? (const T*)ctx->eps : nullptr;
+  d.invd = ctx->prm.has_eps ? (T*)(ws + L.invd) : nullptr;
+  d.r = (T*)(ws + L.r);
+  d.p0 = (T*)(ws + L.p0);
+  d.p1 = (T*)(ws + L.p1);
+  d.q = (T*)(ws + L.q);
+  d.bc.tlo = (const int8_t*)(ws + L.tlo);
+  d.bc.thi = (const int8_t*)(ws + L.thi);
+  d.bc.vlo = (const T*)(ws + L.vlo);
+  d.bc.vhi = (const T*)(ws + L.vhi);
+  const double ih2 = ctx->geo.ih2;
+  for (int k = 0; k < 9; ++k) d.tab.v[k] = k ? (T)(1.0 / ((double)k * ih2)) : (T)0;
+  d.part = (double*)(ws + L.part);
+  d.S = (Scalars*)(ws + L.S);
+  return d;
+}
+
+void recompute_singular(pf_ctx* ctx) {
+  if (ctx->prm.periodic_z) {
+    ctx->singular = 1;
+    return;
+  }
+  bool any = false;
+  for (int8_t t : ctx->tlo_h) any |= (t == PF_DIRICHLET);
+  for (int8_t t : ctx->thi_h) any |= (t == PF_DIRICHLET);
+  ctx->singular = any ? 0 : 1;
+}
+
+// Reset the per-call solver state on the device.
+pf_status reset_scalars(pf_ctx* ctx) {
+  ctx->launches = 0;
+  Scalars& s = *ctx->S_tmpl;
+  std::memset(&s, 0, sizeof(Scalars));
+  s.rtol = ctx->prm.poisson_rtol;
+  s.maxit = ctx->prm.poisson_maxit;
+  s.done = 1;
+  PF_CUDA(cudaMemcpyAsync(ctx->lay.S + ctx->ws, &s, sizeof(Scalars), cudaMemcpyHostToDevice, ctx->stream));
+  return PF_OK;
+}
+
+pf_status read_scalars(pf_ctx* ctx) {
+  PF_CUDA(cudaMemcpyAsync(ctx->S_host, ctx->lay.S + ctx->ws, sizeof(Scalars), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  PF_CUDA(cudaStreamSynchronize(ctx->stream));
+  return PF_OK;
+}
+
+// One Poisson solve for the polarization P (device pointer of the current
+// state): r0, PCG iterations until the device flag says done, final update.
+template <typename T>
+pf_status solve(pf_ctx* ctx, const T* P) {
+  pf::Dev<T> d = dev_view<T>(ctx);
+  const Geo& g = ctx->geo;
+  const double N = (double)g.n, w = sizeof(T), e = ctx->prm.has_eps ? 1.0 : 0.0;
+  if (ctx->prm.has_eps && ctx->invd_dirty) {
+    before_launch(ctx);
+    pf::launch_invdiag<T>(ctx->L, g, d);
+    after_launch(ctx, F_INVDIAG, 2 * N * w);
+    ctx->invd_dirty = false;
+  }
+  if (ctx->singular) {
+    before_launch(ctx);
+    pf::launch_rhs_mean<T>(ctx->L, g, d, P);
+    after_launch(ctx, F_RHS_MEAN, (3 + e) * N * w);
+  }
+  before_launch(ctx);
+  pf::launch_rhs<T>(ctx->L, g, d, P, 0, 0);
+  after_launch(ctx, F_RHS, (5 + 2 * e) * N * w);
+  PF_CUDA(cudaGetLastError());
+  // Every issued iteration either runs or returns at entry once the device
+  // flag is set, and the device sets it by iteration maxit at the latest.
+  const int maxit = ctx->prm.poisson_maxit;
+  int issued = 0;
+  int batch = std::max(1, std::min(ctx->est_iters, maxit));
+  for (;;) {
+    for (int i = 0; i < batch; ++i) {
+      const int it = issued + i + 1;
+      before_launch(ctx);
+      pf::launch_cg_p<T>(ctx->L, g, d);
+      after_launch(ctx, F_CG_P, (6 + 2 * e) * N * w, it, (3 + 2 * e) * N * w);
+      pf::launch_cg_r<T>(ctx->L, g, d, 0, 0);
+      after_launch(ctx, F_CG_R, (3 + e) * N * w, it);
+    }
+    issued += batch;
+    PF_CUDA(cudaGetLastError());
+    pf_status st = read_scalars(ctx);
+    if (st != PF_OK) return st;
+    prof_harvest(ctx, ctx->S_host->iter);
+    if (ctx->S_host->done) break;
+    if (issued >= maxit)
+      return ctx->fail(PF_ERR_STATE, "internal: solver did not stop after %d iterations", issued);
+    batch = std::min(std::max(2, ctx->est_iters / 8), maxit - issued);
+  }
+  const Scalars& s = *ctx->S_host;
+  if (!s.zero_x) ctx->est_iters = std::max(1, s.iter);
+  before_launch(ctx);
+  pf::launch_cg_finish<T>(ctx->L, g, d, ctx->singular);
+  after_launch(ctx, F_FINISH, (s.zero_x ? 1.0 : (s.pending ? 3.0 : 1.0)) * N * w);
+  if (ctx->singular) {
+    pf::launch_sub_mean<T>(ctx->L, g, d);
+    after_launch(ctx, F_SUB_MEAN, 2 * N * w);
+  }
+  PF_CUDA(cudaGetLastError());
+  return PF_OK;
+}
+
+template <typename T>
+pf_status run_steps(pf_ctx* ctx, int nsteps) {
+  pf::Dev<T> d = dev_view<T>(ctx);
+  const Geo& g = ctx->geo;
+  T* Pbuf[2] = {(T*)ctx->P_user, (T*)(ctx->ws + ctx->lay.P_alt)};
+  const double coef[5] = {ctx->prm.a1, ctx->prm.a11, ctx->prm.a12, ctx->prm.g, ctx->prm.dt * ctx->prm.L};
+  for (int s = 0; s < nsteps; ++s) {
+    T* P = Pbuf[ctx->cur];
+    pf_status st = solve<T>(ctx, P);
+    if (st != PF_OK) return st;
+    before_launch(ctx);
+    pf::launch_tdgl<T>(ctx->L, g, d, P, Pbuf[ctx->cur ^ 1], coef);
+    after_launch(ctx, F_TDGL, 7.0 * (double)g.n * sizeof(T));
+    PF_CUDA(cudaGetLastError());
+    ctx->cur ^= 1;
+  }
+  if (ctx->cur == 1) {
+    PF_CUDA(cudaMemcpyAsync(Pbuf[0], Pbuf[1], sizeof(T) * 3 * (size_t)g.n, cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+    ctx->cur = 0;
+  }
+  return PF_OK;
+}
+
+pf_status finish_info(pf_ctx* ctx, int nsteps, pf_step_info* info) {
+  pf_status st = read_scalars(ctx);
+  if (st != PF_OK) return st;
+  prof_harvest(ctx, 0);
+  const Scalars& s = *ctx->S_host;
+  pf_status result = PF_OK;
+  if (s.nonfinite) result = ctx->fail(PF_ERR_NONFINITE, "non-finite value in the Poisson solver scalars");
+  else if (s.nonconv) result = ctx->fail(PF_ERR_NOCONV, "%d Poisson solve(s) hit poisson_maxit", s.nonconv);
+  if (info) {
+    info->steps_done = nsteps;
+    info->last_iters = s.last_iters;
+    info->total_iters = s.total_iters;
+    info->last_relres = s.last_rel;
+    info->nonconverged = s.nonconv;
+    info->status = result;
+    info->kernel_launches = ctx->launches;
+  }
+  return result;
+}
+
+pf_status check_ready(pf_ctx* ctx) {
+  if (!ctx) return PF_ERR_ARG;
+  if (!ctx->bound) return ctx->fail(PF_ERR_STATE, "no buffers bound (call pf_bind first)");
+  return PF_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pf_workspace_bytes(const pf_params* params) {
+  if (!params_valid(params, nullptr)) return 0;
+  return layout_of(params).total;
+}
+
+pf_status pf_create(const pf_params* params, void* cuda_stream, pf_ctx** out) {
+  std::string why;
+  if (!out) {
+    g_create_error = "out is NULL";
+    return PF_ERR_ARG;
+  }
+  *out = nullptr;
+  if (!params_valid(params, &why)) {
+    g_create_error = why;
+    return PF_ERR_ARG;
+  }
+  pf_ctx* ctx = new pf_ctx();
+  ctx->prm = *params;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->S_tmpl, 2 * sizeof(Scalars));
+  if (e != cudaSuccess) {
+    g_create_error = std::string("CUDA: ") + cudaGetErrorString(e);
+    delete ctx;
+    return PF_ERR_CUDA;
+  }
+  ctx->S_host = ctx->S_tmpl + 1;
+  Geo& g = ctx->geo;
+  g.nx = params->nx;
+  g.ny = params->ny;
+  g.nz = params->nz;
+  g.periodic_z = params->periodic_z;
+  g.nxy = (long long)g.nx * g.ny;
+  g.n = g.nxy * g.nz;
+  g.ih = 1.0 / params->dx;
+  g.ih2 = g.ih * g.ih;
+  g.tiles_x = (g.nx + pf::TX - 1) / pf::TX;
+  g.tiles_y = (g.ny + pf::TY - 1) / pf::TY;
+  const long long cols = (long long)g.tiles_x * g.tiles_y;
+  const long long want = 4LL * ctx->nsm;
+  g.tz = 1;
+  for (int tz : {16, 8, 4, 2}) {
+    if (cols * ((g.nz + tz - 1) / tz) >= want) {
+      g.tz = tz;
+      break;
+    }
+  }
+  g.tiles_z = (g.nz + g.tz - 1) / g.tz;
+  g.ntiles = cols * g.tiles_z;
+  ctx->L.block = dim3(pf::TX, pf::TY, 1);
+  ctx->L.grid = (int)std::min<long long>(g.ntiles, std::min(pf::MAX_GRID, 8 * ctx->nsm));
+  ctx->L.stream = ctx->stream;
+  ctx->lay = layout_of(params);
+  ctx->tlo_h.assign((size_t)g.nxy, 0);
+  ctx->thi_h.assign((size_t)g.nxy, 0);
+  recompute_singular(ctx);
+  prof_reset(ctx);
+  *out = ctx;
+  return PF_OK;
+}
+
+pf_status pf_bind(pf_ctx* ctx, void* P, void* phi, const void* eps, void* workspace, size_t workspace_bytes) {
+  if (!ctx) return PF_ERR_ARG;
+  ctx->bound = false;
+  if (!P || !phi || !workspace) return ctx->fail(PF_ERR_ARG, "P, phi and workspace must be non-NULL");
+  if (ctx->prm.has_eps && !eps) return ctx->fail(PF_ERR_ARG, "has_eps = 1 but eps is NULL");
+  if (workspace_bytes < ctx->lay.total)
+    return ctx->fail(PF_ERR_ARG, "workspace too small: %zu < %zu bytes", workspace_bytes, ctx->lay.total);
+  if (((uintptr_t)workspace % ALIGN) != 0) return ctx->fail(PF_ERR_ARG, "workspace must be 256-byte aligned");
+  if (((uintptr_t)P % 16) || ((uintptr_t)phi % 16) || (eps && ctx->prm.has_eps && ((uintptr_t)eps % 16)))
+    return ctx->fail(PF_ERR_ARG, "P, phi and eps must be 16-byte aligned");
+  if (!is_device_ptr(P) || !is_device_ptr(phi) || !is_device_ptr(workspace) ||
+      (ctx->prm.has_eps && !is_device_ptr(eps)))
+    return ctx->fail(PF_ERR_ARG, "P, phi, eps and workspace must be device pointers");
+  ctx->P_user = P;
+  ctx->phi = phi;
+  ctx->eps = ctx->prm.has_eps ? eps : nullptr;
+  ctx->ws = (char*)workspace;
+  ctx->cur = 0;
+  ctx->invd_dirty = true;
+  const Layout& L = ctx->lay;
+  PF_CUDA(cudaMemsetAsync(ctx->ws + L.tlo, 0, L.part - L.tlo, ctx->stream));
+  std::fill(ctx->tlo_h.begin(), ctx->tlo_h.end(), 0);
+  std::fill(ctx->thi_h.begin(), ctx->thi_h.end(), 0);
+  recompute_singular(ctx);
+  PF_CUDA(cudaMemsetAsync(ctx->ws + L.S, 0, sizeof(Scalars), ctx->stream));
+  PF_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->bound = true;
+  return PF_OK;
+}
+
+pf_status pf_set_bc(pf_ctx* ctx, int32_t face, const int8_t* type_xy, const double* volts_xy) {
+  pf_status st = check_ready(ctx);
+  if (st != PF_OK) return st;
+  if (face != PF_ZLO && face != PF_ZHI) return ctx->fail(PF_ERR_ARG, "face must be PF_ZLO or PF_ZHI");
+  if (!type_xy) return ctx->fail(PF_ERR_ARG, "type_xy is NULL");
+  const size_t nxy = (size_t)ctx->geo.nxy;
+  for (size_t i = 0; i < nxy; ++i)
+    if (type_xy[i] != PF_NEUMANN && type_xy[i] != PF_DIRICHLET)
+      return ctx->fail(PF_ERR_ARG, "type_xy[%zu] = %d is neither PF_NEUMANN nor PF_DIRICHLET", i, (int)type_xy[i]);
+  if (volts_xy)
+    for (size_t i = 0; i < nxy; ++i)
+      if (!std::isfinite(volts_xy[i])) return ctx->fail(PF_ERR_ARG, "volts_xy[%zu] is not finite", i);
+  const Layout& L = ctx->lay;
+  char* tdst = ctx->ws + (face == PF_ZLO ? L.tlo : L.thi);
+  char* vdst = ctx->ws + (face == PF_ZLO ? L.vlo : L.vhi);
+  PF_CUDA(cudaMemcpyAsync(tdst, type_xy, nxy, cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->prm.precision == PF_FP32) {
+    std::vector<float> v(nxy, 0.f);
+    if (volts_xy)
+      for (size_t i = 0; i < nxy; ++i) v[i] = (float)volts_xy[i];
+    PF_CUDA(cudaMemcpyAsync(vdst, v.data(), nxy * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    PF_CUDA(cudaStreamSynchronize(ctx->stream));
+  } else {
+    std::vector<double> v(nxy, 0.0);
+    if (volts_xy) std::memcpy(v.data(), volts_xy, nxy * sizeof(double));
+    PF_CUDA(cudaMemcpyAsync(vdst, v.data(), nxy * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    PF_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  std::vector<int8_t>& h = face == PF_ZLO ? ctx->tlo_h : ctx->thi_h;
+  std::memcpy(h.data(), type_xy, nxy);
+  recompute_singular(ctx);
+  ctx->invd_dirty = true;
+  return PF_OK;
+}
+
+pf_status pf_step(pf_ctx* ctx, int32_t nsteps, pf_step_info* info) {
+  pf_status st = check_ready(ctx);
+  if (st != PF_OK) return st;
+  if (nsteps < 0) return ctx->fail(PF_ERR_ARG, "nsteps must be >= 0");
+  st = reset_scalars(ctx);
+  if (st != PF_OK) return st;
+  st = ctx->prm.precision == PF_FP32 ? run_steps<float>(ctx, nsteps) : run_steps<double>(ctx, nsteps);
+  if (st != PF_OK) return st;
+  return finish_info(ctx, nsteps, info);
+}
+
+pf_status pf_step_host(pf_ctx* ctx, void* P_host, void* phi_host, int32_t nsteps, pf_step_info* info) {
+  pf_status st = check_ready(ctx);
+  if (st != PF_OK) return st;
+  if (!P_host || !phi_host) return ctx->fail(PF_ERR_ARG, "P_host and phi_host must be non-NULL");
+  if (nsteps < 0) return ctx->fail(PF_ERR_ARG, "nsteps must be >= 0");
+  const size_t w = ctx->prm.precision == PF_FP32 ? 4 : 8;
+  const size_t n = (size_t)ctx->geo.n;
+  st = reset_scalars(ctx);
+  if (st != PF_OK) return st;
+  for (int s = 0; s < nsteps; ++s) {
+    PF_CUDA(cudaMemcpyAsync(ctx->P_user, P_host, 3 * n * w, cudaMemcpyHostToDevice, ctx->stream));
+    PF_CUDA(cudaMemcpyAsync(ctx->phi, phi_host, n * w, cudaMemcpyHostToDevice, ctx->stream));
+    st = ctx->prm.precision == PF_FP32 ? run_steps<float>(ctx, 1) : run_steps<double>(ctx, 1);
+    if (st != PF_OK) return st;
+    PF_CUDA(cudaMemcpyAsync(P_host, ctx->P_user, 3 * n * w, cudaMemcpyDeviceToHost, ctx->stream));
+    PF_CUDA(cudaMemcpyAsync(phi_host, ctx->phi, n * w, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  return finish_info(ctx, nsteps, info);
+}
+
+pf_status pf_solve_potential(pf_ctx* ctx, pf_step_info* info) {
+  pf_status st = check_ready(ctx);
+  if (st != PF_OK) return st;
+  if (ctx->cur != 0) return ctx->fail(PF_ERR_STATE, "internal: state not in the bound P buffer");
+  st = reset_scalars(ctx);
+  if (st != PF_OK) return st;
+  st = ctx->prm.precision == PF_FP32 ? solve<float>(ctx, (const float*)ctx->P_user)
+                                     : solve<double>(ctx, (const double*)ctx->P_user);
+  if (st != PF_OK) return st;
+  return finish_info(ctx, 0, info);
+}
+
+pf_status pf_adjoint_step(pf_ctx* ctx, const void*, void*, double*, double*) {
+  if (!ctx) return PF_ERR_ARG;
+  return ctx->fail(PF_ERR_NOTIMPL, "pf_adjoint_step is not available in this version");
+}
+
+pf_status pf_profile_enable(pf_ctx* ctx, int32_t enable) {
+  if (!ctx) return PF_ERR_ARG;
+  if (enable != 0 && enable != 1) return ctx->fail(PF_ERR_ARG, "enable must be 0 or 1");
+  ctx->prof = enable == 1;
+  prof_reset(ctx);
+  return PF_OK;
+}
+
+int32_t pf_profile_read(const pf_ctx* ctx, pf_kernel_stat* out, int32_t max) {
+  if (!ctx) return -1;
+  const int32_t n = (int32_t)ctx->stats.size();
+  for (int32_t i = 0; i < n && i < max && out; ++i) out[i] = ctx->stats[i];
+  return n;
+}
+
+pf_status pf_destroy(pf_ctx* ctx) {
+  if (!ctx) return PF_OK;
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  if (ctx->S_tmpl) cudaFreeHost(ctx->S_tmpl);
+  delete ctx;
+  return PF_OK;
+}
+
+const char* pf_last_error(const pf_ctx* ctx) {
+  if (!ctx) return g_create_error.c_str();
+  return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+"""Thin ctypes binding of the C ABI in ``include/pf.h`` (same names).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``_lib/libpfgb.so``.  There is no CPU fallback; if the library is
+missing or cannot be loaded, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_lib", "libpfgb.so")
+
+PF_OK, PF_ERR_ARG, PF_ERR_CUDA, PF_ERR_NOCONV, PF_ERR_NONFINITE, PF_ERR_TIMEOUT, PF_ERR_STATE, \
+    PF_ERR_NOTIMPL = range(8)
+PF_FP64, PF_FP32 = 0, 1
+PF_PCG_JACOBI, PF_PCG_MG = 0, 1
+PF_ZLO, PF_ZHI = 0, 1
+PF_NEUMANN, PF_DIRICHLET = 0, 1
+
+STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_CUDA", 3: "PF_ERR_NOCONV", 4: "PF_ERR_NONFINITE",
+                5: "PF_ERR_TIMEOUT", 6: "PF_ERR_STATE", 7: "PF_ERR_NOTIMPL"}
+
+# Every symbol the header declares.
+EXPORTS = ["pf_workspace_bytes", "pf_create", "pf_bind", "pf_set_bc", "pf_step", "pf_step_host",
+           "pf_solve_potential", "pf_adjoint_step", "pf_profile_enable", "pf_profile_read", "pf_destroy",
+           "pf_last_error"]
+
+
+class pf_params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("dx", C.c_double),
+                ("a1", C.c_double), ("a11", C.c_double), ("a12", C.c_double),
+                ("g", C.c_double), ("L", C.c_double), ("dt", C.c_double),
+                ("precision", C.c_int32), ("solver", C.c_int32),
+                ("poisson_rtol", C.c_double), ("poisson_maxit", C.c_int32),
+                ("periodic_z", C.c_int32), ("has_eps", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
+
+
+class pf_step_info(C.Structure):
+    _fields_ = [("steps_done", C.c_int32), ("last_iters", C.c_int32), ("total_iters", C.c_int64),
+                ("last_relres", C.c_double), ("nonconverged", C.c_int32), ("status", C.c_int32),
+                ("kernel_launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pf_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("idle_launches", C.c_int64),
+                ("total_ms", C.c_double), ("bytes", C.c_double)]
+
+
+class PfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("GPU library %s not built: run paper_1202_6116_gb300.build.build() "
+                               "(there is no CPU fallback)" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        vp, i32, sz = C.c_void_p, C.c_int32, C.c_size_t
+        L.pf_workspace_bytes.restype = sz
+        L.pf_workspace_bytes.argtypes = [C.POINTER(pf_params)]
+        L.pf_create.restype = i32
+        L.pf_create.argtypes = [C.POINTER(pf_params), vp, C.POINTER(vp)]
+        L.pf_bind.restype = i32
+        L.pf_bind.argtypes = [vp, vp, vp, vp, vp, sz]
+        L.pf_set_bc.restype = i32
+        L.pf_set_bc.argtypes = [vp, i32, vp, vp]
+        L.pf_step.restype = i32
+        L.pf_step.argtypes = [vp, i32, C.POINTER(pf_step_info)]
+        L.pf_step_host.restype = i32
+        L.pf_step_host.argtypes = [vp, vp, vp, i32, C.POINTER(pf_step_info)]
+        L.pf_solve_potential.restype = i32
+        L.pf_solve_potential.argtypes = [vp, C.POINTER(pf_step_info)]
+        L.pf_adjoint_step.restype = i32
+        L.pf_adjoint_step.argtypes = [vp, vp, vp, vp, vp]
+        L.pf_profile_enable.restype = i32
+        L.pf_profile_enable.argtypes = [vp, i32]
+        L.pf_profile_read.restype = i32
+        L.pf_profile_read.argtypes = [vp, vp, i32]
+        L.pf_destroy.restype = i32
+        L.pf_destroy.argtypes = [vp]
+        L.pf_last_error.restype = C.c_char_p
+        L.pf_last_error.argtypes = [vp]
+        _lib = L
+    return _lib
+
+
+def _addr(x):
+    """Device/host address of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def pf_last_error(ctx=None) -> str:
+    return lib().pf_last_error(ctx).decode()
+
+
+def check(status, ctx=None, ok=(PF_OK,)):
+    if status not in ok:
+        raise PfError(status, pf_last_error(ctx))
+    return status
+
+
+def pf_workspace_bytes(params: pf_params) -> int:
+    return lib().pf_workspace_bytes(C.byref(params))
+
+
+def pf_create(params: pf_params, stream=None):
+    """Returns the opaque context handle (an int)."""
+    ctx = C.c_void_p()
+    st = lib().pf_create(C.byref(params), _addr(stream) if stream is not None else None, C.byref(ctx))
+    check(st, None)
+    return ctx.value
+
+
+def pf_bind(ctx, P, phi, eps, workspace, workspace_bytes):
+    return check(lib().pf_bind(ctx, _addr(P), _addr(phi), _addr(eps), _addr(workspace), workspace_bytes), ctx)
+
+
+def pf_set_bc(ctx, face, type_xy, volts_xy=None):
+    """type_xy: contiguous int8 host array (nx*ny); volts_xy: float64 host array or None."""
+    return check(lib().pf_set_bc(ctx, face, _addr(type_xy), _addr(volts_xy)), ctx)
+
+
+def pf_step(ctx, nsteps, ok=(PF_OK,)):
+    info = pf_step_info()
+    st = lib().pf_step(ctx, nsteps, C.byref(info))
+    check(st, ctx, ok)
+    return st, info
+
+
+def pf_step_host(ctx, P_host, phi_host, nsteps, ok=(PF_OK,)):
+    info = pf_step_info()
+    st = lib().pf_step_host(ctx, _addr(P_host), _addr(phi_host), nsteps, C.byref(info))
+    check(st, ctx, ok)
+    return st, info
+
+
+def pf_solve_potential(ctx, ok=(PF_OK,)):
+    info = pf_step_info()
+    st = lib().pf_solve_potential(ctx, C.byref(info))
+    check(st, ctx, ok)
+    return st, info
+
+
+def pf_adjoint_step(ctx, lam_in, lam_out, grad_params, grad_volts):
+    return lib().pf_adjoint_step(ctx, _addr(lam_in), _addr(lam_out), _addr(grad_params), _addr(grad_volts))
+
+
+def pf_profile_enable(ctx, enable=1):
+    return check(lib().pf_profile_enable(ctx, int(enable)), ctx)
+
+
+def pf_profile_read(ctx):
+    """Per-kernel-family statistics as a list of dicts."""
+    n = lib().pf_profile_read(ctx, None, 0)
+    arr = (pf_kernel_stat * max(n, 1))()
+    lib().pf_profile_read(ctx, C.cast(arr, C.c_void_p), n)
+    return [dict(name=a.name.decode(), launches=a.launches, idle_launches=a.idle_launches,
+                 total_ms=a.total_ms, bytes=a.bytes) for a in arr[:n]]
+
+
+def pf_destroy(ctx):
+    return lib().pf_destroy(ctx)

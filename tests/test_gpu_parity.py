@@ -1,0 +1,189 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, on the
+same seeded inputs.  Error metric: max|gpu - oracle| / max|oracle| per field.
+FP64 bar 1e-10 on P and phi; FP32 bar 1e-4 on P (FP32 storage, FP64-accurate
+Poisson reductions) and the switched fraction within 0.1 percentage points."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1202_6116_gb300 import build as B
+from paper_1202_6116_gb300 import pf
+from paper_1202_6116_gb300 import workloads as W
+from paper_1202_6116_gb300.film import Film
+
+from helpers import mixed_workload, oracle_run, relerr, switched_fraction, oracle_grid
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+FP32_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    pf.lib()
+
+
+def gpu_run(w, steps=None, **over):
+    f = Film(w, **over)
+    st, info = f.step(w.steps if steps is None else steps, ok=(pf.PF_OK, pf.PF_ERR_NOCONV))
+    P, phi = f.numpy()
+    f.close()
+    return P, phi, st, info
+
+
+@pytest.fixture(scope="module")
+def grounded_32():
+    w = W.film_fp64_grounded()
+    ref = oracle_run(w)
+    ref_tight = oracle_run(w, rtol=1e-14)
+    return w, ref, ref_tight
+
+
+def test_fp64_grounded_film_200_steps(grounded_32):
+    """32^3 FP64 film between grounded electrodes, 200 steps at CG 1e-12."""
+    w, (Po, phio, sto, io), (Pt, phit, _, _) = grounded_32
+    P, phi, st, info = gpu_run(w)
+    assert st == pf.PF_OK and sto == O.OK
+    assert relerr(P, Po) <= FP64_TOL
+    assert relerr(phi, phio) <= FP64_TOL
+    assert relerr(P, Pt) <= FP64_TOL
+    assert relerr(phi, phit) <= FP64_TOL
+    assert abs(info["total_iters"] - io["total_iters"]) <= 0.02 * io["total_iters"] + 5
+
+
+@pytest.mark.parametrize("case", [
+    dict(nx=45, ny=38, nz=13, seed=1, eps=False),
+    dict(nx=45, ny=38, nz=13, seed=2, eps=True),
+    dict(nx=70, ny=9, nz=3, seed=3, eps=True),
+    dict(nx=33, ny=17, nz=1, seed=4, eps=False),
+])
+def test_fp64_ragged_mixed_boundaries(case):
+    """Ragged grids (partial tiles in x, y and z) with random electrode masks and
+    voltages on both faces, optionally a random permittivity field."""
+    w = mixed_workload(case["nx"], case["ny"], case["nz"], case["seed"], eps=case["eps"], steps=8)
+    Po, phio, _, _ = oracle_run(w, rtol=1e-13)
+    P, phi, st, _ = gpu_run(w, poisson_rtol=1e-13)
+    assert st == pf.PF_OK
+    assert relerr(P, Po) <= FP64_TOL
+    assert relerr(phi, phio) <= FP64_TOL
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_fp64_singular_problems(periodic):
+    """No electrode anywhere: fully periodic box, or open top and bottom.  The
+    operator is singular; both sides use the zero-mean potential."""
+    nx, ny, nz = 24, 20, 12
+    z8 = np.zeros((ny, nx), np.int8)
+    zv = np.zeros((ny, nx))
+    w = W.Workload("singular", nx, ny, nz, W.random_film(nx, ny, nz, 5, -0.5, 0.5), z8, zv, z8, zv,
+                   periodic_z=periodic, steps=6, rtol=1e-13)
+    Po, phio, _, _ = oracle_run(w)
+    P, phi, st, _ = gpu_run(w)
+    assert st == pf.PF_OK
+    assert abs(phi.mean()) < 1e-12
+    assert relerr(P, Po) <= FP64_TOL
+    assert relerr(phi, phio) <= FP64_TOL
+
+
+def test_fp64_solve_potential_only():
+    w = mixed_workload(40, 24, 10, 7, eps=True)
+    phio, st, it, rel = O.solve_potential(oracle_grid(w), w.P0, rtol=1e-13)
+    f = Film(w, poisson_rtol=1e-13)
+    st, info = f.solve_potential()
+    P, phi = f.numpy()
+    f.close()
+    assert st == pf.PF_OK
+    assert np.array_equal(P, w.P0)
+    assert relerr(phi, phio) <= FP64_TOL
+    assert abs(info["last_iters"] - it) <= 2
+
+
+def test_homogeneous_recurrence_on_gpu():
+    """Uniform [111] P between grounded electrodes: phi stays 0, no CG iterations,
+    and each component follows p <- p + dt (2p - 5.2 p^3)."""
+    nx, ny, nz = 40, 16, 8
+    one = np.ones((ny, nx), np.int8)
+    zv = np.zeros((ny, nx))
+    P0 = np.full((3, nz, ny, nx), 0.1)
+    w = W.Workload("uniform", nx, ny, nz, P0, one, zv, one, zv, steps=30, rtol=1e-12)
+    P, phi, st, info = gpu_run(w)
+    p = 0.1
+    for _ in range(30):
+        p = p + 0.01 * (2 * p - 5.2 * p ** 3)
+    assert st == pf.PF_OK
+    assert np.abs(P - p).max() < 1e-15
+    assert np.abs(phi).max() == 0.0
+    assert info["total_iters"] == 0
+
+
+def test_noconv_is_reported_and_state_valid():
+    w = mixed_workload(32, 16, 8, 9, steps=3, rtol=1e-14)
+    P, phi, st, info = gpu_run(w, poisson_maxit=2)
+    assert st == pf.PF_ERR_NOCONV
+    assert info["nonconverged"] == 3 and info["last_iters"] == 2 and info["steps_done"] == 3
+    assert np.isfinite(P).all() and np.isfinite(phi).all()
+    Po, phio, sto, io = O.step(oracle_grid(w), O.Params(rtol=1e-14, maxit=2), w.P0, None, 3)
+    assert sto == O.NOCONV
+    assert relerr(P, Po) <= FP64_TOL and relerr(phi, phio) <= FP64_TOL
+
+
+def test_nonfinite_input_is_reported():
+    w = mixed_workload(16, 16, 4, 10, steps=1)
+    w.P0[1, 2, 3, 4] = np.nan
+    f = Film(w)
+    st, info = f.step(1, ok=(pf.PF_ERR_NONFINITE,))
+    f.close()
+    assert st == pf.PF_ERR_NONFINITE
+
+
+def test_step_host_matches_device_path():
+    w = mixed_workload(36, 20, 6, 11, steps=4, rtol=1e-12)
+    P_dev, phi_dev, _, _ = gpu_run(w)
+    f = Film(w)
+    Ph = torch.as_tensor(w.P0).clone().pin_memory()
+    phih = torch.zeros(w.shape, dtype=torch.float64).pin_memory()
+    st, info = pf.pf_step_host(f.ctx, Ph, phih, 4)
+    f.close()
+    assert st == pf.PF_OK
+    assert np.array_equal(Ph.numpy(), P_dev) and np.array_equal(phih.numpy(), phi_dev)
+
+
+def test_bad_arguments_on_gpu():
+    w = mixed_workload(8, 8, 4, 12)
+    f = Film(w)
+    bad = np.full(64, 3, np.int8)
+    with pytest.raises(pf.PfError):
+        pf.pf_set_bc(f.ctx, pf.PF_ZLO, bad, None)
+    with pytest.raises(pf.PfError):
+        pf.pf_set_bc(f.ctx, 5, np.zeros(64, np.int8), None)
+    with pytest.raises(pf.PfError):
+        pf.pf_bind(f.ctx, f.P, f.phi, None, f.workspace, 16)
+    assert pf.pf_adjoint_step(f.ctx, None, None, None, None) == pf.PF_ERR_NOTIMPL
+    f.close()
+
+
+# ------------------------------------------------------------------ FP32 mode
+
+def test_fp32_strip_electrodes_vs_fp64_oracle():
+    """The strip-electrode thin film, shrunk to 64x64x16, 100 steps, CG 1e-8:
+    FP32 fields with FP64-accurate reductions against the FP64 oracle."""
+    w = W.film_strip_fp32(64, 64, 16, steps=100)
+    Po, phio, _, _ = oracle_run(w.with_(precision="fp64"), rtol=1e-12)
+    P, phi, st, info = gpu_run(w)
+    assert st == pf.PF_OK
+    assert relerr(P, Po) <= FP32_TOL
+    assert abs(switched_fraction(P) - switched_fraction(Po)) <= 1e-3
+
+
+def test_fp32_tip_electrode_vs_fp64_oracle():
+    """The tip-electrode stripe-domain film, shrunk to 64x64x16, 40 steps, CG 1e-7."""
+    w = W.film_tip_fp32(64, 64, 16, steps=40).with_(solver="pcg")
+    Po, phio, _, _ = oracle_run(w.with_(precision="fp64"), rtol=1e-12)
+    P, phi, st, info = gpu_run(w)
+    assert st == pf.PF_OK
+    assert relerr(P, Po) <= FP32_TOL
+    assert abs(switched_fraction(P) - switched_fraction(Po)) <= 1e-3
