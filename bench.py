@@ -32,15 +32,21 @@ L2_BYTES = 129 * 2 ** 20
 WORKLOADS = ("strips", "tip", "grounded")
 
 
-def make_workload(name, seed_offset=0):
+def make_workload(name, seed_offset=0, solver=None):
     from paper_1202_6116_gb300 import workloads as W
     if name == "strips":
-        return W.film_strip_fp32(seed=1 + seed_offset)
-    if name == "tip":
-        return W.film_tip_fp32(seed=2 + seed_offset)
-    if name == "grounded":
-        return W.film_fp64_grounded(seed=0 + seed_offset)
-    raise ValueError(name)
+        w = W.film_strip_fp32(seed=1 + seed_offset)
+    elif name == "tip":
+        w = W.film_tip_fp32(seed=2 + seed_offset)
+    elif name == "grounded":
+        w = W.film_fp64_grounded(seed=0 + seed_offset)
+    else:
+        raise ValueError(name)
+    if solver == "mg":
+        w = w.with_(solver="mg", maxit=500)      # MG-PCG needs tens of iterations, not thousands
+    elif solver:
+        w = w.with_(solver=solver)
+    return w
 
 
 def sample_workload(name):
@@ -164,7 +170,7 @@ def run_ours(args):
     B.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    w = make_workload(args.workload, seed_offset=rank)
+    w = make_workload(args.workload, seed_offset=rank, solver=args.solver)
     film = Film(w, device=dev)
     stream = film.stream
     flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
@@ -300,7 +306,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 initial state, electrode masks of the workload)",
-            "config": workload_config(make_workload(args.workload), args.workload, "n/a (CPU)"),
+            "config": workload_config(make_workload(args.workload, solver=args.solver), args.workload, "n/a (CPU)"),
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%s, FP64 serial oracle, %d steps after %d warm-up steps" %
@@ -316,6 +322,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--workload", choices=WORKLOADS, default="strips")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--solver", choices=("pcg", "mg"), default=None,
+                    help="override the workload's Poisson preconditioner (Jacobi or multigrid)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

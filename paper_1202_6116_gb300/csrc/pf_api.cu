@@ -31,8 +31,50 @@ constexpr size_t ALIGN = 256;
 
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
+// One multigrid level on the host: dimensions, coarsening factors to the
+// next level and workspace offsets (level 0 uses r, z, zt and the fine masks).
+struct MgLevelHost {
+  int nx, ny, nz;
+  int fx, fy, fz;
+  double ax, ay, az;
+  size_t f, e, et, tlo, thi;
+  pf::MarchCfg mc;
+  long long n() const { return (long long)nx * ny * nz; }
+  long long nxy() const { return (long long)nx * ny; }
+};
+
+// Level dimensions: halve every even dimension until none can be halved.
+std::vector<MgLevelHost> mg_levels(const pf_params* p) {
+  std::vector<MgLevelHost> L;
+  MgLevelHost l{};
+  l.nx = p->nx;
+  l.ny = p->ny;
+  l.nz = p->nz;
+  const double ih2 = 1.0 / (p->dx * p->dx);
+  l.ax = l.ay = l.az = ih2;
+  for (;;) {
+    l.fx = (l.nx % 2 == 0 && l.nx > 1) ? 2 : 1;
+    l.fy = (l.ny % 2 == 0 && l.ny > 1) ? 2 : 1;
+    l.fz = (l.nz % 2 == 0 && l.nz > 1) ? 2 : 1;
+    const bool last = (l.fx == 1 && l.fy == 1 && l.fz == 1) || (int)L.size() + 1 == pf::MG_MAX_LEVELS;
+    if (last) l.fx = l.fy = l.fz = 1;
+    L.push_back(l);
+    if (last) break;
+    MgLevelHost c{};
+    c.nx = l.nx / l.fx;
+    c.ny = l.ny / l.fy;
+    c.nz = l.nz / l.fz;
+    c.ax = l.ax / (l.fx * l.fx);
+    c.ay = l.ay / (l.fy * l.fy);
+    c.az = l.az / (l.fz * l.fz);
+    l = c;
+  }
+  return L;
+}
+
 struct Layout {
-  size_t P_alt, r, p0, p1, q, invd, tlo, thi, vlo, vhi, part, S, total;
+  size_t P_alt, r, p0, p1, q, invd, tlo, thi, vlo, vhi, part, S, z, zt, total;
+  std::vector<MgLevelHost> mg;
 };
 
 bool params_valid(const pf_params* p, std::string* why) {
@@ -50,6 +92,14 @@ bool params_valid(const pf_params* p, std::string* why) {
   if (p->poisson_maxit < 1) return fail("poisson_maxit must be >= 1");
   if (p->periodic_z != 0 && p->periodic_z != 1) return fail("periodic_z must be 0 or 1");
   if (p->has_eps != 0 && p->has_eps != 1) return fail("has_eps must be 0 or 1");
+  if (p->solver == PF_PCG_MG) {
+    if (p->has_eps) return fail("the multigrid preconditioner needs eps = 1 (has_eps = 0)");
+    std::vector<MgLevelHost> L = mg_levels(p);
+    if (L.size() < 2) return fail("multigrid needs at least one even grid dimension");
+    if (L.back().n() > pf::MG_MAX_COARSE)
+      return fail("multigrid: the coarsest level has more than 1024 cells (make nx, ny, nz powers of two "
+                  "times small factors)");
+  }
   for (double v : {p->a1, p->a11, p->a12, p->g, p->L, p->dt})
     if (!std::isfinite(v)) return fail("coefficients must be finite");
   for (int i = 0; i < 7; ++i)
@@ -77,10 +127,57 @@ Layout layout_of(const pf_params* p) {
   L.thi = take(nxy);
   L.vlo = take(nxy * w);
   L.vhi = take(nxy * w);
-  L.part = take(sizeof(double) * pf::MAX_GRID * pf::MAX_NV);
+  // reduction partials: per block (flat kernels) or per tile (plane-march
+  // kernels; at most one tile per column group of MTX x MTY and plane)
+  const size_t max_tiles = (size_t)((p->nx + pf::MTX - 1) / pf::MTX) * ((p->ny + pf::MTY - 1) / pf::MTY) * p->nz;
+  L.part = take(sizeof(double) * std::max<size_t>((size_t)pf::MAX_GRID * pf::MAX_NV, 2 * max_tiles));
   L.S = take(sizeof(Scalars));
+  L.z = L.zt = 0;
+  if (p->solver == PF_PCG_MG) {
+    L.mg = mg_levels(p);
+    L.z = take(n * w);
+    L.zt = take(n * w);
+    for (size_t k = 0; k < L.mg.size(); ++k) {
+      MgLevelHost& l = L.mg[k];
+      if (k == 0) {
+        l.f = L.r;
+        l.e = L.z;
+        l.et = L.zt;
+        l.tlo = L.tlo;
+        l.thi = L.thi;
+      } else {
+        l.f = take((size_t)l.n() * w);
+        l.e = take((size_t)l.n() * w);
+        l.et = take((size_t)l.n() * w);
+        l.tlo = take((size_t)l.nxy());
+        l.thi = take((size_t)l.nxy());
+      }
+    }
+  }
   L.total = off;
   return L;
+}
+
+// Tiling of a plane-march launch on an nx x ny x nz grid: the deepest z
+// chunk that still gives about three tiles per resident block.
+pf::MarchCfg march_cfg(int nx, int ny, int nz, int resident, bool even_tz, int word) {
+  pf::MarchCfg m{};
+  const int v = 16 / word;
+  m.vx = nx % v == 0 ? v : 1;
+  const int bx = pf::MTX * m.vx;
+  m.tiles_x = (nx + bx - 1) / bx;
+  m.tiles_y = (ny + pf::MTY - 1) / pf::MTY;
+  const long long cols = (long long)m.tiles_x * m.tiles_y;
+  m.tz = even_tz ? 2 : 1;
+  for (int tz : {32, 16, 8, 4, 2}) {
+    if (cols * ((nz + tz - 1) / tz) >= 3LL * resident) {
+      m.tz = tz;
+      break;
+    }
+  }
+  m.ntiles = cols * ((nz + m.tz - 1) / m.tz);
+  m.grid = (int)std::min<long long>(m.ntiles, std::min(pf::MAX_GRID, resident));
+  return m;
 }
 
 }  // namespace
@@ -113,7 +210,9 @@ struct pf_ctx {
   struct Rec {
     int fam;
     double bytes;
-    int iter_no;                  // CG launches: iteration number in its solve, else 0
+    int kind;                     // 0 always runs; 1 CG launch of iteration iter_no (1-based);
+                                  // 2 V-cycle number iter_no (0-based) of its solve
+    int iter_no;
     int first_bytes_alt;          // 1: cg_p, first iteration moves bytes_first
     double bytes_first;
   };
@@ -145,13 +244,26 @@ struct pf_ctx {
 
 namespace {
 
-enum Fam { F_RHS_MEAN, F_RHS, F_CG_P, F_CG_R, F_FINISH, F_SUB_MEAN, F_TDGL, F_INVDIAG, F_COUNT };
+enum Fam {
+  F_RHS_MEAN, F_RHS, F_CG_P, F_CG_R, F_FINISH, F_SUB_MEAN, F_TDGL, F_INVDIAG,
+  F_MG_PRE, F_MG_RR, F_MG_COARSE, F_MG_POST1, F_MG_POST2, F_COUNT
+};
 const char* const FAM_NAMES[F_COUNT] = {"rhs_mean", "rhs", "cg_p", "cg_r", "cg_finish", "sub_mean", "tdgl",
-                                        "invdiag"};
+                                        "invdiag", "mg_pre", "mg_rr", "mg_coarse", "mg_post1", "mg_post2"};
+
+// Multigrid families are kept per level: family id F_COUNT + level * 5 + kind.
+int mg_fam(int kind, size_t level) { return F_COUNT + (int)level * 5 + (kind - F_MG_PRE); }
 
 void prof_reset(pf_ctx* ctx) {
-  ctx->stats.assign(F_COUNT, pf_kernel_stat{});
-  for (int f = 0; f < F_COUNT; ++f) std::snprintf(ctx->stats[f].name, sizeof(ctx->stats[f].name), "%s", FAM_NAMES[f]);
+  const int total = F_COUNT + 5 * pf::MG_MAX_LEVELS;
+  ctx->stats.assign(total, pf_kernel_stat{});
+  for (int f = 0; f < total; ++f) {
+    if (f < F_COUNT)
+      std::snprintf(ctx->stats[f].name, sizeof(ctx->stats[f].name), "%s", FAM_NAMES[f]);
+    else
+      std::snprintf(ctx->stats[f].name, sizeof(ctx->stats[f].name), "%s.L%d", FAM_NAMES[F_MG_PRE + (f - F_COUNT) % 5],
+                    (f - F_COUNT) / 5);
+  }
   ctx->recs.clear();
   ctx->have_base = false;
 }
@@ -175,10 +287,10 @@ void before_launch(pf_ctx* ctx) {
 }
 
 // Call after a launch: counts it and closes its timing interval.
-void after_launch(pf_ctx* ctx, int fam, double bytes, int iter_no = 0, double bytes_first = -1.0) {
+void after_launch(pf_ctx* ctx, int fam, double bytes, int kind = 0, int iter_no = 0, double bytes_first = -1.0) {
   ctx->launches += 1;
   if (!ctx->prof) return;
-  pf_ctx::Rec r{fam, bytes, iter_no, bytes_first >= 0.0 ? 1 : 0, bytes_first};
+  pf_ctx::Rec r{fam, bytes, kind, iter_no, bytes_first >= 0.0 ? 1 : 0, bytes_first};
   ctx->recs.push_back(r);
   prof_event(ctx, ctx->recs.size());
 }
@@ -186,14 +298,16 @@ void after_launch(pf_ctx* ctx, int fam, double bytes, int iter_no = 0, double by
 // After a host wait on the stream: turn the recorded intervals into stats.
 // CG launches numbered beyond the solve's executed iteration count returned
 // at entry and are booked as idle.
-void prof_harvest(pf_ctx* ctx, int executed_iters) {
+void prof_harvest(pf_ctx* ctx, int executed_iters, int done) {
   if (!ctx->prof || !ctx->have_base) return;
   for (size_t i = 0; i < ctx->recs.size(); ++i) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]);
     const pf_ctx::Rec& r = ctx->recs[i];
     pf_kernel_stat& st = ctx->stats[r.fam];
-    if (r.iter_no > 0 && r.iter_no > executed_iters) {
+    const bool idle = (r.kind == 1 && r.iter_no > executed_iters) ||
+                      (r.kind == 2 && (r.iter_no > executed_iters || (r.iter_no == executed_iters && done)));
+    if (idle) {
       st.idle_launches += 1;
       continue;
     }
@@ -217,15 +331,72 @@ pf::Dev<T> dev_view(pf_ctx* ctx) {
   d.p0 = (T*)(ws + L.p0);
   d.p1 = (T*)(ws + L.p1);
   d.q = (T*)(ws + L.q);
+  d.z = L.z ? (T*)(ws + L.z) : nullptr;
   d.bc.tlo = (const int8_t*)(ws + L.tlo);
   d.bc.thi = (const int8_t*)(ws + L.thi);
   d.bc.vlo = (const T*)(ws + L.vlo);
   d.bc.vhi = (const T*)(ws + L.vhi);
-  const double ih2 = ctx->geo.ih2;
-  for (int k = 0; k < 9; ++k) d.tab.v[k] = k ? (T)(1.0 / ((double)k * ih2)) : (T)0;
   d.part = (double*)(ws + L.part);
   d.S = (Scalars*)(ws + L.S);
   return d;
+}
+
+template <typename T>
+pf::MgView<T> mg_view(pf_ctx* ctx, size_t k) {
+  const MgLevelHost& l = ctx->lay.mg[k];
+  pf::MgView<T> v{};
+  v.g.nx = l.nx;
+  v.g.ny = l.ny;
+  v.g.nz = l.nz;
+  v.g.periodic_z = ctx->prm.periodic_z;
+  v.g.nxy = l.nxy();
+  v.g.n = l.n();
+  v.ax = (T)l.ax;
+  v.ay = (T)l.ay;
+  v.az = (T)l.az;
+  v.fx = l.fx;
+  v.fy = l.fy;
+  v.fz = l.fz;
+  v.tlo = (const int8_t*)(ctx->ws + l.tlo);
+  v.thi = (const int8_t*)(ctx->ws + l.thi);
+  v.f = (T*)(ctx->ws + l.f);
+  v.e = (T*)(ctx->ws + l.e);
+  v.et = (T*)(ctx->ws + l.et);
+  v.mc = l.mc;
+  return v;
+}
+
+// One V-cycle z = M^-1 r (number j of its solve, for the profiler).
+template <typename T>
+void vcycle(pf_ctx* ctx, int j) {
+  const size_t nl = ctx->lay.mg.size();
+  const double w = sizeof(T);
+  pf::Scalars* S = (pf::Scalars*)(ctx->ws + ctx->lay.S);
+  double* part = (double*)(ctx->ws + ctx->lay.part);
+  for (size_t k = 0; k + 1 < nl; ++k) {
+    const pf::MgView<T> lv = mg_view<T>(ctx, k), cv = mg_view<T>(ctx, k + 1);
+    const double N = (double)lv.g.n;
+    before_launch(ctx);
+    pf::launch_mg_pre<T>(ctx->L, lv, S);
+    after_launch(ctx, mg_fam(F_MG_PRE, k), 2 * N * w, 2, j);
+    pf::launch_mg_rr<T>(ctx->L, lv, cv, S);
+    after_launch(ctx, mg_fam(F_MG_RR, k), (2 + 1.0 / (lv.fx * lv.fy * lv.fz)) * N * w, 2, j);
+  }
+  {
+    const pf::MgView<T> cv = mg_view<T>(ctx, nl - 1);
+    before_launch(ctx);
+    pf::launch_mg_coarse<T>(ctx->L, cv, ctx->singular, S);
+    after_launch(ctx, mg_fam(F_MG_COARSE, nl - 1), 2.0 * (double)cv.g.n * w, 2, j);
+  }
+  for (size_t k = nl - 1; k-- > 0;) {
+    const pf::MgView<T> lv = mg_view<T>(ctx, k), cv = mg_view<T>(ctx, k + 1);
+    const double N = (double)lv.g.n;
+    before_launch(ctx);
+    pf::launch_mg_post1<T>(ctx->L, lv, cv, S);
+    after_launch(ctx, mg_fam(F_MG_POST1, k), (3 + 1.0 / (lv.fx * lv.fy * lv.fz)) * N * w, 2, j);
+    pf::launch_mg_post2<T>(ctx->L, lv, k == 0, part, S);
+    after_launch(ctx, mg_fam(F_MG_POST2, k), 3 * N * w, 2, j);
+  }
 }
 
 void recompute_singular(pf_ctx* ctx) {
@@ -279,6 +450,8 @@ pf_status solve(pf_ctx* ctx, const T* P) {
   before_launch(ctx);
   pf::launch_rhs<T>(ctx->L, g, d, P, 0, 0);
   after_launch(ctx, F_RHS, (5 + 2 * e) * N * w);
+  const int mg = ctx->prm.solver == PF_PCG_MG;
+  if (mg) vcycle<T>(ctx, 0);
   PF_CUDA(cudaGetLastError());
   // Every issued iteration either runs or returns at entry once the device
   // flag is set, and the device sets it by iteration maxit at the latest.
@@ -289,16 +462,17 @@ pf_status solve(pf_ctx* ctx, const T* P) {
     for (int i = 0; i < batch; ++i) {
       const int it = issued + i + 1;
       before_launch(ctx);
-      pf::launch_cg_p<T>(ctx->L, g, d);
-      after_launch(ctx, F_CG_P, (6 + 2 * e) * N * w, it, (3 + 2 * e) * N * w);
-      pf::launch_cg_r<T>(ctx->L, g, d, 0, 0);
-      after_launch(ctx, F_CG_R, (3 + e) * N * w, it);
+      pf::launch_cg_p<T>(ctx->L, g, d, mg);
+      after_launch(ctx, F_CG_P, (6 + 2 * e) * N * w, 1, it, (3 + 2 * e) * N * w);
+      pf::launch_cg_r<T>(ctx->L, g, d, mg, 0, 0);
+      after_launch(ctx, F_CG_R, (3 + e) * N * w, 1, it);
+      if (mg) vcycle<T>(ctx, it);
     }
     issued += batch;
     PF_CUDA(cudaGetLastError());
     pf_status st = read_scalars(ctx);
     if (st != PF_OK) return st;
-    prof_harvest(ctx, ctx->S_host->iter);
+    prof_harvest(ctx, ctx->S_host->iter, ctx->S_host->done);
     if (ctx->S_host->done) break;
     if (issued >= maxit)
       return ctx->fail(PF_ERR_STATE, "internal: solver did not stop after %d iterations", issued);
@@ -341,10 +515,45 @@ pf_status run_steps(pf_ctx* ctx, int nsteps) {
   return PF_OK;
 }
 
+// Copy the host face masks to the device: the fine level and, for the
+// multigrid hierarchy, every coarse level (a coarse face cell is an electrode
+// where any of its fine children is).  Waits for the copies.
+pf_status upload_masks(pf_ctx* ctx) {
+  const Layout& L = ctx->lay;
+  PF_CUDA(cudaMemcpyAsync(ctx->ws + L.tlo, ctx->tlo_h.data(), ctx->tlo_h.size(), cudaMemcpyHostToDevice,
+                          ctx->stream));
+  PF_CUDA(cudaMemcpyAsync(ctx->ws + L.thi, ctx->thi_h.data(), ctx->thi_h.size(), cudaMemcpyHostToDevice,
+                          ctx->stream));
+  // masks[2k], masks[2k+1]: z_lo / z_hi masks of level k (kept alive until the copies finish)
+  std::vector<std::vector<int8_t>> masks;
+  masks.reserve(2 * L.mg.size() + 2);
+  masks.push_back(ctx->tlo_h);
+  masks.push_back(ctx->thi_h);
+  for (size_t k = 0; k + 1 < L.mg.size(); ++k) {
+    const MgLevelHost &f = L.mg[k], &c = L.mg[k + 1];
+    std::vector<int8_t> clo((size_t)c.nxy(), 0), chi((size_t)c.nxy(), 0);
+    const std::vector<int8_t>&flo = masks[2 * k], &fhi = masks[2 * k + 1];
+    for (int y = 0; y < f.ny; ++y)
+      for (int x = 0; x < f.nx; ++x) {
+        const size_t fi = (size_t)y * f.nx + x, ci = (size_t)(y / f.fy) * c.nx + x / f.fx;
+        clo[ci] = std::max(clo[ci], flo[fi]);
+        chi[ci] = std::max(chi[ci], fhi[fi]);
+      }
+    masks.push_back(std::move(clo));
+    masks.push_back(std::move(chi));
+    PF_CUDA(cudaMemcpyAsync(ctx->ws + c.tlo, masks[2 * k + 2].data(), (size_t)c.nxy(), cudaMemcpyHostToDevice,
+                            ctx->stream));
+    PF_CUDA(cudaMemcpyAsync(ctx->ws + c.thi, masks[2 * k + 3].data(), (size_t)c.nxy(), cudaMemcpyHostToDevice,
+                            ctx->stream));
+  }
+  PF_CUDA(cudaStreamSynchronize(ctx->stream));
+  return PF_OK;
+}
+
 pf_status finish_info(pf_ctx* ctx, int nsteps, pf_step_info* info) {
   pf_status st = read_scalars(ctx);
   if (st != PF_OK) return st;
-  prof_harvest(ctx, 0);
+  prof_harvest(ctx, 0, 1);
   const Scalars& s = *ctx->S_host;
   pf_status result = PF_OK;
   if (s.nonfinite) result = ctx->fail(PF_ERR_NONFINITE, "non-finite value in the Poisson solver scalars");
@@ -430,10 +639,24 @@ pf_status pf_create(const pf_params* params, void* cuda_stream, pf_ctx** out) {
   }
   g.tiles_z = (g.nz + g.tz - 1) / g.tz;
   g.ntiles = cols * g.tiles_z;
+  {
+    const int fp32 = params->precision == PF_FP32;
+    const int resident = ctx->nsm * pf::march_blocks_per_sm(fp32, params->has_eps);
+    ctx->L.march = march_cfg(g.nx, g.ny, g.nz, resident, false, fp32 ? 4 : 8);
+    const long long nvec = (g.n + 3) / 4;
+    ctx->L.flat_grid = (int)std::max<long long>(1, std::min<long long>((nvec + pf::FLAT_THREADS - 1) / pf::FLAT_THREADS,
+                                                                       std::min(pf::MAX_GRID, 4 * ctx->nsm)));
+  }
   ctx->L.block = dim3(pf::TX, pf::TY, 1);
   ctx->L.grid = (int)std::min<long long>(g.ntiles, std::min(pf::MAX_GRID, 8 * ctx->nsm));
   ctx->L.stream = ctx->stream;
   ctx->lay = layout_of(params);
+  if (!ctx->lay.mg.empty()) {
+    const int rmg = ctx->nsm * (params->precision == PF_FP32 ? pf::mg_blocks_per_sm<float>()
+                                                             : pf::mg_blocks_per_sm<double>());
+    for (MgLevelHost& l : ctx->lay.mg)
+      l.mc = march_cfg(l.nx, l.ny, l.nz, rmg, l.fz == 2, params->precision == PF_FP32 ? 4 : 8);
+  }
   ctx->tlo_h.assign((size_t)g.nxy, 0);
   ctx->thi_h.assign((size_t)g.nxy, 0);
   recompute_singular(ctx);
@@ -467,7 +690,8 @@ pf_status pf_bind(pf_ctx* ctx, void* P, void* phi, const void* eps, void* worksp
   std::fill(ctx->thi_h.begin(), ctx->thi_h.end(), 0);
   recompute_singular(ctx);
   PF_CUDA(cudaMemsetAsync(ctx->ws + L.S, 0, sizeof(Scalars), ctx->stream));
-  PF_CUDA(cudaStreamSynchronize(ctx->stream));
+  pf_status ms = upload_masks(ctx);
+  if (ms != PF_OK) return ms;
   ctx->bound = true;
   return PF_OK;
 }
@@ -485,9 +709,7 @@ pf_status pf_set_bc(pf_ctx* ctx, int32_t face, const int8_t* type_xy, const doub
     for (size_t i = 0; i < nxy; ++i)
       if (!std::isfinite(volts_xy[i])) return ctx->fail(PF_ERR_ARG, "volts_xy[%zu] is not finite", i);
   const Layout& L = ctx->lay;
-  char* tdst = ctx->ws + (face == PF_ZLO ? L.tlo : L.thi);
   char* vdst = ctx->ws + (face == PF_ZLO ? L.vlo : L.vhi);
-  PF_CUDA(cudaMemcpyAsync(tdst, type_xy, nxy, cudaMemcpyHostToDevice, ctx->stream));
   if (ctx->prm.precision == PF_FP32) {
     std::vector<float> v(nxy, 0.f);
     if (volts_xy)
@@ -504,7 +726,7 @@ pf_status pf_set_bc(pf_ctx* ctx, int32_t face, const int8_t* type_xy, const doub
   std::memcpy(h.data(), type_xy, nxy);
   recompute_singular(ctx);
   ctx->invd_dirty = true;
-  return PF_OK;
+  return upload_masks(ctx);
 }
 
 pf_status pf_step(pf_ctx* ctx, int32_t nsteps, pf_step_info* info) {

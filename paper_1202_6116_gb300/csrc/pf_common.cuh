@@ -7,10 +7,25 @@
 
 namespace pf {
 
-// Tile of one thread block: TX x TY columns of TZ cells (x fastest).
+// Tile of one thread block in the simple per-cell kernels: TX x TY columns of
+// tz cells (x fastest).
 constexpr int TX = 32;
 constexpr int TY = 8;
 constexpr int NTHREADS = TX * TY;
+// Threads of a plane-march block (MTX x MTY, each owning one 16-byte vector
+// of cells in x) and block size of the flat kernels.
+constexpr int MTX = 16;
+constexpr int MTY = 16;
+constexpr int FLAT_THREADS = 256;
+
+// Tiling of a plane-march launch: tiles of (MTX * vx) x MTY columns times tz
+// planes; vx = cells per thread (16 bytes, or 1 when nx is not a multiple).
+struct MarchCfg {
+  int tiles_x, tiles_y, tz;
+  long long ntiles;
+  int grid;
+  int vx;
+};
 
 struct Geo {
   int nx, ny, nz;
@@ -31,12 +46,36 @@ struct Bc {
   const T* vhi;
 };
 
-// Inverse Jacobi diagonal when eps = 1: the diagonal is (number of interior
-// faces + 2 * number of Dirichlet faces) / dx^2, an integer 3..8 times ih2.
+// 16-byte vector type of a field element type.
 template <typename T>
-struct InvDiagTable {
-  T v[9];
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
 };
+template <>
+struct Vec16<double> {
+  using type = double2;
+};
+
+// 1/diag(A) at column xy of plane z when eps = 1.  The diagonal is
+// (interior faces + 2 x electrode faces)/dx^2: 6/dx^2 away from the z faces.
+// Every kernel forms it through this one expression, so z = r/diag agrees
+// bit for bit between kernels.
+template <typename T>
+__device__ __forceinline__ T inv_diag_unit(const Geo& g, const Bc<T>& bc, long long xy, int z, T inv6) {
+  if (g.periodic_z || (z > 0 && z < g.nz - 1)) return inv6;
+  const int k = 4 + (z > 0 ? 1 : 2 * (int)bc.tlo[xy]) + (z < g.nz - 1 ? 1 : 2 * (int)bc.thi[xy]);
+  return T(1) / (T(k) * T(g.ih2));
+}
+
+// Same, addressed by the linear cell index e.
+template <typename T>
+__device__ __forceinline__ T inv_flat(const Geo& g, const Bc<T>& bc, long long e, T inv6) {
+  if (g.periodic_z || (e >= g.nxy && e < g.n - g.nxy)) return inv6;
+  const int z = e < g.nxy ? 0 : g.nz - 1;
+  return inv_diag_unit(g, bc, e - (long long)z * g.nxy, z, inv6);
+}
 
 // Solver state in device memory (inside the caller's workspace).
 struct Scalars {
@@ -63,7 +102,9 @@ struct Scalars {
   int last_iters;
   unsigned ticket;  // last-block counter of the reduction kernels
   int nonfinite;
-  int pad[4];
+  unsigned long long sched_next;   // dynamic tile scheduler: next tile
+  unsigned sched_done;             // blocks that ran out of tiles
+  int pad;
 };
 
 // ---------------------------------------------------------------- reductions
@@ -116,9 +157,9 @@ struct Acc<float> {
 // block is the last one of the grid to finish (the classic threadfence
 // reduction: no block ever waits for another).  Must be called by every
 // thread of the block.
-template <int NV>
+template <int NV, int NT = NTHREADS>
 __device__ __forceinline__ bool publish_partials(double (&v)[NV], double* part, unsigned* ticket) {
-  __shared__ double sm[NV][NTHREADS / 32];
+  __shared__ double sm[NV][NT / 32];
   __shared__ bool last;
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int lane = tid & 31, wid = tid >> 5;
@@ -132,7 +173,7 @@ __device__ __forceinline__ bool publish_partials(double (&v)[NV], double* part, 
   if (wid == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double x = (lane < NTHREADS / 32) ? sm[k][lane] : 0.0;
+      double x = (lane < NT / 32) ? sm[k][lane] : 0.0;
       v[k] = warp_sum(x);
     }
     if (lane == 0) {
@@ -147,17 +188,58 @@ __device__ __forceinline__ bool publish_partials(double (&v)[NV], double* part, 
   return last;
 }
 
+// Block-reduce NV values of one work tile and store them at part[t*NV + k]
+// (thread 0).  Kernels that hand out tiles dynamically reduce per tile, so the
+// final sum (over tiles, in tile order) does not depend on which block ran
+// which tile.  Must be called by every thread of the block.
+template <int NV, int NT>
+__device__ __forceinline__ void tile_partials(double (&v)[NV], double* part, long long t) {
+  __shared__ double sm[NV][NT / 32];
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  __syncthreads();                 // sm[] may still be read from the previous tile
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sm[k][wid] = v[k];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double x = (lane < NT / 32) ? sm[k][lane] : 0.0;
+      x = warp_sum(x);
+      if (lane == 0) part[t * NV + k] = x;
+    }
+  }
+}
+
+// After every block stored its tile partials: is this the last block to finish?
+template <int NT>
+__device__ __forceinline__ bool last_block(unsigned* ticket) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return last;
+}
+
 // In the last block: sum the published partials in a fixed order (so results
 // are reproducible run to run).  Result valid in thread 0.
-template <int NV>
-__device__ __forceinline__ void gather_partials(const double* part, int nblocks, double (&out)[NV]) {
-  __shared__ double sm[NV][NTHREADS / 32];
+template <int NV, int NT = NTHREADS>
+__device__ __forceinline__ void gather_partials(const double* part, long long nblocks, double (&out)[NV]) {
+  __shared__ double sm[NV][NT / 32];
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int lane = tid & 31, wid = tid >> 5;
   double acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  for (int i = tid; i < nblocks; i += NTHREADS) {
+  for (long long i = tid; i < nblocks; i += NT) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] += __ldcg(part + (long long)i * NV + k);
   }
@@ -171,7 +253,7 @@ __device__ __forceinline__ void gather_partials(const double* part, int nblocks,
   if (wid == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double x = (lane < NTHREADS / 32) ? sm[k][lane] : 0.0;
+      double x = (lane < NT / 32) ? sm[k][lane] : 0.0;
       out[k] = warp_sum(x);
     }
   }

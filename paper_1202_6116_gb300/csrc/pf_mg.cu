@@ -1,0 +1,413 @@
+// Geometric multigrid V-cycle used as the CG preconditioner z = M^-1 r.
+//
+// Cell-centred hierarchy: each level halves every dimension that is even
+// (2 x 2 x 2 cells -> 1), the operator is re-discretised on every level
+// (per-direction spacings, so semi-coarsened levels stay consistent), a
+// coarse z face is an electrode where any of its fine children is, and the
+// error equation has homogeneous boundary data.  Transfers: restriction is
+// the average of the children, prolongation is piecewise constant (its
+// scaled transpose), smoothing is weighted Jacobi (omega = 6/7) with the same
+// number of sweeps before and after, so the V-cycle is a symmetric positive
+// definite preconditioner.  The coarsest level (<= MG_MAX_COARSE cells) is
+// solved by FP64 conjugate gradients inside one thread block.
+//
+// Per level and V-cycle (nu = 2):
+//   k_mg_pre     e = two Jacobi sweeps from zero (the first sweep omega f/diag
+//                is formed on the fly, halo included)   reads f, writes e
+//   k_mg_rr      r = f - A e and its restriction to the next level's rhs,
+//                summed over 2 x 2 columns by warp shuffles and over 2 planes
+//                in registers                            reads e, f, writes f_c
+//   k_mg_post1   e' = e + P e_c, one Jacobi sweep        reads e, e_c, f, writes et
+//   k_mg_post2   one Jacobi sweep (finest level: also r.z -> beta)
+//                                                        reads et, f, writes e
+#include "pf_internal.h"
+#include "pf_march.cuh"
+
+namespace pf {
+
+constexpr int MG_D = 2;   // planes of cp.async look-ahead
+
+template <typename T>
+__device__ __forceinline__ T mg_omega() {
+  return T(6) / T(7);
+}
+
+// 1/diag of a level's operator at column xy of plane z.
+template <typename T>
+__device__ __forceinline__ T mg_inv(const MgView<T>& L, int xy, int z, T inv_int) {
+  if (L.g.periodic_z || (z > 0 && z < L.g.nz - 1)) return inv_int;
+  const int cz = (z > 0 ? 1 : 2 * (int)L.tlo[xy]) + (z < L.g.nz - 1 ? 1 : 2 * (int)L.thi[xy]);
+  return T(1) / (T(2) * L.ax + T(2) * L.ay + T(cz) * L.az);
+}
+
+template <typename T>
+__device__ __forceinline__ T mg_inv_int(const MgView<T>& L) {
+  return T(1) / (T(2) * L.ax + T(2) * L.ay + T(2) * L.az);
+}
+
+// A v at a level with per-direction coefficients ax, ay, az = 1/h^2.
+template <typename T>
+__device__ __forceinline__ T apply_aniso(const Stencil7<T>& s, int dlo, int dhi, T ax, T ay, T az) {
+  const T sx = (s.c - s.xm) + (s.c - s.xp);
+  const T sy = (s.c - s.ym) + (s.c - s.yp);
+  T sz = T(0);
+  if (s.zb >= 0) sz += s.c - s.zm;
+  else if (dlo) sz += T(2) * s.c;
+  if (s.za >= 0) sz += s.c - s.zp;
+  else if (dhi) sz += T(2) * s.c;
+  return ax * sx + ay * sy + az * sz;
+}
+
+template <typename T, int VX>
+using MgPipe1 = Pipe<T, T, MTX, MTY, VX, 1, 0, MG_D>;
+template <typename T, int VX>
+using MgPipe2 = Pipe<T, T, MTX, MTY, VX, 1, 1, MG_D>;
+template <typename T, int VX>
+using MgPipeP = Pipe<T, T, MTX, MTY, VX, 1, 1, MG_D, 1>;
+
+// ------------------------------------------------------------------ kernels
+
+template <typename T, int VX>
+__global__ void __launch_bounds__(MTX* MTY) k_mg_pre(MgView<T> L, Scalars* S) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long tile_slot;
+  if (S->done) return;
+  const T om = mg_omega<T>(), inv_int = mg_inv_int(L);
+  const T* hsrc[1] = {L.f};
+  const T* osrc[1] = {nullptr};
+  TileGeo<MTX, MTY, VX> s;
+  auto val = [&](const T (&h)[1], int xy, int z, int, int) -> T { return om * mg_inv(L, xy, z, inv_int) * h[0]; };
+  auto emit = [&](int xy, int z, const Stencil7<T>& st, const T (&h)[1], const T (&)[1]) -> T {
+    const int dlo = st.zb < 0 ? (int)L.tlo[xy] : 0;
+    const int dhi = st.za < 0 ? (int)L.thi[xy] : 0;
+    const T Ae = apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az);
+    return st.c + om * mg_inv(L, xy, z, inv_int) * (h[0] - Ae);
+  };
+  auto post = [&](int z, const T (&ov)[VX]) { store_n<T, VX>(L.e + (long long)z * L.g.nxy + s.xy, ov); };
+  const TileSched ts{&S->sched_next, &S->sched_done};
+  for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
+    s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
+    march<T, T, T, MTX, MTY, VX, 1, 0, MG_D>(L.g, s, smem, hsrc, osrc, val, emit, post);
+  }
+  sched_finish(ts);
+}
+
+// Residual and its restriction.  Children of one coarse cell: 2 planes (summed
+// in registers across consecutive planes of the march), 2 rows (tile rows 2k,
+// 2k+1 share a warp: lane ^ 16), 2 columns (inside the thread's vector, or
+// lane ^ 1 when a thread owns one cell).
+template <typename T, int VX>
+__global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Scalars* S) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long tile_slot;
+  static_assert(MTX == 16, "row pairs share a warp");
+  if (S->done) return;
+  const T* hsrc[1] = {L.e};
+  const T* osrc[1] = {L.f};
+  const T scale = T(1) / T(L.fx * L.fy * L.fz);
+  TileGeo<MTX, MTY, VX> s;
+  T racc[VX];
+#pragma unroll
+  for (int i = 0; i < VX; ++i) racc[i] = T(0);
+  auto val = [&](const T (&h)[1], int, int, int, int) -> T { return h[0]; };
+  auto emit = [&](int xy, int, const Stencil7<T>& st, const T (&)[1], const T (&o)[1]) -> T {
+    const int dlo = st.zb < 0 ? (int)L.tlo[xy] : 0;
+    const int dhi = st.za < 0 ? (int)L.thi[xy] : 0;
+    return o[0] - apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az);
+  };
+  auto post = [&](int z, const T (&rv)[VX]) {
+#pragma unroll
+    for (int i = 0; i < VX; ++i) racc[i] += rv[i];
+    if (z % L.fz != L.fz - 1) return;
+    T v[VX];
+#pragma unroll
+    for (int i = 0; i < VX; ++i) {
+      v[i] = racc[i];
+      racc[i] = T(0);
+    }
+    const unsigned m = __activemask();
+    if (L.fy == 2) {
+#pragma unroll
+      for (int i = 0; i < VX; ++i) v[i] += __shfl_xor_sync(m, v[i], 16);
+    }
+    int cnt = VX;
+    if (L.fx == 2) {
+      if constexpr (VX >= 2) {
+#pragma unroll
+        for (int j = 0; j < VX / 2; ++j) v[j] = v[2 * j] + v[2 * j + 1];
+        cnt = VX / 2;
+      } else {
+        v[0] += __shfl_xor_sync(m, v[0], 1);
+      }
+    }
+    const bool lead_y = L.fy == 1 || (s.y & 1) == 0;
+    const bool lead_x = VX >= 2 || L.fx == 1 || (s.x & 1) == 0;
+    if (lead_y && lead_x) {
+      T* dst = C.f + (long long)(z / L.fz) * C.g.nxy + (long long)(s.y / L.fy) * C.g.nx + s.x / L.fx;
+      for (int j = 0; j < cnt; ++j) dst[j] = v[j] * scale;
+    }
+  };
+  const TileSched ts{&S->sched_next, &S->sched_done};
+  for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
+    s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
+    march<T, T, T, MTX, MTY, VX, 1, 1, MG_D>(L.g, s, smem, hsrc, osrc, val, emit, post);
+  }
+  sched_finish(ts);
+}
+
+// Prolongation + correction fused into the first post-smoothing sweep: the
+// stencil field is e + e_c(parent), the parents staged with the fine planes.
+template <typename T, int VX>
+__global__ void __launch_bounds__(MTX* MTY) k_mg_post1(MgView<T> L, MgView<T> C, Scalars* S) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long tile_slot;
+  if (S->done) return;
+  const T om = mg_omega<T>(), inv_int = mg_inv_int(L);
+  const T* hsrc[1] = {L.e};
+  const T* osrc[1] = {L.f};
+  const ParentSrc<T> par{C.e, L.fx, L.fy, L.fz, C.g.nx, C.g.nxy};
+  TileGeo<MTX, MTY, VX> s;
+  auto val = [&](const T (&h)[1], int, int, int, int, T parent) -> T { return h[0] + parent; };
+  auto emit = [&](int xy, int z, const Stencil7<T>& st, const T (&)[1], const T (&o)[1]) -> T {
+    const int dlo = st.zb < 0 ? (int)L.tlo[xy] : 0;
+    const int dhi = st.za < 0 ? (int)L.thi[xy] : 0;
+    const T Ae = apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az);
+    return st.c + om * mg_inv(L, xy, z, inv_int) * (o[0] - Ae);
+  };
+  auto post = [&](int z, const T (&ov)[VX]) { store_n<T, VX>(L.et + (long long)z * L.g.nxy + s.xy, ov); };
+  const TileSched ts{&S->sched_next, &S->sched_done};
+  for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
+    s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
+    march<T, T, T, MTX, MTY, VX, 1, 1, MG_D, 1>(L.g, s, smem, hsrc, osrc, val, emit, post, par);
+  }
+  sched_finish(ts);
+}
+
+// Last post-smoothing sweep.  On the finest level (LAST) it also forms
+// r.z (f = r, e = z): the last block sets beta = (r.z)_new / (r.z)_old.
+template <typename T, bool LAST, int VX>
+__global__ void __launch_bounds__(MTX* MTY) k_mg_post2(MgView<T> L, double* part, Scalars* S) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long tile_slot;
+  if (S->done) return;
+  const T om = mg_omega<T>(), inv_int = mg_inv_int(L);
+  const T* hsrc[1] = {L.et};
+  const T* osrc[1] = {L.f};
+  Acc<T> arz;
+  TileGeo<MTX, MTY, VX> s;
+  auto val = [&](const T (&h)[1], int, int, int, int) -> T { return h[0]; };
+  auto emit = [&](int xy, int z, const Stencil7<T>& st, const T (&)[1], const T (&o)[1]) -> T {
+    const int dlo = st.zb < 0 ? (int)L.tlo[xy] : 0;
+    const int dhi = st.za < 0 ? (int)L.thi[xy] : 0;
+    const T Ae = apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az);
+    const T e = st.c + om * mg_inv(L, xy, z, inv_int) * (o[0] - Ae);
+    if (LAST) arz.add(o[0], e);
+    return e;
+  };
+  auto post = [&](int z, const T (&ov)[VX]) { store_n<T, VX>(L.e + (long long)z * L.g.nxy + s.xy, ov); };
+  const TileSched ts{&S->sched_next, &S->sched_done};
+  for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
+    s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
+    arz = Acc<T>();
+    march<T, T, T, MTX, MTY, VX, 1, 1, MG_D>(L.g, s, smem, hsrc, osrc, val, emit, post);
+    if (LAST) {
+      double v[1] = {arz.value()};
+      tile_partials<1, MTX * MTY>(v, part, t);
+    }
+  }
+  sched_finish(ts);
+  if (!LAST) return;
+  if (last_block<MTX * MTY>(&S->ticket)) {
+    double out[1];
+    gather_partials<1, MTX * MTY>(part, L.mc.ntiles, out);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      const double rz = out[0];
+      if (!isfinite(rz)) {
+        S->nonfinite = 1;
+        S->status = 3;
+        S->pending = 0;
+        S->done = 1;
+      } else {
+        if (!S->first) S->beta = rz / S->rz;
+        S->rz = rz;
+      }
+      S->ticket = 0;
+    }
+  }
+}
+
+// ------------------------------------------------------ coarsest-level solve
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();                 // red[] may still be read from the previous call
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];   // same order in every thread
+  return s;
+}
+
+// Conjugate gradients on the coarsest level, FP64, one block, one cell per
+// thread (n <= MG_MAX_COARSE), to a relative residual of 1e-12.  With no
+// electrode the level is singular: the right-hand side and the solution are
+// projected to zero mean.
+template <typename T>
+__global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_coarse(MgView<T> C, int singular, Scalars* S) {
+  __shared__ double ps[MG_MAX_COARSE];
+  __shared__ double red[32];
+  if (S->done) return;
+  const int n = (int)C.g.n, tid = threadIdx.x;
+  const bool on = tid < n;
+  int x = 0, y = 0, z = 0;
+  if (on) {
+    x = tid % C.g.nx;
+    y = (tid / C.g.nx) % C.g.ny;
+    z = tid / (int)C.g.nxy;
+  }
+  const int xm = (x == 0 ? C.g.nx - 1 : x - 1) + (tid - x), xp = (x == C.g.nx - 1 ? 0 : x + 1) + (tid - x);
+  const int rowo = z * (int)C.g.nxy;
+  const int ym = rowo + (y == 0 ? C.g.ny - 1 : y - 1) * C.g.nx + x;
+  const int yp = rowo + (y == C.g.ny - 1 ? 0 : y + 1) * C.g.nx + x;
+  const int zb = z > 0 ? z - 1 : (C.g.periodic_z ? C.g.nz - 1 : -1);
+  const int za = z < C.g.nz - 1 ? z + 1 : (C.g.periodic_z ? 0 : -1);
+  const int zm = zb >= 0 ? zb * (int)C.g.nxy + y * C.g.nx + x : -1;
+  const int zp = za >= 0 ? za * (int)C.g.nxy + y * C.g.nx + x : -1;
+  const int xy = y * C.g.nx + x;
+  const double ax = C.ax, ay = C.ay, az = C.az;
+  const int dlo = (on && zb < 0) ? (int)C.tlo[xy] : 0;
+  const int dhi = (on && za < 0) ? (int)C.thi[xy] : 0;
+  auto apply = [&](const double* v) -> double {
+    const double c = v[tid];
+    double sz = 0.0;
+    if (zm >= 0) sz += c - v[zm];
+    else if (dlo) sz += 2.0 * c;
+    if (zp >= 0) sz += c - v[zp];
+    else if (dhi) sz += 2.0 * c;
+    return ax * ((c - v[xm]) + (c - v[xp])) + ay * ((c - v[ym]) + (c - v[yp])) + az * sz;
+  };
+  double b = on ? (double)C.f[tid] : 0.0;
+  if (singular) b -= block_sum(b, red) / n;
+  double xv = 0.0, r = b;
+  double rr = block_sum(r * r, red);
+  const double bb = rr;
+  if (bb > 0.0) {
+    double p = r;
+    for (int it = 0; it < 4 * n + 20; ++it) {
+      if (on) ps[tid] = p;
+      __syncthreads();
+      const double q = on ? apply(ps) : 0.0;
+      const double pq = block_sum(p * q, red);
+      if (!(pq > 0.0)) break;
+      const double a = rr / pq;
+      xv += a * p;
+      r -= a * q;
+      const double rrn = block_sum(r * r, red);
+      if (rrn <= 1e-24 * bb) break;
+      p = r + (rrn / rr) * p;
+      rr = rrn;
+    }
+  }
+  if (singular) xv -= block_sum(on ? xv : 0.0, red) / n;
+  if (on) C.e[tid] = (T)xv;
+}
+
+// ---------------------------------------------------------------- launchers
+
+template <typename K>
+static void smem_once(K kernel, size_t bytes, bool& flag) {
+  if (!flag) {
+    allow_smem(kernel, bytes);
+    flag = true;
+  }
+}
+
+template <typename T, int VX>
+static void pre_v(const LaunchCfg& L, const MgView<T>& lv, Scalars* S) {
+  static bool f = false;
+  smem_once(k_mg_pre<T, VX>, MgPipe1<T, VX>::bytes(), f);
+  k_mg_pre<T, VX><<<lv.mc.grid, dim3(MTX, MTY), MgPipe1<T, VX>::bytes(), L.stream>>>(lv, S);
+}
+template <typename T, int VX>
+static void rr_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
+  static bool f = false;
+  smem_once(k_mg_rr<T, VX>, MgPipe2<T, VX>::bytes(), f);
+  k_mg_rr<T, VX><<<lv.mc.grid, dim3(MTX, MTY), MgPipe2<T, VX>::bytes(), L.stream>>>(lv, cv, S);
+}
+template <typename T, int VX>
+static void post1_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
+  static bool f = false;
+  smem_once(k_mg_post1<T, VX>, MgPipeP<T, VX>::bytes(), f);
+  k_mg_post1<T, VX><<<lv.mc.grid, dim3(MTX, MTY), MgPipeP<T, VX>::bytes(), L.stream>>>(lv, cv, S);
+}
+template <typename T, bool LAST, int VX>
+static void post2_v(const LaunchCfg& L, const MgView<T>& lv, double* part, Scalars* S) {
+  static bool f = false;
+  smem_once(k_mg_post2<T, LAST, VX>, MgPipe2<T, VX>::bytes(), f);
+  k_mg_post2<T, LAST, VX><<<lv.mc.grid, dim3(MTX, MTY), MgPipe2<T, VX>::bytes(), L.stream>>>(lv, part, S);
+}
+
+constexpr int vec_of(size_t bytes) { return (int)(16 / bytes); }
+
+template <typename T>
+void launch_mg_pre(const LaunchCfg& L, const MgView<T>& lv, Scalars* S) {
+  if (lv.mc.vx > 1) pre_v<T, vec_of(sizeof(T))>(L, lv, S);
+  else pre_v<T, 1>(L, lv, S);
+}
+
+template <typename T>
+void launch_mg_rr(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
+  if (lv.mc.vx > 1) rr_v<T, vec_of(sizeof(T))>(L, lv, cv, S);
+  else rr_v<T, 1>(L, lv, cv, S);
+}
+
+template <typename T>
+void launch_mg_coarse(const LaunchCfg& L, const MgView<T>& cv, int singular, Scalars* S) {
+  const int threads = ((int)cv.g.n + 31) / 32 * 32;
+  k_mg_coarse<T><<<1, threads, 0, L.stream>>>(cv, singular, S);
+}
+
+template <typename T>
+void launch_mg_post1(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
+  if (lv.mc.vx > 1) post1_v<T, vec_of(sizeof(T))>(L, lv, cv, S);
+  else post1_v<T, 1>(L, lv, cv, S);
+}
+
+template <typename T>
+void launch_mg_post2(const LaunchCfg& L, const MgView<T>& lv, int last, double* part, Scalars* S) {
+  constexpr int V = vec_of(sizeof(T));
+  if (last) {
+    if (lv.mc.vx > 1) post2_v<T, true, V>(L, lv, part, S);
+    else post2_v<T, true, 1>(L, lv, part, S);
+  } else {
+    if (lv.mc.vx > 1) post2_v<T, false, V>(L, lv, part, S);
+    else post2_v<T, false, 1>(L, lv, part, S);
+  }
+}
+
+template <typename T>
+int mg_blocks_per_sm() {
+  constexpr int V = vec_of(sizeof(T));
+  allow_smem(k_mg_post1<T, V>, MgPipeP<T, V>::bytes());
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mg_post1<T, V>, MTX * MTY, MgPipeP<T, V>::bytes()) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+
+#define PF_MG_INSTANTIATE(T)                                                           \
+  template void launch_mg_pre<T>(const LaunchCfg&, const MgView<T>&, Scalars*);                  \
+  template void launch_mg_rr<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*); \
+  template void launch_mg_coarse<T>(const LaunchCfg&, const MgView<T>&, int, Scalars*);          \
+  template void launch_mg_post1<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*); \
+  template void launch_mg_post2<T>(const LaunchCfg&, const MgView<T>&, int, double*, Scalars*);        \
+  template int mg_blocks_per_sm<T>();
+
+PF_MG_INSTANTIATE(float)
+PF_MG_INSTANTIATE(double)
+
+}  // namespace pf

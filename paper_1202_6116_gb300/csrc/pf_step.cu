@@ -1,0 +1,294 @@
+// Once-per-step kernels on the plane march: the Poisson right-hand side with
+// the warm-start residual, and the forward-Euler TDGL update.
+//
+//   k_rhs   b = -div P + (Dirichlet terms) (Eqs. rho, Poisson; face values of P:
+//           mean inside, P_cell at an electrode, 0 at an open face), the warm
+//           start residual r0 = b - A phi (Section Numerical Performance), and
+//           ||b||^2, ||r||^2, r.z.  With MEAN = true it only sums b (the zero-mean
+//           projection of singular problems).
+//   k_tdgl  P' = P + dt L (-df/dP + g Lap P + E), E = -grad phi from face values
+//           (Eq. TDGL with Eqs. F_bulk, dF_grad/dP, F_elec; Section Time Integration).
+//
+// Both read P (3 components) and phi with their 6 neighbours; the neighbours
+// come straight from the staged planes (march_direct).  Algorithmic traffic
+// per cell: k_rhs reads 4 words and writes 1; k_tdgl reads 4 and writes 3.
+#include "pf_internal.h"
+#include "pf_march.cuh"
+
+namespace pf {
+
+constexpr int STEP_D = 2;
+
+template <typename T, bool EPS, int VX>
+using StepPipe = Pipe<T, void, MTX, MTY, VX, EPS ? 5 : 4, EPS ? 1 : 0, STEP_D>;
+
+// Face values of P along the face normal (reading of the boundary kinds).
+template <typename T, int NH>
+__device__ __forceinline__ T divergence(const Stencil7<Raw<T, NH>>& s, int dlo, int dhi) {
+  const T h = T(0.5);
+  const T pxc = s.c.v[0], pyc = s.c.v[1], pzc = s.c.v[2];
+  T div = T(0);
+  div += -(h * (pxc + s.xm.v[0]));
+  div += h * (pxc + s.xp.v[0]);
+  div += -(h * (pyc + s.ym.v[1]));
+  div += h * (pyc + s.yp.v[1]);
+  if (s.zb >= 0) div += -(h * (pzc + s.zm.v[2]));
+  else if (dlo) div += -pzc;
+  if (s.za >= 0) div += h * (pzc + s.zp.v[2]);
+  else if (dhi) div += pzc;
+  return div;
+}
+
+template <typename T, bool EPS, bool MEAN, int VX>
+__global__ void __launch_bounds__(MTX* MTY) k_rhs(Geo g, Bc<T> bc, const T* __restrict__ P, const T* __restrict__ phi,
+                                                 const T* __restrict__ eps, const T* __restrict__ invd,
+                                                 T* __restrict__ r, double* part, Scalars* S, MarchCfg mc,
+                                                 cudaGraphConditionalHandle cond, int use_cond) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long tile_slot;
+  constexpr int NH = EPS ? 5 : 4;     // Px, Py, Pz, phi (, eps)
+  constexpr int NO = EPS ? 1 : 0;     // (1/diag)
+  constexpr int NV = MEAN ? 1 : 3;
+  const T mb = MEAN ? T(0) : T(S->mean_b);
+  const T inv6 = T(1) / (T(6) * T(g.ih2));
+  const T ih = T(g.ih), ih2 = T(g.ih2);
+  const T* hsrc[NH];
+  hsrc[0] = P;
+  hsrc[1] = P + g.n;
+  hsrc[2] = P + 2 * g.n;
+  hsrc[3] = phi;
+  if constexpr (EPS) hsrc[4] = eps;
+  const T* osrc[1] = {invd};
+  Acc<T> abb, arr, arz;
+  TileGeo<MTX, MTY, VX> s;
+  auto emit = [&](int xy, int z, const Stencil7<Raw<T, NH>>& st, const T (&o)[NO > 0 ? NO : 1]) -> T {
+    const int dlo = st.zb < 0 ? (int)bc.tlo[xy] : 0;
+    const int dhi = st.za < 0 ? (int)bc.thi[xy] : 0;
+    const T ec = EPS ? st.c.v[NH - 1] : T(1);
+    T dir = T(0);
+    if (dlo) dir += T(2) * ec * bc.vlo[xy];
+    if (dhi) dir += T(2) * ec * bc.vhi[xy];
+    const T b = -divergence(st, dlo, dhi) * ih + dir * ih2 - mb;
+    if (MEAN) {
+      abb.add(b, T(1));
+      return T(0);
+    }
+    T Aphi;
+    if constexpr (EPS) {
+      Stencil7<EpsVal<T>> se;
+      auto ev = [&](const Raw<T, NH>& rw) { return EpsVal<T>{rw.v[3], rw.v[4]}; };
+      se.c = ev(st.c);
+      se.xm = ev(st.xm);
+      se.xp = ev(st.xp);
+      se.ym = ev(st.ym);
+      se.yp = ev(st.yp);
+      se.zm = ev(st.zm);
+      se.zp = ev(st.zp);
+      se.zb = st.zb;
+      se.za = st.za;
+      Aphi = apply_field<T>(se, dlo, dhi, ih2);
+    } else {
+      Aphi = apply_field<T>(pick(st, 3), dlo, dhi, ih2);
+    }
+    const T rv = b - Aphi;
+    const T inv = EPS ? o[0] : inv_diag_unit(g, bc, xy, z, inv6);
+    abb.add(b, b);
+    arr.add(rv, rv);
+    arz.add(rv, rv * inv);
+    return rv;
+  };
+  auto post = [&](int z, const T (&ov)[VX]) {
+    if (!MEAN) store_n<T, VX>(r + (long long)z * g.nxy + s.xy, ov);
+  };
+  const TileSched ts{&S->sched_next, &S->sched_done};
+  for (long long t = sched_take(ts, &tile_slot); t < mc.ntiles; t = sched_take(ts, &tile_slot)) {
+    s = tile_geo<MTX, MTY, VX>(g, t, mc);
+    abb = Acc<T>();
+    arr = Acc<T>();
+    arz = Acc<T>();
+    march_direct<T, T, MTX, MTY, VX, NH, NO, STEP_D>(g, s, smem, hsrc, osrc, emit, post);
+    double v[3] = {abb.value(), arr.value(), arz.value()};
+    double (&vv)[NV] = *reinterpret_cast<double(*)[NV]>(v);
+    tile_partials<NV, MTX * MTY>(vv, part, t);
+  }
+  sched_finish(ts);
+  if (!last_block<MTX * MTY>(&S->ticket)) return;
+  double out[NV];
+  gather_partials<NV, MTX * MTY>(part, mc.ntiles, out);
+  if (threadIdx.x != 0 || threadIdx.y != 0) return;
+  if (MEAN) {
+    S->mean_b = out[0] / (double)g.n;
+    S->ticket = 0;
+    return;
+  }
+  const double bb = out[0], rr = out[NV > 1 ? 1 : 0], rz = out[NV > 2 ? 2 : 0];
+  S->bb = bb;
+  S->rr = rr;
+  S->rz = rz;
+  S->iter = 0;
+  S->first = 1;
+  S->pending = 0;
+  S->status = 0;
+  S->alpha = 0.0;
+  S->beta = 0.0;
+  if (!isfinite(bb) || !isfinite(rr)) {
+    S->nonfinite = 1;
+    S->zero_x = 0;
+    S->done = 1;
+    S->last_rel = rr;
+  } else if (bb == 0.0) {
+    S->zero_x = 1;
+    S->done = 1;
+    S->last_rel = 0.0;
+  } else {
+    const double rel = sqrt(rr) / sqrt(bb);
+    S->zero_x = 0;
+    S->last_rel = rel;
+    S->done = (rel < S->rtol) ? 1 : 0;
+  }
+  S->ticket = 0;
+  if (use_cond) cudaGraphSetConditional(cond, S->done ? 0u : 1u);
+}
+
+template <typename T>
+struct Coef {
+  T a1, a11, a12, g, dtL;
+};
+
+template <typename T>
+struct P3 {
+  T x, y, z;
+};
+
+template <typename T, int VX>
+__global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __restrict__ P, T* __restrict__ Pn,
+                                                  const T* __restrict__ phi, Coef<T> k, Scalars* S, MarchCfg mc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long tile_slot;
+  const T h = T(0.5), ih = T(g.ih), ih2 = T(g.ih2);
+  const T* hsrc[4] = {P, P + g.n, P + 2 * g.n, phi};
+  const T* osrc[1] = {nullptr};
+  TileGeo<MTX, MTY, VX> s;
+  auto emit = [&](int xy, int, const Stencil7<Raw<T, 4>>& st, const T (&)[1]) -> P3<T> {
+    // E = -grad phi from face values (mean inside, V at an electrode, phi_cell at an open face)
+    const T fc = st.c.v[3];
+    T E[3];
+    E[0] = -(h * (fc + st.xp.v[3]) - h * (fc + st.xm.v[3])) * ih;
+    E[1] = -(h * (fc + st.yp.v[3]) - h * (fc + st.ym.v[3])) * ih;
+    T flo, fhi;
+    if (st.zb >= 0) flo = h * (fc + st.zm.v[3]);
+    else flo = bc.tlo[xy] ? bc.vlo[xy] : fc;
+    if (st.za >= 0) fhi = h * (fc + st.zp.v[3]);
+    else fhi = bc.thi[xy] ? bc.vhi[xy] : fc;
+    E[2] = -(fhi - flo) * ih;
+    T p[3] = {st.c.v[0], st.c.v[1], st.c.v[2]};
+    T out[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int j = (i + 1) % 3, l = (i + 2) % 3;
+      const T hi = T(2) * k.a1 * p[i] + T(4) * k.a11 * p[i] * p[i] * p[i] +
+                   T(2) * k.a12 * p[i] * (p[j] * p[j] + p[l] * p[l]);
+      T lap = T(0);
+      lap += st.xm.v[i] - p[i];
+      lap += st.xp.v[i] - p[i];
+      lap += st.ym.v[i] - p[i];
+      lap += st.yp.v[i] - p[i];
+      if (st.zb >= 0) lap += st.zm.v[i] - p[i];
+      if (st.za >= 0) lap += st.zp.v[i] - p[i];
+      lap *= ih2;
+      out[i] = p[i] + k.dtL * (-hi + k.g * lap + E[i]);
+    }
+    return P3<T>{out[0], out[1], out[2]};
+  };
+  auto post = [&](int z, const P3<T> (&ov)[VX]) {
+    const long long c = (long long)z * g.nxy + s.xy;
+    T a[VX], b[VX], d[VX];
+#pragma unroll
+    for (int i = 0; i < VX; ++i) {
+      a[i] = ov[i].x;
+      b[i] = ov[i].y;
+      d[i] = ov[i].z;
+    }
+    store_n<T, VX>(Pn + c, a);
+    store_n<T, VX>(Pn + g.n + c, b);
+    store_n<T, VX>(Pn + 2 * g.n + c, d);
+  };
+  const TileSched ts{&S->sched_next, &S->sched_done};
+  for (long long t = sched_take(ts, &tile_slot); t < mc.ntiles; t = sched_take(ts, &tile_slot)) {
+    s = tile_geo<MTX, MTY, VX>(g, t, mc);
+    march_direct<T, P3<T>, MTX, MTY, VX, 4, 0, STEP_D>(g, s, smem, hsrc, osrc, emit, post);
+  }
+  sched_finish(ts);
+}
+
+// ---------------------------------------------------------------- launchers
+
+template <typename K>
+static void smem_attr(K kernel, size_t bytes, bool& done) {
+  if (!done) {
+    allow_smem(kernel, bytes);
+    done = true;
+  }
+}
+
+template <typename T, bool EPS, bool MEAN, int VX>
+static void rhs_t(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, cudaGraphConditionalHandle cond,
+                  int use_cond) {
+  static bool f = false;
+  const size_t bytes = StepPipe<T, EPS, VX>::bytes();
+  smem_attr(k_rhs<T, EPS, MEAN, VX>, bytes, f);
+  k_rhs<T, EPS, MEAN, VX><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(
+      g, d.bc, P, d.phi, d.eps, d.invd, d.r, d.part, d.S, L.march, cond, use_cond);
+}
+
+template <typename T, bool MEAN>
+static void rhs_v(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, cudaGraphConditionalHandle cond,
+                  int use_cond) {
+  constexpr int V = 16 / sizeof(T);
+  const bool vec = L.march.vx == V;
+  if (d.eps) {
+    if (vec) rhs_t<T, true, MEAN, V>(L, g, d, P, cond, use_cond);
+    else rhs_t<T, true, MEAN, 1>(L, g, d, P, cond, use_cond);
+  } else {
+    if (vec) rhs_t<T, false, MEAN, V>(L, g, d, P, cond, use_cond);
+    else rhs_t<T, false, MEAN, 1>(L, g, d, P, cond, use_cond);
+  }
+}
+
+template <typename T>
+void launch_rhs_mean(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P) {
+  rhs_v<T, true>(L, g, d, P, 0, 0);
+}
+
+template <typename T>
+void launch_rhs(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, cudaGraphConditionalHandle cond,
+                int use_cond) {
+  rhs_v<T, false>(L, g, d, P, cond, use_cond);
+}
+
+template <typename T, int VX>
+static void tdgl_t(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, T* Pn, const Coef<T>& k) {
+  static bool f = false;
+  const size_t bytes = StepPipe<T, false, VX>::bytes();
+  smem_attr(k_tdgl<T, VX>, bytes, f);
+  k_tdgl<T, VX><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(g, d.bc, P, Pn, d.phi, k, d.S, L.march);
+}
+
+template <typename T>
+void launch_tdgl(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, T* Pn, const double* coef) {
+  const Coef<T> k{T(coef[0]), T(coef[1]), T(coef[2]), T(coef[3]), T(coef[4])};
+  constexpr int V = 16 / sizeof(T);
+  if (L.march.vx == V) tdgl_t<T, V>(L, g, d, P, Pn, k);
+  else tdgl_t<T, 1>(L, g, d, P, Pn, k);
+}
+
+#define PF_STEP_INSTANTIATE(T)                                                                              \
+  template void launch_rhs_mean<T>(const LaunchCfg&, const Geo&, const Dev<T>&, const T*);                  \
+  template void launch_rhs<T>(const LaunchCfg&, const Geo&, const Dev<T>&, const T*,                        \
+                              cudaGraphConditionalHandle, int);                                             \
+  template void launch_tdgl<T>(const LaunchCfg&, const Geo&, const Dev<T>&, const T*, T*, const double*);
+
+PF_STEP_INSTANTIATE(float)
+PF_STEP_INSTANTIATE(double)
+
+}  // namespace pf

@@ -67,7 +67,7 @@ class Workload:
     dt: float = 0.01
     steps: int = 1
     rtol: float = 1e-12
-    maxit: int = 100000
+    maxit: int = 20000
     precision: str = "fp64"              # "fp64" or "fp32"
     solver: str = "pcg"                  # "pcg" (Jacobi-PCG) or "mg" (multigrid-PCG)
     periodic_z: bool = False
@@ -178,7 +178,7 @@ def film_tip_fp32(nx=1024, ny=1024, nz=128, steps=1000, seed=2, v=3.0) -> Worklo
     P0 = stripe_film(nx, ny, nz, seed)
     tl, vl, th, vh = tip_electrode(nx, ny, v)
     return Workload("fp32_tip_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, P0, tl, vl, th, vh,
-                    dt=0.005, steps=steps, rtol=1e-7, precision="fp32", solver="mg", seed=seed)
+                    dt=0.005, steps=steps, rtol=1e-7, maxit=500, precision="fp32", solver="mg", seed=seed)
 
 
 def film_adjoint_fp64(nx=128, ny=128, nz=32, steps=500, seed=3, v=2.0) -> Workload:

@@ -187,3 +187,67 @@ def test_fp32_tip_electrode_vs_fp64_oracle():
     assert st == pf.PF_OK
     assert relerr(P, Po) <= FP32_TOL
     assert abs(switched_fraction(P) - switched_fraction(Po)) <= 1e-3
+
+
+# ---------------------------------------------------- multigrid-preconditioned CG
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (48, 40, 8), (64, 32, 6)])
+def test_mg_fp64_matches_oracle(shape):
+    """MG-PCG (FP64) on grids with full, ragged-tile and semi-coarsened
+    hierarchies: the potential solves the same linear system as the oracle's
+    Jacobi-PCG, so both agree to the solver tolerance."""
+    nx, ny, nz = shape
+    w = mixed_workload(nx, ny, nz, 21, steps=5, rtol=1e-13).with_(solver="mg", maxit=300)
+    Po, phio, _, _ = oracle_run(w, rtol=1e-13)
+    P, phi, st, info = gpu_run(w)
+    assert st == pf.PF_OK
+    assert relerr(P, Po) <= FP64_TOL
+    assert relerr(phi, phio) <= FP64_TOL
+    assert info["total_iters"] <= 5 * 40
+
+
+def test_mg_fp64_grounded_film_200_steps(grounded_32):
+    w, (Po, phio, _, _), (Pt, phit, _, _) = grounded_32
+    P, phi, st, info = gpu_run(w.with_(solver="mg", maxit=300))
+    assert st == pf.PF_OK
+    assert relerr(P, Pt) <= FP64_TOL and relerr(phi, phit) <= FP64_TOL
+    assert info["total_iters"] < 200 * 25
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_mg_fp64_singular(periodic):
+    nx, ny, nz = 32, 16, 8
+    z8 = np.zeros((ny, nx), np.int8)
+    zv = np.zeros((ny, nx))
+    w = W.Workload("singular", nx, ny, nz, W.random_film(nx, ny, nz, 6, -0.5, 0.5), z8, zv, z8, zv,
+                   periodic_z=periodic, steps=4, rtol=1e-12, solver="mg", maxit=300)
+    Po, phio, _, _ = oracle_run(w, rtol=1e-13)
+    P, phi, st, _ = gpu_run(w)
+    assert st == pf.PF_OK
+    assert abs(phi.mean()) < 1e-12
+    assert relerr(P, Po) <= FP64_TOL and relerr(phi, phio) <= 1e-9
+
+
+@pytest.mark.parametrize("maker", ["tip", "strips"])
+def test_mg_fp32_vs_fp64_oracle(maker):
+    """FP32 MG-PCG on the shrunk tip-electrode (rtol 1e-7) and strip-electrode
+    (rtol 1e-8) films against the FP64 oracle."""
+    if maker == "tip":
+        w = W.film_tip_fp32(64, 64, 16, steps=40).with_(maxit=300)
+    else:
+        w = W.film_strip_fp32(64, 64, 16, steps=60).with_(solver="mg", maxit=300)
+    Po, phio, _, _ = oracle_run(w.with_(precision="fp64"), rtol=1e-12)
+    P, phi, st, info = gpu_run(w)
+    assert st == pf.PF_OK
+    assert relerr(P, Po) <= FP32_TOL
+    assert abs(switched_fraction(P) - switched_fraction(Po)) <= 1e-3
+    assert info["total_iters"] <= w.steps * 20
+
+
+def test_mg_rejects_grids_it_cannot_coarsen():
+    from paper_1202_6116_gb300.film import make_params
+    w = mixed_workload(45, 38, 13, 1).with_(solver="mg")
+    p = make_params(w)
+    assert pf.pf_workspace_bytes(p) == 0
+    with pytest.raises(pf.PfError):
+        pf.pf_create(p, None)
