@@ -167,6 +167,36 @@ pf_status pf_profile_enable(pf_ctx* ctx, int32_t enable);
  * exist (may exceed max), or -1 on a NULL context. */
 int32_t pf_profile_read(const pf_ctx* ctx, pf_kernel_stat* out, int32_t max);
 
+/* Size of the device array behind pf_solve_potential_noalloc. */
+#define PF_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* The Poisson solve of pf_solve_potential for callers that cannot allocate
+ * device memory (code running inside CUDA-graph capture or replay, real-time
+ * loops that must not touch an allocator, processes with a fixed memory
+ * pool).  The paper has no counterpart: it is a deployment variant.
+ *   - No context and no workspace: every intermediate vector lives in one
+ *     file-scope __device__ array of PF_NOALLOC_SCRATCH_BYTES (32 MiB) that
+ *     every GPU loading the library keeps until the process exits; the call
+ *     itself allocates nothing (no cudaMalloc/cudaFree, no allocating library
+ *     routine).  Grids that need more scratch than the array holds (about
+ *     800k cells in FP64, 1.6M in FP32) are rejected with PF_ERR_ARG.
+ *   - params as for pf_create, restricted to solver = PF_PCG_JACOBI and
+ *     has_eps = 0.  P (3N, input) and phi (N: initial guess in, potential out)
+ *     are device pointers of the current device, 16-byte aligned, in the
+ *     precision of params.  type_lo/type_hi (nx*ny int8, PF_NEUMANN or
+ *     PF_DIRICHLET) and volt_lo/volt_hi (nx*ny double) are host arrays as in
+ *     pf_set_bc; NULL means open face / 0 V.
+ *   - Blocks until the solve is done; info as for pf_solve_potential.  On
+ *     failure pf_last_error(NULL) holds the message.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call on a device shares the array: calls that overlap on the GPU
+ *     (other streams, other host threads) race.  The array keeps the last
+ *     call's contents; each call rewrites what it reads. */
+pf_status pf_solve_potential_noalloc(const pf_params* params, void* cuda_stream, const void* P, void* phi,
+                                     const int8_t* type_lo, const double* volt_lo, const int8_t* type_hi,
+                                     const double* volt_hi, pf_step_info* info);
+
 /* Release the context (not the bound buffers).  Safe on NULL. */
 pf_status pf_destroy(pf_ctx* ctx);
 

@@ -25,7 +25,9 @@ using pf::Scalars;
 
 namespace {
 
-thread_local std::string g_create_error;
+// Message of the last failure without a context (pf_create, the
+// allocation-free solve): a fixed buffer, so recording it never allocates.
+thread_local char g_create_error[512];
 
 constexpr size_t ALIGN = 256;
 
@@ -158,29 +160,14 @@ Layout layout_of(const pf_params* p) {
   return L;
 }
 
-// Tiling of a plane-march launch on an nx x ny x nz grid: the deepest z
-// chunk that still gives about three tiles per resident block.
-pf::MarchCfg march_cfg(int nx, int ny, int nz, int resident, bool even_tz, int word) {
-  pf::MarchCfg m{};
-  const int v = 16 / word;
-  m.vx = nx % v == 0 ? v : 1;
-  const int bx = pf::MTX * m.vx;
-  m.tiles_x = (nx + bx - 1) / bx;
-  m.tiles_y = (ny + pf::MTY - 1) / pf::MTY;
-  const long long cols = (long long)m.tiles_x * m.tiles_y;
-  m.tz = even_tz ? 2 : 1;
-  for (int tz : {32, 16, 8, 4, 2}) {
-    if (cols * ((nz + tz - 1) / tz) >= 3LL * resident) {
-      m.tz = tz;
-      break;
-    }
-  }
-  m.ntiles = cols * ((nz + m.tz - 1) / m.tz);
-  m.grid = (int)std::min<long long>(m.ntiles, std::min(pf::MAX_GRID, resident));
-  return m;
-}
-
 }  // namespace
+
+namespace pf {
+void set_global_error(const char* what, const char* detail) {
+  if (detail) std::snprintf(g_create_error, sizeof(g_create_error), "%s: %s", what, detail);
+  else std::snprintf(g_create_error, sizeof(g_create_error), "%s", what);
+}
+}  // namespace pf
 
 struct pf_ctx {
   pf_params prm;
@@ -597,12 +584,12 @@ size_t pf_workspace_bytes(const pf_params* params) {
 pf_status pf_create(const pf_params* params, void* cuda_stream, pf_ctx** out) {
   std::string why;
   if (!out) {
-    g_create_error = "out is NULL";
+    pf::set_global_error("out is NULL");
     return PF_ERR_ARG;
   }
   *out = nullptr;
   if (!params_valid(params, &why)) {
-    g_create_error = why;
+    pf::set_global_error(why.c_str());
     return PF_ERR_ARG;
   }
   pf_ctx* ctx = new pf_ctx();
@@ -612,50 +599,19 @@ pf_status pf_create(const pf_params* params, void* cuda_stream, pf_ctx** out) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->S_tmpl, 2 * sizeof(Scalars));
   if (e != cudaSuccess) {
-    g_create_error = std::string("CUDA: ") + cudaGetErrorString(e);
+    pf::set_global_error("CUDA", cudaGetErrorString(e));
     delete ctx;
     return PF_ERR_CUDA;
   }
   ctx->S_host = ctx->S_tmpl + 1;
   Geo& g = ctx->geo;
-  g.nx = params->nx;
-  g.ny = params->ny;
-  g.nz = params->nz;
-  g.periodic_z = params->periodic_z;
-  g.nxy = (long long)g.nx * g.ny;
-  g.n = g.nxy * g.nz;
-  g.ih = 1.0 / params->dx;
-  g.ih2 = g.ih * g.ih;
-  g.tiles_x = (g.nx + pf::TX - 1) / pf::TX;
-  g.tiles_y = (g.ny + pf::TY - 1) / pf::TY;
-  const long long cols = (long long)g.tiles_x * g.tiles_y;
-  const long long want = 4LL * ctx->nsm;
-  g.tz = 1;
-  for (int tz : {16, 8, 4, 2}) {
-    if (cols * ((g.nz + tz - 1) / tz) >= want) {
-      g.tz = tz;
-      break;
-    }
-  }
-  g.tiles_z = (g.nz + g.tz - 1) / g.tz;
-  g.ntiles = cols * g.tiles_z;
-  {
-    const int fp32 = params->precision == PF_FP32;
-    const int resident = ctx->nsm * pf::march_blocks_per_sm(fp32, params->has_eps);
-    ctx->L.march = march_cfg(g.nx, g.ny, g.nz, resident, false, fp32 ? 4 : 8);
-    const long long nvec = (g.n + 3) / 4;
-    ctx->L.flat_grid = (int)std::max<long long>(1, std::min<long long>((nvec + pf::FLAT_THREADS - 1) / pf::FLAT_THREADS,
-                                                                       std::min(pf::MAX_GRID, 4 * ctx->nsm)));
-  }
-  ctx->L.block = dim3(pf::TX, pf::TY, 1);
-  ctx->L.grid = (int)std::min<long long>(g.ntiles, std::min(pf::MAX_GRID, 8 * ctx->nsm));
-  ctx->L.stream = ctx->stream;
+  pf::setup_launch(params, ctx->nsm, ctx->stream, g, ctx->L);
   ctx->lay = layout_of(params);
   if (!ctx->lay.mg.empty()) {
     const int rmg = ctx->nsm * (params->precision == PF_FP32 ? pf::mg_blocks_per_sm<float>()
                                                              : pf::mg_blocks_per_sm<double>());
     for (MgLevelHost& l : ctx->lay.mg)
-      l.mc = march_cfg(l.nx, l.ny, l.nz, rmg, l.fz == 2, params->precision == PF_FP32 ? 4 : 8);
+      l.mc = pf::march_cfg(l.nx, l.ny, l.nz, rmg, l.fz == 2, params->precision == PF_FP32 ? 4 : 8);
   }
   ctx->tlo_h.assign((size_t)g.nxy, 0);
   ctx->thi_h.assign((size_t)g.nxy, 0);
@@ -801,7 +757,7 @@ pf_status pf_destroy(pf_ctx* ctx) {
 }
 
 const char* pf_last_error(const pf_ctx* ctx) {
-  if (!ctx) return g_create_error.c_str();
+  if (!ctx) return g_create_error;
   return ctx->err.c_str();
 }
 

@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
+#include "pf.h"
 #include "pf_common.cuh"
 
 namespace pf {
@@ -73,8 +76,70 @@ void launch_tdgl(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, 
 template <typename T>
 void launch_invdiag(const LaunchCfg& L, const Geo& g, const Dev<T>& d);
 
-// Resident 512-thread plane-march blocks per SM for this precision.
+// Tiling of a plane-march launch on an nx x ny x nz grid: the deepest z
+// chunk that still gives about three tiles per resident block.
+// Resident plane-march blocks (MTX x MTY threads) per SM for this precision.
 int march_blocks_per_sm(int fp32, int eps);
+
+inline MarchCfg march_cfg(int nx, int ny, int nz, int resident, bool even_tz, int word) {
+  MarchCfg m{};
+  const int v = 16 / word;
+  m.vx = nx % v == 0 ? v : 1;
+  const int bx = MTX * m.vx;
+  m.tiles_x = (nx + bx - 1) / bx;
+  m.tiles_y = (ny + MTY - 1) / MTY;
+  const long long cols = (long long)m.tiles_x * m.tiles_y;
+  m.tz = even_tz ? 2 : 1;
+  for (int tz : {32, 16, 8, 4, 2}) {
+    if (cols * ((nz + tz - 1) / tz) >= 3LL * resident) {
+      m.tz = tz;
+      break;
+    }
+  }
+  m.ntiles = cols * ((nz + m.tz - 1) / m.tz);
+  m.grid = (int)std::min<long long>(m.ntiles, std::min(MAX_GRID, resident));
+  return m;
+}
+
+// Grid geometry and launch shapes of the fine level for these parameters
+// (shared by the context-based entry points and the allocation-free solve).
+inline void setup_launch(const pf_params* p, int nsm, cudaStream_t stream, Geo& g, LaunchCfg& L) {
+  g = Geo{};
+  g.nx = p->nx;
+  g.ny = p->ny;
+  g.nz = p->nz;
+  g.periodic_z = p->periodic_z;
+  g.nxy = (long long)g.nx * g.ny;
+  g.n = g.nxy * g.nz;
+  g.ih = 1.0 / p->dx;
+  g.ih2 = g.ih * g.ih;
+  g.tiles_x = (g.nx + TX - 1) / TX;
+  g.tiles_y = (g.ny + TY - 1) / TY;
+  const long long cols = (long long)g.tiles_x * g.tiles_y;
+  g.tz = 1;
+  for (int tz : {16, 8, 4, 2}) {
+    if (cols * ((g.nz + tz - 1) / tz) >= 4LL * nsm) {
+      g.tz = tz;
+      break;
+    }
+  }
+  g.tiles_z = (g.nz + g.tz - 1) / g.tz;
+  g.ntiles = cols * g.tiles_z;
+  L = LaunchCfg{};
+  const int fp32 = p->precision == PF_FP32;
+  const int resident = nsm * march_blocks_per_sm(fp32, p->has_eps);
+  L.march = march_cfg(g.nx, g.ny, g.nz, resident, false, fp32 ? 4 : 8);
+  const long long nvec = (g.n + 3) / 4;
+  L.flat_grid = (int)std::max<long long>(
+      1, std::min<long long>((nvec + FLAT_THREADS - 1) / FLAT_THREADS, std::min(MAX_GRID, 4 * nsm)));
+  L.block = dim3(TX, TY, 1);
+  L.grid = (int)std::min<long long>(g.ntiles, std::min(MAX_GRID, 8 * nsm));
+  L.stream = stream;
+}
+
+// Record the message returned by pf_last_error(NULL) (fixed buffer, no allocation).
+void set_global_error(const char* what, const char* detail = nullptr);
+
 
 // Multigrid V-cycle pieces (pf_mg.cu).
 template <typename T>

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_CUDA", 3: "PF_ERR_NOCONV
 # Every symbol the header declares.
 EXPORTS = ["pf_workspace_bytes", "pf_create", "pf_bind", "pf_set_bc", "pf_step", "pf_step_host",
            "pf_solve_potential", "pf_adjoint_step", "pf_profile_enable", "pf_profile_read", "pf_destroy",
-           "pf_last_error"]
+           "pf_last_error", "pf_solve_potential_noalloc"]
 
 
 class pf_params(C.Structure):
@@ -90,6 +90,9 @@ def lib():
         L.pf_profile_enable.argtypes = [vp, i32]
         L.pf_profile_read.restype = i32
         L.pf_profile_read.argtypes = [vp, vp, i32]
+        L.pf_solve_potential_noalloc.restype = i32
+        L.pf_solve_potential_noalloc.argtypes = [C.POINTER(pf_params), vp, vp, vp, vp, vp, vp, vp,
+                                                 C.POINTER(pf_step_info)]
         L.pf_destroy.restype = i32
         L.pf_destroy.argtypes = [vp]
         L.pf_last_error.restype = C.c_char_p
@@ -178,6 +181,17 @@ def pf_profile_read(ctx):
     lib().pf_profile_read(ctx, C.cast(arr, C.c_void_p), n)
     return [dict(name=a.name.decode(), launches=a.launches, idle_launches=a.idle_launches,
                  total_ms=a.total_ms, bytes=a.bytes) for a in arr[:n]]
+
+
+def pf_solve_potential_noalloc(params: pf_params, stream, P, phi, type_lo=None, volt_lo=None, type_hi=None,
+                               volt_hi=None, ok=(PF_OK,)):
+    """Poisson solve with no allocation (device P, phi; host int8 masks and
+    float64 volts).  Returns (status, info)."""
+    info = pf_step_info()
+    st = lib().pf_solve_potential_noalloc(C.byref(params), _addr(stream), _addr(P), _addr(phi), _addr(type_lo),
+                                          _addr(volt_lo), _addr(type_hi), _addr(volt_hi), C.byref(info))
+    check(st, None, ok)
+    return st, info
 
 
 def pf_destroy(ctx):
