@@ -29,17 +29,18 @@ sys.path.insert(0, ROOT)
 METRIC = "TDGL cell-steps/s incl. Poisson solve"
 UNIT = "cell-steps/s"
 L2_BYTES = 129 * 2 ** 20
-WORKLOADS = ("strips", "tip", "grounded")
+WORKLOADS = ("tip", "strips", "grounded")
 
 
-def make_workload(name, seed_offset=0, solver=None):
+def make_workload(name, seed_offset=0, solver=None, size=None):
     from paper_1202_6116_gb300 import workloads as W
+    dims = {} if size is None else dict(zip(("nx", "ny", "nz"), size))
     if name == "strips":
-        w = W.film_strip_fp32(seed=1 + seed_offset)
+        w = W.film_strip_fp32(seed=1 + seed_offset, **dims)
     elif name == "tip":
-        w = W.film_tip_fp32(seed=2 + seed_offset)
+        w = W.film_tip_fp32(seed=2 + seed_offset, **dims)
     elif name == "grounded":
-        w = W.film_fp64_grounded(seed=0 + seed_offset)
+        w = W.film_fp64_grounded(seed=0 + seed_offset, **dims)
     else:
         raise ValueError(name)
     if solver == "mg":
@@ -50,12 +51,12 @@ def make_workload(name, seed_offset=0, solver=None):
 
 
 def sample_workload(name):
-    """Bounded CPU sample of a workload: same recipe, each dimension / 4."""
+    """Bounded CPU sample of a workload: the same recipe on a smaller film."""
     from paper_1202_6116_gb300 import workloads as W
     if name == "strips":
         return W.film_strip_fp32(64, 64, 16, seed=1), "64x64x16 film of the strip-electrode recipe"
     if name == "tip":
-        return W.film_tip_fp32(256, 256, 32, seed=2), "256x256x32 film of the tip-electrode recipe"
+        return W.film_tip_fp32(128, 128, 16, seed=2), "128x128x16 film of the tip-electrode recipe"
     return W.film_fp64_grounded(32, 32, 32, seed=0), "the full 32x32x32 grounded film"
 
 
@@ -170,7 +171,7 @@ def run_ours(args):
     B.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    w = make_workload(args.workload, seed_offset=rank, solver=args.solver)
+    w = make_workload(args.workload, seed_offset=rank, solver=args.solver, size=args.size)
     film = Film(w, device=dev)
     stream = film.stream
     flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
@@ -183,7 +184,6 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         film.step(1)
-    pf.pf_profile_enable(film.ctx, 1)
     clocks = ClockSampler(local)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -201,8 +201,6 @@ def run_ours(args):
         iters += info["total_iters"]
     barrier()
     clk = clocks.stop()
-    stats = pf.pf_profile_read(film.ctx)
-    pf.pf_profile_enable(film.ctx, 0)
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     ms_max = ms
     if world > 1:
@@ -211,12 +209,31 @@ def run_ours(args):
         ms_max = float(t.item())
     value = w.n * args.steps * world / (ms_max / 1e3)
 
+    # per-kernel device times: a second pass of the same steps with the
+    # library's CUDA-event profiler on (kept out of the headline timing)
+    prof_steps = max(1, min(args.steps, args.profile_steps))
+    pf.pf_profile_enable(film.ctx, 1)
+    barrier()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    prof_ms = 0.0
+    for k in range(prof_steps):
+        flush_buf.zero_()
+        p0.record(stream)
+        film.step(1)
+        p1.record(stream)
+        p1.synchronize()
+        prof_ms += p0.elapsed_time(p1)
+    stats = pf.pf_profile_read(film.ctx)
+    pf.pf_profile_enable(film.ctx, 0)
+
     # end to end: host-resident state, copies inside the timed region
     w_bytes = 4 if w.precision == "fp32" else 8
     tdt = torch.float32 if w.precision == "fp32" else torch.float64
     Ph = film.P.detach().to("cpu").pin_memory()
     phih = film.phi.detach().to("cpu").pin_memory()
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    film.step(1)
     barrier()
     t0 = time.perf_counter()
     pf.pf_step_host(film.ctx, Ph, phih, e2e_steps)
@@ -244,6 +261,7 @@ def run_ours(args):
                 "avg_launch_us": 1e3 * dom["total_ms"] / dom["launches"],
                 "share_of_kernel_time": round(dom["total_ms"] / total_kernel_ms, 3),
                 "step_achieved_gbs": round(sum(s["bytes"] for s in work) / (total_kernel_ms / 1e3) / 1e9, 1),
+                "profiled_steps": prof_steps, "profiled_ms_per_step": prof_ms / prof_steps,
                 "kernels": {s["name"]: {"launches": s["launches"], "idle": s["idle_launches"],
                                         "ms": round(s["total_ms"], 3),
                                         "gbs": round(s["bytes"] / (s["total_ms"] / 1e3) / 1e9, 1)}
@@ -306,7 +324,8 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 initial state, electrode masks of the workload)",
-            "config": workload_config(make_workload(args.workload, solver=args.solver), args.workload, "n/a (CPU)"),
+            "config": workload_config(make_workload(args.workload, solver=args.solver, size=args.size), args.workload,
+                                      "n/a (CPU)"),
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%s, FP64 serial oracle, %d steps after %d warm-up steps" %
@@ -320,11 +339,14 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=None)
-    ap.add_argument("--workload", choices=WORKLOADS, default="strips")
+    ap.add_argument("--workload", choices=WORKLOADS, default="tip")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--solver", choices=("pcg", "mg"), default=None,
                     help="override the workload's Poisson preconditioner (Jacobi or multigrid)")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--profile-steps", type=int, default=10)
+    ap.add_argument("--size", type=lambda v: tuple(int(x) for x in v.lower().split("x")), default=None,
+                    help="NXxNYxNZ: the workload's recipe on another grid (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -333,8 +355,8 @@ def main():
         args.warmup = 3 if args.warmup is None else args.warmup
         run_reference(args)
     else:
-        args.steps = 200 if args.steps is None else args.steps
-        args.warmup = 10 if args.warmup is None else max(3, args.warmup)
+        args.steps = 30 if args.steps is None else args.steps
+        args.warmup = 5 if args.warmup is None else max(3, args.warmup)
         run_ours(args)
 
 

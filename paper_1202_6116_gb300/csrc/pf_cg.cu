@@ -52,24 +52,25 @@ __global__ void __launch_bounds__(MTX* MTY) k_cg_p(Geo g, Bc<T> bc, const T* __r
   };
   TileGeo<MTX, MTY, VX> s;
 
-  auto val = [&](const T (&h)[NH], int xy, int z, int, int) -> F {
+  auto val = [&](const T (&h)[NH], int xy, int z, int, int, const bool bt) -> F {
     T zz;
     if constexpr (MG) {
       zz = h[0];
     } else {
       T inv;
       if constexpr (EPS) inv = h[3];
-      else inv = inv_diag_unit(g, bc, xy, z, inv6);
+      else inv = bt ? inv_diag_unit(g, bc, xy, z, inv6) : inv6;
       zz = h[0] * inv;
     }
     const T v = first ? zz : zz + beta * h[1];
     if constexpr (EPS) return F{v, h[2]};
     else return v;
   };
-  auto emit = [&](int xy, int, const Stencil7<F>& st, const T (&h)[NH], const T (&o)[1]) -> Out {
-    const int dlo = st.zb < 0 ? (int)bc.tlo[xy] : 0;
-    const int dhi = st.za < 0 ? (int)bc.thi[xy] : 0;
-    const T qv = apply_field<T>(st, dlo, dhi, ih2);
+  auto emit = [&](int xy, int, const Stencil7<F>& st, const T (&h)[NH], const T (&o)[1], const bool bt) -> Out {
+    const bool B = bt;
+    const int dlo = (B && st.zb < 0) ? (int)bc.tlo[xy] : 0;
+    const int dhi = (B && st.za < 0) ? (int)bc.thi[xy] : 0;
+    const T qv = apply_bt(st, dlo, dhi, ih2, bt);
     const T pc = field_value<T>(st.c);
     apq.add(pc, qv);
     return Out{first ? o[0] : o[0] + alpha * h[1], pc, qv};

@@ -21,8 +21,6 @@
 // z = 0 / above nz - 1 exist only for periodic z.
 #pragma once
 
-#include <type_traits>
-
 #include "pf_common.cuh"
 
 namespace pf {
@@ -242,7 +240,7 @@ struct Stager {
     return stages + (size_t)st * STAGE + (NH * HH + rw) * RS + cl;
   }
   // parent slot of vector element i (own vector or a y-halo vector)
-  __device__ __forceinline__ int pslot(int i) const { return col + i / par.fx; }
+  __device__ __forceinline__ int pslot(int i) const { return col + (i >> (par.fx - 1)); }
   // copy the parents of a vector starting at fine (x, y) of plane z into slot (rw, col)
   __device__ __forceinline__ void issue_parent_vec(int st, int rw, int x, int y, int z) const {
     const T* src = par.ec + (long long)(z / par.fz) * par.nxyc + (long long)(y / par.fy) * par.nxc + x / par.fx;
@@ -310,11 +308,16 @@ struct Raw {
 // Walk one tile, stencil field formed by val.
 //   hsrc[k]  NH raw arrays needed with halo;  osrc[k]  NO raw arrays needed at
 //            the own cells only (linear cell index).
-//   val(const T (&h)[NH], xy, z, col, i) -> F   stencil field at one cell from its
-//            raw values; col: 0 own vector, 1..4 left/right/top/bottom halo;
-//            i: index inside the vector (0 for the x halo).
-//   emit(xy, z, const Stencil7<F>&, const T (&h)[NH], const T (&o)[NO]) -> Out
+//   val(const T (&h)[NH], xy, z, col, i, [parent,] bt) -> F   stencil field at one
+//            cell from its raw values; col: 0 own vector, 1..4 left/right/top/
+//            bottom halo; i: index inside the vector (0 for the x halo); parent:
+//            the staged coarse parent (NP = 1 only).
+//   emit(xy, z, const Stencil7<F>&, const T (&h)[NH], const T (&o)[NO], bt) -> Out
 //            consumes one own cell and returns its outputs.
+//   bt is true on the planes next to a non-periodic z face and false
+//   elsewhere (always a constant after inlining): the functors keep their
+//   boundary handling behind it (there zb/za of the stencil say which face
+//   is open); on other planes zb = za = 0.
 //   post(z, const Out (&out)[VX])  receives the outputs of the own vector
 //            (and stores them: 16-byte stores of whole vectors).
 // smem: Pipe<...>::bytes() bytes, 16-byte aligned.  Every thread of the block
@@ -329,10 +332,13 @@ __device__ __forceinline__ void march(const Geo& g, const TileGeo<TXT, TYT, VX>&
   constexpr int OFF = P::OFF, RS = P::RS, HH = P::HH, NS = P::NS;
   static_assert(TXT == 16 || TXT == 32, "a warp holds one or two tile rows");
   const SG sg(g, s, reinterpret_cast<T*>(smem), hsrc, osrc, par);
-  // the stencil field at one cell; with staged parents val also gets the parent
-  auto val_at = [&](const T (&h1)[NH], int xy, int z, int colid, int i, int st, int rw, int pcl) -> F {
-    if constexpr (NP > 0) return val(h1, xy, z, colid, i, *sg.PA(st, rw, pcl));
-    else return val(h1, xy, z, colid, i);
+  // the stencil field at one cell; with staged parents val also gets the parent.
+  // bt is true on the planes next to a non-periodic z face, where boundary
+  // data matter; the march calls its (inlined) loops with the constants true
+  // and false, so each copy compiles only the code it needs.
+  auto val_at = [&](const T (&h1)[NH], int xy, int z, int colid, int i, int st, int rw, int pcl, const bool bt) -> F {
+    if constexpr (NP > 0) return val(h1, xy, z, colid, i, *sg.PA(st, rw, pcl), bt);
+    else return val(h1, xy, z, colid, i, bt);
   };
   F* pn = reinterpret_cast<F*>(smem + (size_t)NS * P::STAGE * sizeof(T));
   auto PN = [&](int b, int rw, int cl) -> F* { return pn + (b * HH + rw) * RS + cl; };
@@ -340,7 +346,7 @@ __device__ __forceinline__ void march(const Geo& g, const TileGeo<TXT, TYT, VX>&
   const bool left_in_warp = s.tx > 0;
   const bool right_in_warp = s.tx < TXT - 1 && (s.tx + 1) * VX < s.w;
 
-  auto form_vec = [&](int st, int rw, int cl, int xy, int z, int colid, F (&fv)[VX]) {
+  auto form_vec = [&](int st, int rw, int cl, int xy, int z, int colid, F (&fv)[VX], const bool bt) {
     T hv[NH][VX];
 #pragma unroll
     for (int k = 0; k < NH; ++k) load_n<T, VX>(sg.H(st, k, rw, cl), hv[k]);
@@ -349,37 +355,41 @@ __device__ __forceinline__ void march(const Geo& g, const TileGeo<TXT, TYT, VX>&
       T h1[NH];
 #pragma unroll
       for (int k = 0; k < NH; ++k) h1[k] = hv[k][i];
-      fv[i] = val_at(h1, xy + i, z, colid, i, st, rw, NP > 0 ? sg.pslot(i) : 0);
+      fv[i] = val_at(h1, xy + i, z, colid, i, st, rw, NP > 0 ? sg.pslot(i) : 0, bt);
     }
   };
   // Stencil field of plane v: own vector, plus the halo cells for in-tile planes.
-  auto form = [&](int v) {
-    const int z = sg.plane(v);
-    if (!s.act || z < 0) return;
+  auto form_t = [&](int v, int z, const bool bt) {
     const int st = v % NS, b = v % 3;
     F fv[VX];
-    form_vec(st, row, col, s.xy, z, 0, fv);
+    form_vec(st, row, col, s.xy, z, 0, fv, bt);
     store_n<F, VX>(PN(b, row, col), fv);
     if (v < 1 || v > nt) return;
     T h1[NH];
     if (s.xy_l >= 0) {
 #pragma unroll
       for (int k = 0; k < NH; ++k) h1[k] = *sg.H(st, k, row, OFF - 1);
-      *PN(b, row, OFF - 1) = val_at(h1, s.xy_l, z, 1, 0, st, row, OFF - 1);
+      *PN(b, row, OFF - 1) = val_at(h1, s.xy_l, z, 1, 0, st, row, OFF - 1, bt);
     }
     if (s.xy_r >= 0) {
 #pragma unroll
       for (int k = 0; k < NH; ++k) h1[k] = *sg.H(st, k, row, OFF + s.w);
-      *PN(b, row, OFF + s.w) = val_at(h1, s.xy_r, z, 2, 0, st, row, OFF + s.w);
+      *PN(b, row, OFF + s.w) = val_at(h1, s.xy_r, z, 2, 0, st, row, OFF + s.w, bt);
     }
     if (s.xy_t >= 0) {
-      form_vec(st, 0, col, s.xy_t, z, 3, fv);
+      form_vec(st, 0, col, s.xy_t, z, 3, fv, bt);
       store_n<F, VX>(PN(b, 0, col), fv);
     }
     if (s.xy_b >= 0) {
-      form_vec(st, s.h + 1, col, s.xy_b, z, 4, fv);
+      form_vec(st, s.h + 1, col, s.xy_b, z, 4, fv, bt);
       store_n<F, VX>(PN(b, s.h + 1, col), fv);
     }
+  };
+  auto form = [&](int v) {
+    const int z = sg.plane(v);
+    if (!s.act || z < 0) return;
+    if (z_below(g, z) < 0 || z_above(g, z) < 0) form_t(v, z, true);
+    else form_t(v, z, false);
   };
 
   for (int v = 0; v <= D; ++v) sg.issue(v);
@@ -414,31 +424,35 @@ __device__ __forceinline__ void march(const Geo& g, const TileGeo<TXT, TYT, VX>&
       const int z = s.z0 + v - 1;
       const int st = v % NS;
       T hv[NH][VX], ov[NO > 0 ? NO : 1][VX];
-      Out outv[VX];
 #pragma unroll
       for (int k = 0; k < NH; ++k) load_n<T, VX>(sg.H(st, k, row, col), hv[k]);
 #pragma unroll
       for (int k = 0; k < NO; ++k) load_n<T, VX>(sg.O(st, k), ov[k]);
+      auto emit_all = [&](const bool B) {
+        Out outv[VX];
 #pragma unroll
-      for (int i = 0; i < VX; ++i) {
-        Stencil7<F> sc;
-        sc.c = cv[i];
-        sc.xm = i == 0 ? lft : cv[i - 1];
-        sc.xp = i == VX - 1 ? rgt : cv[i + 1];
-        sc.ym = ym[i];
-        sc.yp = yp[i];
-        sc.zm = zb >= 0 ? zm[i] : F{};
-        sc.zp = za >= 0 ? zp[i] : F{};
-        sc.zb = zb;
-        sc.za = za;
-        T h1[NH], o1[NO > 0 ? NO : 1];
+        for (int i = 0; i < VX; ++i) {
+          Stencil7<F> sc;
+          sc.c = cv[i];
+          sc.xm = i == 0 ? lft : cv[i - 1];
+          sc.xp = i == VX - 1 ? rgt : cv[i + 1];
+          sc.ym = ym[i];
+          sc.yp = yp[i];
+          sc.zm = (!B || zb >= 0) ? zm[i] : F{};
+          sc.zp = (!B || za >= 0) ? zp[i] : F{};
+          sc.zb = B ? zb : 0;
+          sc.za = B ? za : 0;
+          T h1[NH], o1[NO > 0 ? NO : 1];
 #pragma unroll
-        for (int k = 0; k < NH; ++k) h1[k] = hv[k][i];
+          for (int k = 0; k < NH; ++k) h1[k] = hv[k][i];
 #pragma unroll
-        for (int k = 0; k < NO; ++k) o1[k] = ov[k][i];
-        outv[i] = emit(s.xy + i, z, sc, h1, o1);
-      }
-      post(z, outv);
+          for (int k = 0; k < NO; ++k) o1[k] = ov[k][i];
+          outv[i] = emit(s.xy + i, z, sc, h1, o1, B);
+        }
+        post(z, outv);
+      };
+      if (zb < 0 || za < 0) emit_all(true);
+      else emit_all(false);
     }
   }
   cp_wait<0>();
@@ -446,8 +460,8 @@ __device__ __forceinline__ void march(const Geo& g, const TileGeo<TXT, TYT, VX>&
 
 // Walk one tile whose stencil is the raw input itself: the neighbours are read
 // straight from the staged planes (after the plane's barrier), with no field
-// buffer.  emit(xy, z, const Stencil7<Raw<T,NH>>&, const T (&o)[NO]) -> Out;
-// post as in march.
+// buffer.  emit(xy, z, const Stencil7<Raw<T,NH>>&, const T (&o)[NO], bt) -> Out;
+// post and bt as in march.
 template <typename T, typename Out, int TXT, int TYT, int VX, int NH, int NO, int D, class Emit, class Post>
 __device__ __forceinline__ void march_direct(const Geo& g, const TileGeo<TXT, TYT, VX>& s, unsigned char* smem,
                                              const T* const (&hsrc)[NH], const T* const (&osrc)[NO > 0 ? NO : 1],
@@ -493,28 +507,32 @@ __device__ __forceinline__ void march_direct(const Geo& g, const TileGeo<TXT, TY
       T ov[NO > 0 ? NO : 1][VX];
 #pragma unroll
       for (int k = 0; k < NO; ++k) load_n<T, VX>(sg.O(st, k), ov[k]);
-      Out outv[VX];
+      auto emit_all = [&](const bool B) {
+        Out outv[VX];
 #pragma unroll
-      for (int i = 0; i < VX; ++i) {
-        Stencil7<R> sc;
+        for (int i = 0; i < VX; ++i) {
+          Stencil7<R> sc;
 #pragma unroll
-        for (int k = 0; k < NH; ++k) {
-          sc.c.v[k] = c[k][i];
-          sc.xm.v[k] = i == 0 ? lft[k] : c[k][i - 1];
-          sc.xp.v[k] = i == VX - 1 ? rgt[k] : c[k][i + 1];
-          sc.ym.v[k] = ym[k][i];
-          sc.yp.v[k] = yp[k][i];
-          sc.zm.v[k] = zb >= 0 ? zm[k][i] : T(0);
-          sc.zp.v[k] = za >= 0 ? zp[k][i] : T(0);
+          for (int k = 0; k < NH; ++k) {
+            sc.c.v[k] = c[k][i];
+            sc.xm.v[k] = i == 0 ? lft[k] : c[k][i - 1];
+            sc.xp.v[k] = i == VX - 1 ? rgt[k] : c[k][i + 1];
+            sc.ym.v[k] = ym[k][i];
+            sc.yp.v[k] = yp[k][i];
+            sc.zm.v[k] = (!B || zb >= 0) ? zm[k][i] : T(0);
+            sc.zp.v[k] = (!B || za >= 0) ? zp[k][i] : T(0);
+          }
+          sc.zb = B ? zb : 0;
+          sc.za = B ? za : 0;
+          T o1[NO > 0 ? NO : 1];
+#pragma unroll
+          for (int k = 0; k < NO; ++k) o1[k] = ov[k][i];
+          outv[i] = emit(s.xy + i, z, sc, o1, B);
         }
-        sc.zb = zb;
-        sc.za = za;
-        T o1[NO > 0 ? NO : 1];
-#pragma unroll
-        for (int k = 0; k < NO; ++k) o1[k] = ov[k][i];
-        outv[i] = emit(s.xy + i, z, sc, o1);
-      }
-      post(z, outv);
+        post(z, outv);
+      };
+      if (zb < 0 || za < 0) emit_all(true);
+      else emit_all(false);
     }
   }
   cp_wait<0>();
@@ -555,6 +573,7 @@ __device__ __forceinline__ T apply_field(const Stencil7<T>& s, int dlo, int dhi,
   return acc * ih2;
 }
 
+
 template <typename T, bool EPS>
 struct FieldOf {
   using type = T;
@@ -587,6 +606,25 @@ __device__ __forceinline__ T apply_field(const Stencil7<EpsVal<T>>& s, int dlo, 
   if (s.za >= 0) acc += hmean2(ec, s.zp.e) * (vc - s.zp.v);
   else if (dhi) acc += T(2) * ec * vc;
   return acc * ih2;
+}
+
+// Boundary-aware on the planes next to a z face (bt), plain 7-point stencil
+// elsewhere.  Same face order, so both give identical sums.
+template <typename T>
+__device__ __forceinline__ T apply_bt(const Stencil7<T>& s, int dlo, int dhi, T ih2, const bool bt) {
+  if (bt) return apply_field(s, dlo, dhi, ih2);
+  Stencil7<T> t = s;
+  t.zb = 0;
+  t.za = 0;
+  return apply_field(t, 0, 0, ih2);
+}
+template <typename T>
+__device__ __forceinline__ T apply_bt(const Stencil7<EpsVal<T>>& s, int dlo, int dhi, T ih2, const bool bt) {
+  if (bt) return apply_field(s, dlo, dhi, ih2);
+  Stencil7<EpsVal<T>> t = s;
+  t.zb = 0;
+  t.za = 0;
+  return apply_field(t, 0, 0, ih2);
 }
 
 // Set the dynamic shared-memory limit of a kernel.

@@ -45,17 +45,27 @@ __device__ __forceinline__ T mg_inv_int(const MgView<T>& L) {
   return T(1) / (T(2) * L.ax + T(2) * L.ay + T(2) * L.az);
 }
 
-// A v at a level with per-direction coefficients ax, ay, az = 1/h^2.
+// A v at a level with per-direction coefficients ax, ay, az = 1/h^2; the z
+// face logic only on the planes next to a z face (bt).
 template <typename T>
-__device__ __forceinline__ T apply_aniso(const Stencil7<T>& s, int dlo, int dhi, T ax, T ay, T az) {
+__device__ __forceinline__ T apply_aniso(const Stencil7<T>& s, int dlo, int dhi, T ax, T ay, T az, const bool bt) {
   const T sx = (s.c - s.xm) + (s.c - s.xp);
   const T sy = (s.c - s.ym) + (s.c - s.yp);
   T sz = T(0);
-  if (s.zb >= 0) sz += s.c - s.zm;
-  else if (dlo) sz += T(2) * s.c;
-  if (s.za >= 0) sz += s.c - s.zp;
-  else if (dhi) sz += T(2) * s.c;
+  if (bt) {
+    if (s.zb >= 0) sz += s.c - s.zm;
+    else if (dlo) sz += T(2) * s.c;
+    if (s.za >= 0) sz += s.c - s.zp;
+    else if (dhi) sz += T(2) * s.c;
+  } else {
+    sz = (s.c - s.zm) + (s.c - s.zp);
+  }
   return ax * sx + ay * sy + az * sz;
+}
+
+template <typename T>
+__device__ __forceinline__ T mg_inv_bt(const MgView<T>& L, int xy, int z, T inv_int, const bool bt) {
+  return bt ? mg_inv(L, xy, z, inv_int) : inv_int;
 }
 
 template <typename T, int VX>
@@ -76,12 +86,15 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_pre(MgView<T> L, Scalars* S) {
   const T* hsrc[1] = {L.f};
   const T* osrc[1] = {nullptr};
   TileGeo<MTX, MTY, VX> s;
-  auto val = [&](const T (&h)[1], int xy, int z, int, int) -> T { return om * mg_inv(L, xy, z, inv_int) * h[0]; };
-  auto emit = [&](int xy, int z, const Stencil7<T>& st, const T (&h)[1], const T (&)[1]) -> T {
-    const int dlo = st.zb < 0 ? (int)L.tlo[xy] : 0;
-    const int dhi = st.za < 0 ? (int)L.thi[xy] : 0;
-    const T Ae = apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az);
-    return st.c + om * mg_inv(L, xy, z, inv_int) * (h[0] - Ae);
+  auto val = [&](const T (&h)[1], int xy, int z, int, int, const bool bt) -> T {
+    return om * mg_inv_bt(L, xy, z, inv_int, bt) * h[0];
+  };
+  auto emit = [&](int xy, int z, const Stencil7<T>& st, const T (&h)[1], const T (&)[1], const bool bt) -> T {
+    const bool B = bt;
+    const int dlo = (B && st.zb < 0) ? (int)L.tlo[xy] : 0;
+    const int dhi = (B && st.za < 0) ? (int)L.thi[xy] : 0;
+    const T Ae = apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az, bt);
+    return st.c + om * mg_inv_bt(L, xy, z, inv_int, bt) * (h[0] - Ae);
   };
   auto post = [&](int z, const T (&ov)[VX]) { store_n<T, VX>(L.e + (long long)z * L.g.nxy + s.xy, ov); };
   const TileSched ts{&S->sched_next, &S->sched_done};
@@ -109,11 +122,12 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Sc
   T racc[VX];
 #pragma unroll
   for (int i = 0; i < VX; ++i) racc[i] = T(0);
-  auto val = [&](const T (&h)[1], int, int, int, int) -> T { return h[0]; };
-  auto emit = [&](int xy, int, const Stencil7<T>& st, const T (&)[1], const T (&o)[1]) -> T {
-    const int dlo = st.zb < 0 ? (int)L.tlo[xy] : 0;
-    const int dhi = st.za < 0 ? (int)L.thi[xy] : 0;
-    return o[0] - apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az);
+  auto val = [&](const T (&h)[1], int, int, int, int, bool) -> T { return h[0]; };
+  auto emit = [&](int xy, int, const Stencil7<T>& st, const T (&)[1], const T (&o)[1], const bool bt) -> T {
+    const bool B = bt;
+    const int dlo = (B && st.zb < 0) ? (int)L.tlo[xy] : 0;
+    const int dhi = (B && st.za < 0) ? (int)L.thi[xy] : 0;
+    return o[0] - apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az, bt);
   };
   auto post = [&](int z, const T (&rv)[VX]) {
 #pragma unroll
@@ -167,12 +181,13 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_post1(MgView<T> L, MgView<T> C,
   const T* osrc[1] = {L.f};
   const ParentSrc<T> par{C.e, L.fx, L.fy, L.fz, C.g.nx, C.g.nxy};
   TileGeo<MTX, MTY, VX> s;
-  auto val = [&](const T (&h)[1], int, int, int, int, T parent) -> T { return h[0] + parent; };
-  auto emit = [&](int xy, int z, const Stencil7<T>& st, const T (&)[1], const T (&o)[1]) -> T {
-    const int dlo = st.zb < 0 ? (int)L.tlo[xy] : 0;
-    const int dhi = st.za < 0 ? (int)L.thi[xy] : 0;
-    const T Ae = apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az);
-    return st.c + om * mg_inv(L, xy, z, inv_int) * (o[0] - Ae);
+  auto val = [&](const T (&h)[1], int, int, int, int, T parent, bool) -> T { return h[0] + parent; };
+  auto emit = [&](int xy, int z, const Stencil7<T>& st, const T (&)[1], const T (&o)[1], const bool bt) -> T {
+    const bool B = bt;
+    const int dlo = (B && st.zb < 0) ? (int)L.tlo[xy] : 0;
+    const int dhi = (B && st.za < 0) ? (int)L.thi[xy] : 0;
+    const T Ae = apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az, bt);
+    return st.c + om * mg_inv_bt(L, xy, z, inv_int, bt) * (o[0] - Ae);
   };
   auto post = [&](int z, const T (&ov)[VX]) { store_n<T, VX>(L.et + (long long)z * L.g.nxy + s.xy, ov); };
   const TileSched ts{&S->sched_next, &S->sched_done};
@@ -195,12 +210,13 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_post2(MgView<T> L, double* part
   const T* osrc[1] = {L.f};
   Acc<T> arz;
   TileGeo<MTX, MTY, VX> s;
-  auto val = [&](const T (&h)[1], int, int, int, int) -> T { return h[0]; };
-  auto emit = [&](int xy, int z, const Stencil7<T>& st, const T (&)[1], const T (&o)[1]) -> T {
-    const int dlo = st.zb < 0 ? (int)L.tlo[xy] : 0;
-    const int dhi = st.za < 0 ? (int)L.thi[xy] : 0;
-    const T Ae = apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az);
-    const T e = st.c + om * mg_inv(L, xy, z, inv_int) * (o[0] - Ae);
+  auto val = [&](const T (&h)[1], int, int, int, int, bool) -> T { return h[0]; };
+  auto emit = [&](int xy, int z, const Stencil7<T>& st, const T (&)[1], const T (&o)[1], const bool bt) -> T {
+    const bool B = bt;
+    const int dlo = (B && st.zb < 0) ? (int)L.tlo[xy] : 0;
+    const int dhi = (B && st.za < 0) ? (int)L.thi[xy] : 0;
+    const T Ae = apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az, bt);
+    const T e = st.c + om * mg_inv_bt(L, xy, z, inv_int, bt) * (o[0] - Ae);
     if (LAST) arz.add(o[0], e);
     return e;
   };

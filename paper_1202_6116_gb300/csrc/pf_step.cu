@@ -61,9 +61,10 @@ __global__ void __launch_bounds__(MTX* MTY) k_rhs(Geo g, Bc<T> bc, const T* __re
   const T* osrc[1] = {invd};
   Acc<T> abb, arr, arz;
   TileGeo<MTX, MTY, VX> s;
-  auto emit = [&](int xy, int z, const Stencil7<Raw<T, NH>>& st, const T (&o)[NO > 0 ? NO : 1]) -> T {
-    const int dlo = st.zb < 0 ? (int)bc.tlo[xy] : 0;
-    const int dhi = st.za < 0 ? (int)bc.thi[xy] : 0;
+  auto emit = [&](int xy, int z, const Stencil7<Raw<T, NH>>& st, const T (&o)[NO > 0 ? NO : 1], const bool bt) -> T {
+    const bool B = bt;
+    const int dlo = (B && st.zb < 0) ? (int)bc.tlo[xy] : 0;
+    const int dhi = (B && st.za < 0) ? (int)bc.thi[xy] : 0;
     const T ec = EPS ? st.c.v[NH - 1] : T(1);
     T dir = T(0);
     if (dlo) dir += T(2) * ec * bc.vlo[xy];
@@ -86,12 +87,14 @@ __global__ void __launch_bounds__(MTX* MTY) k_rhs(Geo g, Bc<T> bc, const T* __re
       se.zp = ev(st.zp);
       se.zb = st.zb;
       se.za = st.za;
-      Aphi = apply_field<T>(se, dlo, dhi, ih2);
+      Aphi = apply_bt(se, dlo, dhi, ih2, bt);
     } else {
-      Aphi = apply_field<T>(pick(st, 3), dlo, dhi, ih2);
+      Aphi = apply_bt(pick(st, 3), dlo, dhi, ih2, bt);
     }
     const T rv = b - Aphi;
-    const T inv = EPS ? o[0] : inv_diag_unit(g, bc, xy, z, inv6);
+    T inv;
+    if constexpr (EPS) inv = o[0];
+    else inv = B ? inv_diag_unit(g, bc, xy, z, inv6) : inv6;
     abb.add(b, b);
     arr.add(rv, rv);
     arz.add(rv, rv * inv);
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __r
   const T* hsrc[4] = {P, P + g.n, P + 2 * g.n, phi};
   const T* osrc[1] = {nullptr};
   TileGeo<MTX, MTY, VX> s;
-  auto emit = [&](int xy, int, const Stencil7<Raw<T, 4>>& st, const T (&)[1]) -> P3<T> {
+  auto emit = [&](int xy, int, const Stencil7<Raw<T, 4>>& st, const T (&)[1], bool) -> P3<T> {
     // E = -grad phi from face values (mean inside, V at an electrode, phi_cell at an open face)
     const T fc = st.c.v[3];
     T E[3];
