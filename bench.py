@@ -189,6 +189,7 @@ def run_ours(args):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     launches = 0
     iters = 0
+    graph_steps = 0
     barrier()
     clocks.start()
     time.sleep(0.3)
@@ -199,6 +200,7 @@ def run_ours(args):
         ends[k].record(stream)
         launches += info["kernel_launches"]
         iters += info["total_iters"]
+        graph_steps += info["graph_steps"]
     barrier()
     clk = clocks.stop()
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
@@ -278,6 +280,7 @@ def run_ours(args):
                 "data": "synthetic (seeded SplitMix64 initial state, electrode masks of the workload)",
                 "config": workload_config(w, args.workload, flush),
                 "poisson_iters_per_step": iters / args.steps,
+                "graph_steps": graph_steps,
                 "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
                 "clocks": clk, "impl": "ours"}
         print(json.dumps(line))

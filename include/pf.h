@@ -84,6 +84,10 @@ typedef struct {
   int32_t status;            /* pf_status of this call */
   int64_t kernel_launches;   /* kernels this call launched (including ones that
                                 returned at entry because the solve had finished) */
+  int64_t graph_steps;       /* steps of this call run as one CUDA graph each (a
+                                device-driven Krylov loop, no host round trip);
+                                the others ran host-driven (profiling on, or
+                                graphs unavailable) */
 } pf_step_info;
 
 /* Per-kernel device-time statistics collected while profiling is on (see

@@ -191,6 +191,13 @@ struct pf_ctx {
   Scalars* S_host = nullptr;      // pinned host: mirror read back
   std::string err;
   int64_t launches = 0;           // kernels launched by the current call
+  // Whole-step CUDA graphs (one per polarization buffer parity); the Krylov
+  // loop is a conditional while node driven from the device.
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int graph_key = -1;             // singular flag the graphs were captured for
+  bool graphs_broken = false;     // capture not possible: host-driven loop
+  int64_t graph_steps = 0;        // steps of the current call run as graphs
+  cudaStream_t cap_stream = nullptr;
 
   // Profiling: events recorded between consecutive launches; each record
   // says which kernel family ran in the interval and what it moved.
@@ -400,6 +407,7 @@ void recompute_singular(pf_ctx* ctx) {
 // Reset the per-call solver state on the device.
 pf_status reset_scalars(pf_ctx* ctx) {
   ctx->launches = 0;
+  ctx->graph_steps = 0;
   Scalars& s = *ctx->S_tmpl;
   std::memset(&s, 0, sizeof(Scalars));
   s.rtol = ctx->prm.poisson_rtol;
@@ -478,12 +486,154 @@ pf_status solve(pf_ctx* ctx, const T* P) {
   return PF_OK;
 }
 
+void drop_graphs(pf_ctx* ctx) {
+  for (cudaGraphExec_t& e : ctx->gexec) {
+    if (e) cudaGraphExecDestroy(e);
+    e = nullptr;
+  }
+  ctx->graph_key = -1;
+}
+
+// Nodes of g that nothing depends on.
+bool graph_leaves(cudaGraph_t g, std::vector<cudaGraphNode_t>& out) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return false;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return false;
+  for (cudaGraphNode_t nd : nodes) {
+    size_t k = 0;
+    if (cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &k) != cudaSuccess) return false;
+    if (k == 0) out.push_back(nd);
+  }
+  return true;
+}
+
+// Capture one whole time step reading P from buffer cur:
+//   phase 1  [b mean] r0 = b - A phi  (+ first V-cycle)
+//   while    { CG iteration (+ V-cycle) }   -- condition set by the kernels
+//   phase 3  last x update [mean removal], TDGL update into buffer cur ^ 1
+template <typename T>
+pf_status capture_step(pf_ctx* ctx, int cur, cudaGraphExec_t* out) {
+  const pf::LaunchCfg saved = ctx->L;
+  const int64_t saved_launches = ctx->launches;
+  ctx->L.stream = ctx->cap_stream;
+  pf::Dev<T> d = dev_view<T>(ctx);
+  const Geo& g = ctx->geo;
+  T* Pbuf[2] = {(T*)ctx->P_user, (T*)(ctx->ws + ctx->lay.P_alt)};
+  const double coef[5] = {ctx->prm.a1, ctx->prm.a11, ctx->prm.a12, ctx->prm.g, ctx->prm.dt * ctx->prm.L};
+  const int mg = ctx->prm.solver == PF_PCG_MG;
+  cudaStream_t st = ctx->cap_stream;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle h = 0;
+  std::vector<cudaGraphNode_t> leaves;
+  cudaGraphNode_t cnode = nullptr;
+  cudaGraphNodeParams cp{};
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(st, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    if (ctx->singular) pf::launch_rhs_mean<T>(ctx->L, g, d, Pbuf[cur]);
+    pf::launch_rhs<T>(ctx->L, g, d, Pbuf[cur], h, 1);
+    if (mg) vcycle<T>(ctx, 0);
+    e = cudaStreamEndCapture(st, &graph);
+  }
+  if (e == cudaSuccess && !graph_leaves(graph, leaves)) e = cudaErrorUnknown;
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&cnode, graph, leaves.data(), nullptr, leaves.size(), &cp);
+  }
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      pf::launch_cg_p<T>(ctx->L, g, d, mg);
+      pf::launch_cg_r<T>(ctx->L, g, d, mg, h, 1);
+      if (mg) vcycle<T>(ctx, 1);
+      e = cudaStreamEndCapture(st, &body);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(st, graph, &cnode, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    pf::launch_cg_finish<T>(ctx->L, g, d, ctx->singular);
+    if (ctx->singular) pf::launch_sub_mean<T>(ctx->L, g, d);
+    pf::launch_tdgl<T>(ctx->L, g, d, Pbuf[cur], Pbuf[cur ^ 1], coef);
+    e = cudaStreamEndCapture(st, &graph);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  ctx->L = saved;
+  ctx->launches = saved_launches;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ctx->fail(PF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  }
+  *out = exec;
+  return PF_OK;
+}
+
+// Kernels one graph-launched step runs: fixed part and per Krylov iteration.
+void graph_kernel_counts(const pf_ctx* ctx, int64_t* fixed, int64_t* per_iter) {
+  const int64_t vc = ctx->prm.solver == PF_PCG_MG ? 4 * ((int64_t)ctx->lay.mg.size() - 1) + 1 : 0;
+  *fixed = (ctx->singular ? 2 : 0) + 3 + vc;
+  *per_iter = 2 + vc;
+}
+
+// Graph-launched steps: no host round trip inside a step.  Returns false
+// (nothing launched) when graphs cannot be used here.
+template <typename T>
+bool run_steps_graph(pf_ctx* ctx, int nsteps, pf_status* st) {
+  *st = PF_OK;
+  if (ctx->prof || ctx->graphs_broken || nsteps == 0) return false;
+  if (ctx->graph_key != ctx->singular) {
+    drop_graphs(ctx);
+    if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->graphs_broken = true;
+      return false;
+    }
+    for (int c = 0; c < 2; ++c) {
+      if (capture_step<T>(ctx, c, &ctx->gexec[c]) != PF_OK) {
+        drop_graphs(ctx);
+        ctx->graphs_broken = true;
+        ctx->err.clear();
+        return false;
+      }
+    }
+    ctx->graph_key = ctx->singular;
+  }
+  if (ctx->prm.has_eps && ctx->invd_dirty) {
+    pf::Dev<T> d = dev_view<T>(ctx);
+    pf::launch_invdiag<T>(ctx->L, ctx->geo, d);
+    ctx->launches += 1;
+    ctx->invd_dirty = false;
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    const cudaError_t e = cudaGraphLaunch(ctx->gexec[ctx->cur], ctx->stream);
+    if (e != cudaSuccess) {
+      *st = ctx->cuda_fail(e, "cudaGraphLaunch");
+      return true;
+    }
+    ctx->cur ^= 1;
+  }
+  ctx->graph_steps += nsteps;
+  return true;
+}
+
 template <typename T>
 pf_status run_steps(pf_ctx* ctx, int nsteps) {
   pf::Dev<T> d = dev_view<T>(ctx);
   const Geo& g = ctx->geo;
   T* Pbuf[2] = {(T*)ctx->P_user, (T*)(ctx->ws + ctx->lay.P_alt)};
   const double coef[5] = {ctx->prm.a1, ctx->prm.a11, ctx->prm.a12, ctx->prm.g, ctx->prm.dt * ctx->prm.L};
+  pf_status gst;
+  if (run_steps_graph<T>(ctx, nsteps, &gst)) {
+    if (gst != PF_OK) return gst;
+    nsteps = 0;
+  }
   for (int s = 0; s < nsteps; ++s) {
     T* P = Pbuf[ctx->cur];
     pf_status st = solve<T>(ctx, P);
@@ -552,7 +702,11 @@ pf_status finish_info(pf_ctx* ctx, int nsteps, pf_step_info* info) {
     info->last_relres = s.last_rel;
     info->nonconverged = s.nonconv;
     info->status = result;
-    info->kernel_launches = ctx->launches;
+    int64_t fixed = 0, per_iter = 0;
+    graph_kernel_counts(ctx, &fixed, &per_iter);
+    // graph-launched steps: kernels = fixed part + one loop body per iteration
+    info->kernel_launches = ctx->launches + (ctx->graph_steps ? ctx->graph_steps * fixed + s.total_iters * per_iter : 0);
+    info->graph_steps = ctx->graph_steps;
   }
   return result;
 }
@@ -634,6 +788,7 @@ pf_status pf_bind(pf_ctx* ctx, void* P, void* phi, const void* eps, void* worksp
   if (!is_device_ptr(P) || !is_device_ptr(phi) || !is_device_ptr(workspace) ||
       (ctx->prm.has_eps && !is_device_ptr(eps)))
     return ctx->fail(PF_ERR_ARG, "P, phi, eps and workspace must be device pointers");
+  drop_graphs(ctx);
   ctx->P_user = P;
   ctx->phi = phi;
   ctx->eps = ctx->prm.has_eps ? eps : nullptr;
@@ -750,6 +905,8 @@ int32_t pf_profile_read(const pf_ctx* ctx, pf_kernel_stat* out, int32_t max) {
 
 pf_status pf_destroy(pf_ctx* ctx) {
   if (!ctx) return PF_OK;
+  drop_graphs(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   if (ctx->S_tmpl) cudaFreeHost(ctx->S_tmpl);
   delete ctx;

@@ -124,7 +124,13 @@ template <typename T, bool EPS, bool MG>
 __global__ void __launch_bounds__(FLAT_THREADS) k_cg_r(Geo g, Bc<T> bc, const T* __restrict__ invd,
                                                       T* __restrict__ r, const T* __restrict__ q, double* part,
                                                       Scalars* S, cudaGraphConditionalHandle cond, int use_cond) {
-  if (S->done) return;
+  if (S->done) {
+    // In a graph loop the condition must drop whatever finished the solve
+    // (a breakdown in k_cg_p, a non-finite r.z in the V-cycle): every pass
+    // of the loop body either counts an iteration or ends the loop.
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+    return;
+  }
   using V = typename Vec16<T>::type;
   constexpr int NV = 16 / sizeof(T);
   const T alpha = T(S->alpha);

@@ -177,6 +177,7 @@ pf_status solve(const pf_params* prm, cudaStream_t st, char* base, const Layout&
     info->nonconverged = host.nonconv;
     info->status = result;
     info->kernel_launches = launches + (singular ? 1 : 0);
+    info->graph_steps = 0;
   }
   return result;
 }

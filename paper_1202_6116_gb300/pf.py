@@ -41,7 +41,7 @@ class pf_params(C.Structure):
 class pf_step_info(C.Structure):
     _fields_ = [("steps_done", C.c_int32), ("last_iters", C.c_int32), ("total_iters", C.c_int64),
                 ("last_relres", C.c_double), ("nonconverged", C.c_int32), ("status", C.c_int32),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("graph_steps", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -53,6 +53,26 @@ def test_fp64_grounded_film_200_steps(grounded_32):
     assert relerr(P, Pt) <= FP64_TOL
     assert relerr(phi, phit) <= FP64_TOL
     assert abs(info["total_iters"] - io["total_iters"]) <= 0.02 * io["total_iters"] + 5
+    assert info["graph_steps"] == w.steps          # every step ran as one CUDA graph
+
+
+def test_graph_and_host_driven_steps_agree():
+    """The same steps launched as CUDA graphs (device-driven Krylov loop) and
+    host-driven (profiling on) give bit-identical states."""
+    for solver in ("pcg", "mg"):
+        w = mixed_workload(48, 32, 8, 41, steps=4, rtol=1e-12).with_(solver=solver, maxit=2000)
+        f1 = Film(w)
+        st1, i1 = f1.step(4)
+        a = f1.numpy()
+        f1.close()
+        f2 = Film(w)
+        pf.pf_profile_enable(f2.ctx, 1)
+        st2, i2 = f2.step(4)
+        b = f2.numpy()
+        f2.close()
+        assert i1["graph_steps"] == 4 and i2["graph_steps"] == 0
+        assert i1["total_iters"] == i2["total_iters"]
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
 @pytest.mark.parametrize("case", [
