@@ -127,10 +127,11 @@ def measured_peak_hbm():
 
 
 def kernel_source_hash():
+    """Hash of the device-code sources (host-only driver files excluded)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1202_6116_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f.endswith((".cu", ".cuh", ".h")) and f not in ("pf_api.cu", "pf_noalloc.cu"):
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -172,7 +173,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     w = make_workload(args.workload, seed_offset=rank, solver=args.solver, size=args.size)
-    film = Film(w, device=dev)
+    film = Film(w, device=dev, **({"flags": 1} if args.no_graphs else {}))
     stream = film.stream
     flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     flush = "flushed (a %d MiB buffer is written between timed steps)" % (2 * L2_BYTES // 2 ** 20)
@@ -352,6 +353,9 @@ def main():
                     help="NXxNYxNZ: the workload's recipe on another grid (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every kernel from the host (profilers cannot see kernels inside CUDA graphs "
+                         "with conditional nodes)")
     args = ap.parse_args()
     if args.impl == "reference":
         args.steps = 5 if args.steps is None else args.steps

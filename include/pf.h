@@ -72,8 +72,14 @@ typedef struct {
   int32_t poisson_maxit;     /* iteration cap per solve (>= 1) */
   int32_t periodic_z;        /* 1: z periodic too (masks ignored; zero-mean potential) */
   int32_t has_eps;           /* 1: a cell permittivity field is bound; 0: eps = 1 */
-  int32_t reserved[7];       /* must be zero */
+  int32_t flags;             /* PF_FLAG_* bits (0 = defaults) */
+  int32_t reserved[6];       /* must be zero */
 } pf_params;
+
+/* pf_params.flags: launch every kernel from the host instead of running each
+ * step as one CUDA graph (profilers cannot see kernels inside graphs that
+ * contain conditional nodes). */
+enum { PF_FLAG_NO_GRAPHS = 1 };
 
 typedef struct {
   int32_t steps_done;        /* steps completed by this call */

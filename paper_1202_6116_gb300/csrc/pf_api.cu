@@ -104,7 +104,8 @@ bool params_valid(const pf_params* p, std::string* why) {
   }
   for (double v : {p->a1, p->a11, p->a12, p->g, p->L, p->dt})
     if (!std::isfinite(v)) return fail("coefficients must be finite");
-  for (int i = 0; i < 7; ++i)
+  if (p->flags & ~PF_FLAG_NO_GRAPHS) return fail("unknown bits in flags");
+  for (int i = 0; i < 6; ++i)
     if (p->reserved[i] != 0) return fail("reserved fields must be zero");
   return true;
 }
@@ -587,7 +588,7 @@ void graph_kernel_counts(const pf_ctx* ctx, int64_t* fixed, int64_t* per_iter) {
 template <typename T>
 bool run_steps_graph(pf_ctx* ctx, int nsteps, pf_status* st) {
   *st = PF_OK;
-  if (ctx->prof || ctx->graphs_broken || nsteps == 0) return false;
+  if (ctx->prof || ctx->graphs_broken || nsteps == 0 || (ctx->prm.flags & PF_FLAG_NO_GRAPHS)) return false;
   if (ctx->graph_key != ctx->singular) {
     drop_graphs(ctx);
     if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {

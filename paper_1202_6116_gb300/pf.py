@@ -18,6 +18,7 @@ PF_FP64, PF_FP32 = 0, 1
 PF_PCG_JACOBI, PF_PCG_MG = 0, 1
 PF_ZLO, PF_ZHI = 0, 1
 PF_NEUMANN, PF_DIRICHLET = 0, 1
+PF_FLAG_NO_GRAPHS = 1
 
 STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_CUDA", 3: "PF_ERR_NOCONV", 4: "PF_ERR_NONFINITE",
                 5: "PF_ERR_TIMEOUT", 6: "PF_ERR_STATE", 7: "PF_ERR_NOTIMPL"}
@@ -34,8 +35,8 @@ class pf_params(C.Structure):
                 ("g", C.c_double), ("L", C.c_double), ("dt", C.c_double),
                 ("precision", C.c_int32), ("solver", C.c_int32),
                 ("poisson_rtol", C.c_double), ("poisson_maxit", C.c_int32),
-                ("periodic_z", C.c_int32), ("has_eps", C.c_int32),
-                ("reserved", C.c_int32 * 7)]
+                ("periodic_z", C.c_int32), ("has_eps", C.c_int32), ("flags", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class pf_step_info(C.Structure):

@@ -79,6 +79,11 @@ def test_workspace_bytes_and_validation(L):
     q = good_params()
     q.reserved[3] = 1
     assert pf.pf_workspace_bytes(q) == 0
+    q = good_params()
+    q.flags = 4
+    assert pf.pf_workspace_bytes(q) == 0
+    q.flags = pf.PF_FLAG_NO_GRAPHS
+    assert pf.pf_workspace_bytes(q) > 0
 
 
 def test_null_context_calls_are_rejected(L):
