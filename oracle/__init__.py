@@ -57,6 +57,7 @@ def lib():
         L.or_step.argtypes = [vp, vp, vp, vp, i, vp]
         L.or_energy.restype = d
         L.or_energy.argtypes = [vp, vp, vp, d]
+        L.or_adjoint_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -212,6 +213,49 @@ def energy(G: Grid, prm: Params, P, rtol=1e-14) -> float:
     P = _f64(P).reshape((3,) + G.shape)
     g, p = G._c(), prm._c()
     return lib().or_energy(C.byref(g), C.byref(p), _ptr(P), float(rtol))
+
+
+def adjoint_step(G: Grid, prm: Params, P, lam, psi=None):
+    """Transposed Jacobian of one forward step at state P applied to lam.
+
+    Returns (lam_out, psi, grad[4] (a1, a11, a12, g), gv_lo, gv_hi, status,
+    iters): the step's sensitivities alone (not accumulated)."""
+    P = _f64(P).reshape((3,) + G.shape)
+    lam = _f64(lam).reshape((3,) + G.shape)
+    out = np.empty_like(lam)
+    psi = np.zeros(G.shape) if psi is None else _f64(psi).reshape(G.shape).copy()
+    grad = np.zeros(4)
+    gv_lo = np.zeros((G.ny, G.nx))
+    gv_hi = np.zeros((G.ny, G.nx))
+    it = C.c_int(0)
+    g, p = G._c(), prm._c()
+    st = lib().or_adjoint_step(C.byref(g), C.byref(p), _ptr(P), _ptr(lam), _ptr(out), _ptr(psi),
+                               _ptr(grad), _ptr(gv_lo), _ptr(gv_hi), C.byref(it))
+    return out, psi, grad, gv_lo, gv_hi, st, it.value
+
+
+def gradient(G: Grid, prm: Params, P0, lam_final, nsteps, phi0=None):
+    """Reverse pass over nsteps forward steps from (P0, phi0): every state is
+    kept, then the adjoint steps run backwards from lam_final = dJ/dP_nsteps.
+    Returns (dJ/dP0, dJ/d(a1, a11, a12, g), dJ/dvolt_lo, dJ/dvolt_hi)."""
+    states = [_f64(P0).reshape((3,) + G.shape).copy()]
+    phi = None if phi0 is None else _f64(phi0)
+    for _ in range(nsteps):
+        P, phi, st, _info = step(G, prm, states[-1], phi, 1)
+        assert st == OK
+        states.append(P)
+    lam = _f64(lam_final).reshape((3,) + G.shape).copy()
+    grad = np.zeros(4)
+    gv_lo = np.zeros((G.ny, G.nx))
+    gv_hi = np.zeros((G.ny, G.nx))
+    psi = None
+    for k in range(nsteps - 1, -1, -1):
+        lam, psi, gk, glo, ghi, st, _it = adjoint_step(G, prm, states[k], lam, psi)
+        assert st == OK
+        grad += gk
+        gv_lo += glo
+        gv_hi += ghi
+    return lam, grad, gv_lo, gv_hi
 
 
 OK, NOCONV = 0, 3

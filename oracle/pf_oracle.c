@@ -388,3 +388,73 @@ double or_energy(const or_grid* G, const or_params* prm, const double* P, double
   free(phi); free(E); free(zero);
   return F;
 }
+
+/* Discrete adjoint of one forward-Euler step of or_step.
+ *
+ * One step maps P_n to P_{n+1} = P_n + dt L (-f'(P_n) + g Lap P_n + E(phi_n))
+ * with A phi_n = -div P_n + B(V) (Eqs. TDGL, rho, Poisson; Section Time
+ * Integration).  Write E(phi) = E0(phi) + E_V, where E0 is the face rule R3
+ * with every electrode voltage at zero and E_V the field of the voltages
+ * alone.  By R3, E0 is the transpose of the divergence, and A and Lap are
+ * symmetric, so for a cotangent lambda = dJ/dP_{n+1}:
+ *   dJ/dP_n = lambda + dt L (-H(P_n) lambda + g Lap lambda + E0(psi)),
+ *   A psi = -div lambda,
+ * with H the 3x3 Hessian of the Landau density of each cell.  The step's
+ * parameter sensitivities lambda . dP_{n+1}/dtheta are added to grad
+ * (a1, a11, a12, g) and, per face cell, to gv_lo / gv_hi (the voltage of
+ * that face cell; nothing is added at a Neumann cell).  psi holds the warm
+ * start of the adjoint solve and is updated in place. */
+int or_adjoint_step(const or_grid* G, const or_params* prm, const double* P, const double* lam,
+                    double* lam_out, double* psi, double* grad, double* gv_lo, double* gv_hi,
+                    int* iters) {
+  long n = ncells(G), nxy = (long)G->nx * G->ny;
+  double ih = 1.0 / G->dx, ih2 = ih * ih, dtL = prm->dt * prm->L;
+  double* zero_v = (double*)calloc(2 * nxy, sizeof(double));
+  or_grid G0 = *G;                              /* same grid, electrodes at 0 V */
+  G0.volt_lo = zero_v;
+  G0.volt_hi = zero_v + nxy;
+  double* b = (double*)malloc(sizeof(double) * n);
+  double* E = (double*)malloc(sizeof(double) * 3 * n);
+  double* lapl = (double*)malloc(sizeof(double) * 3 * n);
+  double* lapP = (double*)malloc(sizeof(double) * 3 * n);
+
+  or_rhs(&G0, lam, b);                          /* -div lambda */
+  int st = or_solve(&G0, b, psi, prm->rtol, prm->maxit, iters, NULL);
+  or_field(&G0, psi, E);                        /* E0(psi) */
+  for (int c = 0; c < 3; ++c) {
+    or_laplacian(G, lam + (long)c * n, lapl + (long)c * n);
+    or_laplacian(G, P + (long)c * n, lapP + (long)c * n);
+  }
+  for (long c = 0; c < n; ++c) {
+    double p[3] = {P[c], P[n + c], P[2 * n + c]};
+    double l[3] = {lam[c], lam[n + c], lam[2 * n + c]};
+    for (int i = 0; i < 3; ++i) {
+      int j = (i + 1) % 3, k = (i + 2) % 3;
+      double Hl = (2.0 * prm->a1 + 12.0 * prm->a11 * p[i] * p[i] +
+                   2.0 * prm->a12 * (p[j] * p[j] + p[k] * p[k])) * l[i] +
+                  4.0 * prm->a12 * p[i] * (p[j] * l[j] + p[k] * l[k]);
+      long ic = (long)i * n + c;
+      lam_out[ic] = l[i] + dtL * (-Hl + prm->g * lapl[ic] + E[ic]);
+      /* d/dtheta of dt L (-f'_i(P) + g Lap P_i) */
+      grad[0] += l[i] * dtL * -(2.0 * p[i]);
+      grad[1] += l[i] * dtL * -(4.0 * p[i] * p[i] * p[i]);
+      grad[2] += l[i] * dtL * -(2.0 * p[i] * (p[j] * p[j] + p[k] * p[k]));
+      grad[3] += l[i] * dtL * lapP[ic];
+    }
+  }
+  /* A face voltage V enters b of its cell as 2 eps_c V / dx^2 and the face
+   * value of phi in E_z of that cell (R3, R4). */
+  if (!G->periodic_z) {
+    for (int y = 0; y < G->ny; ++y)
+      for (int x = 0; x < G->nx; ++x) {
+        long m = (long)y * G->nx + x;
+        long c0 = cell_index(G, x, y, 0), c1 = cell_index(G, x, y, G->nz - 1);
+        if (G->type_lo[m] == 1)
+          gv_lo[m] += dtL * (-psi[c0] * 2.0 * eps_of(G, c0) * ih2 + lam[2 * n + c0] * ih);
+        if (G->type_hi[m] == 1)
+          gv_hi[m] += dtL * (-psi[c1] * 2.0 * eps_of(G, c1) * ih2 - lam[2 * n + c1] * ih);
+      }
+  }
+  free(zero_v); free(b); free(E); free(lapl); free(lapP);
+  return st;
+}

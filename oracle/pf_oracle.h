@@ -115,6 +115,15 @@ int or_step(const or_grid* G, const or_params* prm, double* P, double* phi, int 
  * with phi solved to rtol; E_ext is the field of the electrodes with P = 0. */
 double or_energy(const or_grid* G, const or_params* prm, const double* P, double rtol);
 
+/* Discrete adjoint of one or_step step at the state P (= P_n): from
+ * lam = dJ/dP_{n+1} computes lam_out = dJ/dP_n, and adds this step's
+ * sensitivities to grad[4] (a1, a11, a12, g) and to the per-face-cell
+ * voltage sensitivities gv_lo, gv_hi (nx*ny each).  psi is the warm start of
+ * the adjoint Poisson solve (in/out).  Returns the solve's status. */
+int or_adjoint_step(const or_grid* G, const or_params* prm, const double* P, const double* lam,
+                    double* lam_out, double* psi, double* grad, double* gv_lo, double* gv_hi,
+                    int* iters);
+
 #ifdef __cplusplus
 }
 #endif
