@@ -76,10 +76,13 @@ typedef struct {
   int32_t reserved[6];       /* must be zero */
 } pf_params;
 
-/* pf_params.flags: launch every kernel from the host instead of running each
- * step as one CUDA graph (profilers cannot see kernels inside graphs that
- * contain conditional nodes). */
-enum { PF_FLAG_NO_GRAPHS = 1 };
+/* pf_params.flags:
+ *   PF_FLAG_NO_GRAPHS  launch every kernel from the host instead of running
+ *                      each step as one CUDA graph (profilers cannot see
+ *                      kernels inside graphs that contain conditional nodes);
+ *   PF_FLAG_ADJOINT    reserve workspace for pf_adjoint_step (one more scalar
+ *                      field, the adjoint potential, and one face array). */
+enum { PF_FLAG_NO_GRAPHS = 1, PF_FLAG_ADJOINT = 2 };
 
 typedef struct {
   int32_t steps_done;        /* steps completed by this call */
@@ -162,10 +165,34 @@ pf_status pf_step_host(pf_ctx* ctx, void* P_host, void* phi_host, int32_t nsteps
 /* Solve the Poisson problem for the current P only (no P update). */
 pf_status pf_solve_potential(pf_ctx* ctx, pf_step_info* info);
 
-/* Reverse-mode step of the discrete TDGL + Poisson map; not available in
- * this version (returns PF_ERR_NOTIMPL). */
+/* Reverse-mode (discrete adjoint) step of one forward-Euler TDGL + Poisson
+ * step (Eq. TDGL, Eqs. rho and Poisson, Section Time Integration), taken at
+ * the state P_n held in the bound P buffer.
+ *
+ * The forward step is P_{n+1} = P_n + dt L (-df/dP + g Lap P_n + E), with E
+ * the field of the potential solved from P_n.  Given lam_in = dJ/dP_{n+1}
+ * this writes lam_out = dJ/dP_n, obtained from one Poisson solve for the
+ * adjoint potential (A psi = -div lam_in, electrodes at 0 V; same solver,
+ * rtol and maxit as the forward solve, warm-started from the previous
+ * adjoint step's psi, which pf_bind zeroes), and ADDS this step's
+ * contribution lam_in . dP_{n+1}/dtheta to
+ *   grad_params[0..3]  for theta = a1, a11, a12, g;
+ *   grad_volts         (NULL to skip) for theta = each face voltage:
+ *                      grad_volts[m] for volts of face PF_ZLO at m = y*nx + x,
+ *                      grad_volts[nx*ny + m] for face PF_ZHI; entries of
+ *                      Neumann face cells are left unchanged.
+ * Summing over the steps in reverse order gives the gradient of J with
+ * respect to the initial state (the last lam_out) and to the parameters.
+ *
+ * lam_in, lam_out: device, 3*nx*ny*nz values of the context precision,
+ *   component-major like P, 16-byte aligned; lam_out must not overlap lam_in
+ *   or the bound buffers.  grad_params (4 doubles) and grad_volts
+ *   (2*nx*ny doubles): device, accumulated in place.
+ * Needs a context created with PF_FLAG_ADJOINT (else PF_ERR_STATE).
+ * Returns PF_ERR_NOCONV / PF_ERR_NONFINITE like pf_solve_potential; info
+ * (may be NULL) reports the adjoint solve. */
 pf_status pf_adjoint_step(pf_ctx* ctx, const void* lam_in, void* lam_out, double* grad_params,
-                          double* grad_volts);
+                          double* grad_volts, pf_step_info* info);
 
 /* Turn per-kernel timing on (1) or off (0); turning it on clears the
  * counters.  While on, every launch is bracketed by CUDA events on the

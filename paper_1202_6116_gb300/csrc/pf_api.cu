@@ -76,6 +76,8 @@ std::vector<MgLevelHost> mg_levels(const pf_params* p) {
 
 struct Layout {
   size_t P_alt, r, p0, p1, q, invd, tlo, thi, vlo, vhi, part, S, z, zt, total;
+  bool adj = false;               // psi and vzero exist (PF_FLAG_ADJOINT)
+  size_t psi = 0, vzero = 0;      // adjoint potential; zero face voltages
   std::vector<MgLevelHost> mg;
 };
 
@@ -104,7 +106,7 @@ bool params_valid(const pf_params* p, std::string* why) {
   }
   for (double v : {p->a1, p->a11, p->a12, p->g, p->L, p->dt})
     if (!std::isfinite(v)) return fail("coefficients must be finite");
-  if (p->flags & ~PF_FLAG_NO_GRAPHS) return fail("unknown bits in flags");
+  if (p->flags & ~(PF_FLAG_NO_GRAPHS | PF_FLAG_ADJOINT)) return fail("unknown bits in flags");
   for (int i = 0; i < 6; ++i)
     if (p->reserved[i] != 0) return fail("reserved fields must be zero");
   return true;
@@ -133,8 +135,13 @@ Layout layout_of(const pf_params* p) {
   // reduction partials: per block (flat kernels) or per tile (plane-march
   // kernels; at most one tile per column group of MTX x MTY and plane)
   const size_t max_tiles = (size_t)((p->nx + pf::MTX - 1) / pf::MTX) * ((p->ny + pf::MTY - 1) / pf::MTY) * p->nz;
-  L.part = take(sizeof(double) * std::max<size_t>((size_t)pf::MAX_GRID * pf::MAX_NV, 2 * max_tiles));
+  L.part = take(sizeof(double) * std::max<size_t>((size_t)pf::MAX_GRID * pf::MAX_NV, pf::MAX_NV * max_tiles));
   L.S = take(sizeof(Scalars));
+  if (p->flags & PF_FLAG_ADJOINT) {
+    L.adj = true;
+    L.psi = take(n * w);
+    L.vzero = take(nxy * w);
+  }
   L.z = L.zt = 0;
   if (p->solver == PF_PCG_MG) {
     L.mg = mg_levels(p);
@@ -187,6 +194,7 @@ struct pf_ctx {
   int singular = 1;               // no Dirichlet face anywhere (or periodic z)
   bool invd_dirty = true;
   int est_iters = 8;              // iterations issued before the first poll
+  int est_iters_adj = 8;          // the same for the adjoint solves
   std::vector<int8_t> tlo_h, thi_h;
   Scalars* S_tmpl = nullptr;      // pinned host: template written at each call
   Scalars* S_host = nullptr;      // pinned host: mirror read back
@@ -240,11 +248,12 @@ struct pf_ctx {
 namespace {
 
 enum Fam {
-  F_RHS_MEAN, F_RHS, F_CG_P, F_CG_R, F_FINISH, F_SUB_MEAN, F_TDGL, F_INVDIAG,
+  F_RHS_MEAN, F_RHS, F_CG_P, F_CG_R, F_FINISH, F_SUB_MEAN, F_TDGL, F_INVDIAG, F_TDGL_ADJ,
   F_MG_PRE, F_MG_RR, F_MG_COARSE, F_MG_POST1, F_MG_POST2, F_COUNT
 };
-const char* const FAM_NAMES[F_COUNT] = {"rhs_mean", "rhs", "cg_p", "cg_r", "cg_finish", "sub_mean", "tdgl",
-                                        "invdiag", "mg_pre", "mg_rr", "mg_coarse", "mg_post1", "mg_post2"};
+const char* const FAM_NAMES[F_COUNT] = {"rhs_mean", "rhs",    "cg_p",      "cg_r",     "cg_finish",
+                                        "sub_mean", "tdgl",   "invdiag",   "tdgl_adj", "mg_pre",
+                                        "mg_rr",    "mg_coarse", "mg_post1", "mg_post2"};
 
 // Multigrid families are kept per level: family id F_COUNT + level * 5 + kind.
 int mg_fam(int kind, size_t level) { return F_COUNT + (int)level * 5 + (kind - F_MG_PRE); }
@@ -425,11 +434,22 @@ pf_status read_scalars(pf_ctx* ctx) {
   return PF_OK;
 }
 
+// The adjoint solve's view: the unknown is psi and every electrode is at 0 V.
+template <typename T>
+void adjoint_view(pf_ctx* ctx, pf::Dev<T>& d) {
+  d.phi = (T*)(ctx->ws + ctx->lay.psi);
+  d.bc.vlo = (const T*)(ctx->ws + ctx->lay.vzero);
+  d.bc.vhi = d.bc.vlo;
+}
+
 // One Poisson solve for the polarization P (device pointer of the current
 // state): r0, PCG iterations until the device flag says done, final update.
+// adj: solve for the adjoint potential instead (P is then the cotangent).
 template <typename T>
-pf_status solve(pf_ctx* ctx, const T* P) {
+pf_status solve(pf_ctx* ctx, const T* P, bool adj = false) {
   pf::Dev<T> d = dev_view<T>(ctx);
+  if (adj) adjoint_view<T>(ctx, d);
+  int& est_iters = adj ? ctx->est_iters_adj : ctx->est_iters;
   const Geo& g = ctx->geo;
   const double N = (double)g.n, w = sizeof(T), e = ctx->prm.has_eps ? 1.0 : 0.0;
   if (ctx->prm.has_eps && ctx->invd_dirty) {
@@ -453,7 +473,7 @@ pf_status solve(pf_ctx* ctx, const T* P) {
   // flag is set, and the device sets it by iteration maxit at the latest.
   const int maxit = ctx->prm.poisson_maxit;
   int issued = 0;
-  int batch = std::max(1, std::min(ctx->est_iters, maxit));
+  int batch = std::max(1, std::min(est_iters, maxit));
   for (;;) {
     for (int i = 0; i < batch; ++i) {
       const int it = issued + i + 1;
@@ -472,10 +492,10 @@ pf_status solve(pf_ctx* ctx, const T* P) {
     if (ctx->S_host->done) break;
     if (issued >= maxit)
       return ctx->fail(PF_ERR_STATE, "internal: solver did not stop after %d iterations", issued);
-    batch = std::min(std::max(2, ctx->est_iters / 8), maxit - issued);
+    batch = std::min(std::max(2, est_iters / 8), maxit - issued);
   }
   const Scalars& s = *ctx->S_host;
-  if (!s.zero_x) ctx->est_iters = std::max(1, s.iter);
+  if (!s.zero_x) est_iters = std::max(1, s.iter);
   before_launch(ctx);
   pf::launch_cg_finish<T>(ctx->L, g, d, ctx->singular);
   after_launch(ctx, F_FINISH, (s.zero_x ? 1.0 : (s.pending ? 3.0 : 1.0)) * N * w);
@@ -802,6 +822,11 @@ pf_status pf_bind(pf_ctx* ctx, void* P, void* phi, const void* eps, void* worksp
   std::fill(ctx->thi_h.begin(), ctx->thi_h.end(), 0);
   recompute_singular(ctx);
   PF_CUDA(cudaMemsetAsync(ctx->ws + L.S, 0, sizeof(Scalars), ctx->stream));
+  if (L.adj) {
+    const size_t w = ctx->prm.precision == PF_FP32 ? 4 : 8;
+    PF_CUDA(cudaMemsetAsync(ctx->ws + L.psi, 0, (size_t)ctx->geo.n * w, ctx->stream));
+    PF_CUDA(cudaMemsetAsync(ctx->ws + L.vzero, 0, (size_t)ctx->geo.nxy * w, ctx->stream));
+  }
   pf_status ms = upload_masks(ctx);
   if (ms != PF_OK) return ms;
   ctx->bound = true;
@@ -884,9 +909,54 @@ pf_status pf_solve_potential(pf_ctx* ctx, pf_step_info* info) {
   return finish_info(ctx, 0, info);
 }
 
-pf_status pf_adjoint_step(pf_ctx* ctx, const void*, void*, double*, double*) {
-  if (!ctx) return PF_ERR_ARG;
-  return ctx->fail(PF_ERR_NOTIMPL, "pf_adjoint_step is not available in this version");
+pf_status pf_adjoint_step(pf_ctx* ctx, const void* lam_in, void* lam_out, double* grad_params,
+                          double* grad_volts, pf_step_info* info) {
+  pf_status st = check_ready(ctx);
+  if (st != PF_OK) return st;
+  if (!ctx->lay.adj) return ctx->fail(PF_ERR_STATE, "the context was created without PF_FLAG_ADJOINT");
+  if (!lam_in || !lam_out || !grad_params) return ctx->fail(PF_ERR_ARG, "lam_in, lam_out and grad_params must be non-NULL");
+  if (((uintptr_t)lam_in % 16) || ((uintptr_t)lam_out % 16))
+    return ctx->fail(PF_ERR_ARG, "lam_in and lam_out must be 16-byte aligned");
+  if (((uintptr_t)grad_params % 8) || ((uintptr_t)grad_volts % 8))
+    return ctx->fail(PF_ERR_ARG, "grad_params and grad_volts must be 8-byte aligned");
+  if (!is_device_ptr(lam_in) || !is_device_ptr(lam_out) || !is_device_ptr(grad_params) ||
+      (grad_volts && !is_device_ptr(grad_volts)))
+    return ctx->fail(PF_ERR_ARG, "lam_in, lam_out, grad_params and grad_volts must be device pointers");
+  const size_t w = ctx->prm.precision == PF_FP32 ? 4 : 8;
+  const size_t n = (size_t)ctx->geo.n;
+  auto overlap = [](const void* a, size_t na, const void* b, size_t nb) {
+    const char *pa = (const char*)a, *pb = (const char*)b;
+    return pa < pb + nb && pb < pa + na;
+  };
+  if (overlap(lam_out, 3 * n * w, lam_in, 3 * n * w) || overlap(lam_out, 3 * n * w, ctx->P_user, 3 * n * w) ||
+      overlap(lam_out, 3 * n * w, ctx->phi, n * w) || overlap(lam_out, 3 * n * w, ctx->ws, ctx->lay.total))
+    return ctx->fail(PF_ERR_ARG, "lam_out overlaps lam_in or a bound buffer");
+  if (ctx->cur != 0) return ctx->fail(PF_ERR_STATE, "internal: state not in the bound P buffer");
+  st = reset_scalars(ctx);
+  if (st != PF_OK) return st;
+  const double coef[5] = {ctx->prm.a1, ctx->prm.a11, ctx->prm.a12, ctx->prm.g, ctx->prm.dt * ctx->prm.L};
+  double* gv_lo = grad_volts;
+  double* gv_hi = grad_volts ? grad_volts + ctx->geo.nxy : nullptr;
+  if (ctx->prm.precision == PF_FP32) {
+    st = solve<float>(ctx, (const float*)lam_in, true);
+    if (st != PF_OK) return st;
+    pf::Dev<float> d = dev_view<float>(ctx);
+    before_launch(ctx);
+    pf::launch_tdgl_adj<float>(ctx->L, ctx->geo, d, (const float*)lam_in, (float*)lam_out,
+                               (const float*)(ctx->ws + ctx->lay.psi), (const float*)ctx->P_user, coef,
+                               grad_params, gv_lo, gv_hi);
+  } else {
+    st = solve<double>(ctx, (const double*)lam_in, true);
+    if (st != PF_OK) return st;
+    pf::Dev<double> d = dev_view<double>(ctx);
+    before_launch(ctx);
+    pf::launch_tdgl_adj<double>(ctx->L, ctx->geo, d, (const double*)lam_in, (double*)lam_out,
+                                (const double*)(ctx->ws + ctx->lay.psi), (const double*)ctx->P_user, coef,
+                                grad_params, gv_lo, gv_hi);
+  }
+  after_launch(ctx, F_TDGL_ADJ, 10.0 * (double)n * w);
+  PF_CUDA(cudaGetLastError());
+  return finish_info(ctx, 0, info);
 }
 
 pf_status pf_profile_enable(pf_ctx* ctx, int32_t enable) {

@@ -75,6 +75,12 @@ template <typename T>
 void launch_tdgl(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, T* Pn, const double* coef);
 template <typename T>
 void launch_invdiag(const LaunchCfg& L, const Geo& g, const Dev<T>& d);
+// Adjoint update (pf_adjoint.cu): lam_out from lam, the adjoint potential psi
+// and the state P; adds the parameter sensitivities to grad[4] and, when
+// gv_lo/gv_hi are non-NULL, the face-voltage sensitivities.
+template <typename T>
+void launch_tdgl_adj(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* lam, T* lam_out, const T* psi,
+                     const T* P, const double* coef, double* grad, double* gv_lo, double* gv_hi);
 
 // Tiling of a plane-march launch on an nx x ny x nz grid: the deepest z
 // chunk that still gives about three tiles per resident block.

@@ -62,7 +62,7 @@ Layout layout(const pf_params* p) {
   L.thi = take(nxy);
   L.vlo = take(nxy * w);
   L.vhi = take(nxy * w);
-  L.part = take(sizeof(double) * std::max<size_t>((size_t)pf::MAX_GRID * pf::MAX_NV, 2 * max_tiles));
+  L.part = take(sizeof(double) * std::max<size_t>((size_t)pf::MAX_GRID * pf::MAX_NV, pf::MAX_NV * max_tiles));
   L.S = take(sizeof(pf::Scalars));
   L.total = off;
   return L;

@@ -30,13 +30,17 @@ def make_params(w: Workload, **overrides) -> pf.pf_params:
 class Film:
     """Device state (P, phi, eps, workspace) of one film plus its context."""
 
-    def __init__(self, w: Workload, device="cuda", stream=None, phi0=None, **overrides):
+    def __init__(self, w: Workload, device="cuda", stream=None, phi0=None, P0=None, **overrides):
+        """P0 (optional): a device tensor that replaces w.P0 (copied)."""
         self.w = w
         self.params = make_params(w, **overrides)
         self.dtype = torch.float32 if self.params.precision == pf.PF_FP32 else torch.float64
         dev = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
-        self.P = torch.as_tensor(np.ascontiguousarray(w.P0), dtype=self.dtype, device=dev).contiguous()
+        if P0 is not None:
+            self.P = P0.detach().to(device=dev, dtype=self.dtype).clone().contiguous()
+        else:
+            self.P = torch.as_tensor(np.ascontiguousarray(w.P0), dtype=self.dtype, device=dev).contiguous()
         self.phi = torch.zeros(w.shape, dtype=self.dtype, device=dev) if phi0 is None else \
             torch.as_tensor(np.ascontiguousarray(phi0), dtype=self.dtype, device=dev).contiguous()
         self.eps = None if w.eps is None else \

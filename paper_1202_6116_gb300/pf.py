@@ -19,6 +19,7 @@ PF_PCG_JACOBI, PF_PCG_MG = 0, 1
 PF_ZLO, PF_ZHI = 0, 1
 PF_NEUMANN, PF_DIRICHLET = 0, 1
 PF_FLAG_NO_GRAPHS = 1
+PF_FLAG_ADJOINT = 2
 
 STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_CUDA", 3: "PF_ERR_NOCONV", 4: "PF_ERR_NONFINITE",
                 5: "PF_ERR_TIMEOUT", 6: "PF_ERR_STATE", 7: "PF_ERR_NOTIMPL"}
@@ -86,7 +87,7 @@ def lib():
         L.pf_solve_potential.restype = i32
         L.pf_solve_potential.argtypes = [vp, C.POINTER(pf_step_info)]
         L.pf_adjoint_step.restype = i32
-        L.pf_adjoint_step.argtypes = [vp, vp, vp, vp, vp]
+        L.pf_adjoint_step.argtypes = [vp, vp, vp, vp, vp, vp]
         L.pf_profile_enable.restype = i32
         L.pf_profile_enable.argtypes = [vp, i32]
         L.pf_profile_read.restype = i32
@@ -167,8 +168,14 @@ def pf_solve_potential(ctx, ok=(PF_OK,)):
     return st, info
 
 
-def pf_adjoint_step(ctx, lam_in, lam_out, grad_params, grad_volts):
-    return lib().pf_adjoint_step(ctx, _addr(lam_in), _addr(lam_out), _addr(grad_params), _addr(grad_volts))
+def pf_adjoint_step(ctx, lam_in, lam_out, grad_params, grad_volts=None, ok=(PF_OK,)):
+    """lam_in/lam_out: device 3N of the context precision; grad_params (4) and
+    grad_volts (2*nx*ny or None): device float64, accumulated."""
+    info = pf_step_info()
+    st = lib().pf_adjoint_step(ctx, _addr(lam_in), _addr(lam_out), _addr(grad_params), _addr(grad_volts),
+                               C.byref(info))
+    check(st, ctx, ok)
+    return st, info
 
 
 def pf_profile_enable(ctx, enable=1):
