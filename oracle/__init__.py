@@ -58,6 +58,7 @@ def lib():
         L.or_energy.restype = d
         L.or_energy.argtypes = [vp, vp, vp, d]
         L.or_adjoint_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.or_diagnostics.argtypes = [vp, vp, vp, vp, d, vp]
         _lib = L
     return _lib
 
@@ -256,6 +257,19 @@ def gradient(G: Grid, prm: Params, P0, lam_final, nsteps, phi0=None):
         gv_lo += glo
         gv_hi += ghi
     return lam, grad, gv_lo, gv_hi
+
+
+DIAG_NAMES = ("mean_px", "mean_py", "mean_pz", "switched_fraction", "f_landau", "f_grad", "f_elec")
+
+
+def diagnostics(G: Grid, prm: Params, P, phi, threshold=0.3) -> dict:
+    """Mean P, switched fraction (P_x > threshold) and the three energy terms."""
+    P = _f64(P).reshape((3,) + G.shape)
+    phi = _f64(phi).reshape(G.shape)
+    out = np.zeros(7)
+    g, p = G._c(), prm._c()
+    lib().or_diagnostics(C.byref(g), C.byref(p), _ptr(P), _ptr(phi), float(threshold), _ptr(out))
+    return dict(zip(DIAG_NAMES, out.tolist()))
 
 
 OK, NOCONV = 0, 3

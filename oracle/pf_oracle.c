@@ -458,3 +458,50 @@ int or_adjoint_step(const or_grid* G, const or_params* prm, const double* P, con
   free(zero_v); free(b); free(E); free(lapl); free(lapP);
   return st;
 }
+
+/* Run diagnostics of a state (P, phi), each summed over all cells:
+ *   out[0..2]  mean of P_x, P_y, P_z (the polarization of P-V loops);
+ *   out[3]     fraction of cells with P_x > threshold (switched domains);
+ *   out[4]     sum f(P)                                  (Eq. F_bulk);
+ *   out[5]     (g/2) sum over interior faces |P_nb - P_c|^2 / dx^2
+ *                                                        (Eq. F_grad, R1);
+ *   out[6]     -1/2 sum P . E(phi), E from phi with the face voltages (R3)
+ *                                                        (Eq. F_elec).
+ * With the electrodes at 0 V and phi the potential of P, out[4] + out[5] +
+ * out[6] is the free energy or_energy returns. */
+void or_diagnostics(const or_grid* G, const or_params* prm, const double* P, const double* phi,
+                    double threshold, double* out) {
+  long n = ncells(G);
+  for (int k = 0; k < 7; ++k) out[k] = 0.0;
+  for (long c = 0; c < n; ++c) {
+    out[0] += P[c];
+    out[1] += P[n + c];
+    out[2] += P[2 * n + c];
+    if (P[c] > threshold) out[3] += 1.0;
+  }
+  for (int k = 0; k < 4; ++k) out[k] /= (double)n;
+  out[4] = or_landau_energy(P, n, prm->a1, prm->a11, prm->a12);
+  double fg = 0.0;
+  for (int z = 0; z < G->nz; ++z)
+    for (int y = 0; y < G->ny; ++y)
+      for (int x = 0; x < G->nx; ++x) {
+        long c = cell_index(G, x, y, z);
+        for (int d = 0; d < 3; ++d) {
+          long nb;
+          int bt;
+          double bv;
+          if (!face_of(G, x, y, z, d, +1, &nb, &bt, &bv)) continue;
+          for (int i = 0; i < 3; ++i) {
+            double dp = P[(long)i * n + nb] - P[(long)i * n + c];
+            fg += dp * dp;
+          }
+        }
+      }
+  out[5] = 0.5 * prm->g * fg / (G->dx * G->dx);
+  double* E = (double*)malloc(sizeof(double) * 3 * n);
+  or_field(G, phi, E);
+  double pe = 0.0;
+  for (long i = 0; i < 3 * n; ++i) pe += P[i] * E[i];
+  out[6] = -0.5 * pe;
+  free(E);
+}

@@ -124,6 +124,12 @@ int or_adjoint_step(const or_grid* G, const or_params* prm, const double* P, con
                     double* lam_out, double* psi, double* grad, double* gv_lo, double* gv_hi,
                     int* iters);
 
+/* Diagnostics of (P, phi): out[0..2] mean P, out[3] fraction of cells with
+ * P_x > threshold, out[4] sum f(P), out[5] gradient energy, out[6]
+ * -1/2 sum P.E(phi).  out has 7 entries. */
+void or_diagnostics(const or_grid* G, const or_params* prm, const double* P, const double* phi,
+                    double threshold, double* out);
+
 #ifdef __cplusplus
 }
 #endif
