@@ -271,9 +271,12 @@ def run_ours(args):
                             for s in work}}
 
     cpu = None
+    film.close()
+    prec = None
+    if rank == 0 and world == 1 and args.precision_steps > 3:
+        prec = precision_check(dev, args.precision_steps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, args.cpu_seconds)
-    film.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -283,10 +286,45 @@ def run_ours(args):
                 "poisson_iters_per_step": iters / args.steps,
                 "graph_steps": graph_steps,
                 "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
-                "clocks": clk, "impl": "ours"}
+                "clocks": clk, "fp32_vs_fp64": prec, "impl": "ours"}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+# -------------------------------------------------------- FP32 against FP64
+
+def precision_check(dev, steps):
+    """The strip-electrode film (256x256x64, MG-PCG to 1e-8) advanced in FP32
+    (FP64 reductions) and in plain FP64 on this GPU: time per step of each,
+    the FP32 error on P (max |P32 - P64| / max |P64| per component) and the
+    switched-domain fraction (P_x > 0.3) of both."""
+    import torch
+    from paper_1202_6116_gb300 import workloads as W
+    from paper_1202_6116_gb300.film import Film
+    out = {"workload": "strips 256x256x64 MG-PCG rtol=1e-08 dt=0.01, %d steps from the seeded state" % steps}
+    finals = {}
+    for prec in ("fp32", "fp64"):
+        w = W.film_strip_fp32().with_(precision=prec, solver="mg", maxit=500)
+        f = Film(w, device=dev)
+        f.step(3)                                  # graph capture and warm-up, excluded
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(f.stream)
+        _, info = f.step(steps - 3)
+        e1.record(f.stream)
+        e1.synchronize()
+        d = f.diagnostics(0.3)
+        finals[prec] = f.P.double()
+        out[prec + "_ms_per_step"] = round(e0.elapsed_time(e1) / (steps - 3), 4)
+        out[prec + "_poisson_iters_per_step"] = round(info["total_iters"] / (steps - 3), 2)
+        out[prec + "_switched_fraction"] = d["switched_fraction"]
+        f.close()
+    a, b = finals["fp32"], finals["fp64"]
+    out["max_rel_err_P"] = max(float((a[c] - b[c]).abs().max() / b[c].abs().max()) for c in range(3))
+    out["switched_diff_pp"] = 100.0 * abs(out["fp32_switched_fraction"] - out["fp64_switched_fraction"])
+    out["fp32_speedup"] = round(out["fp64_ms_per_step"] / out["fp32_ms_per_step"], 3)
+    return out
 
 
 # ----------------------------------------------------------------- CPU oracle
@@ -352,6 +390,8 @@ def main():
     ap.add_argument("--size", type=lambda v: tuple(int(x) for x in v.lower().split("x")), default=None,
                     help="NXxNYxNZ: the workload's recipe on another grid (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--precision-steps", type=int, default=200,
+                    help="steps of the FP32-against-FP64 comparison on the strip film (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel from the host (profilers cannot see kernels inside CUDA graphs "

@@ -194,6 +194,22 @@ pf_status pf_solve_potential(pf_ctx* ctx, pf_step_info* info);
 pf_status pf_adjoint_step(pf_ctx* ctx, const void* lam_in, void* lam_out, double* grad_params,
                           double* grad_volts, pf_step_info* info);
 
+/* Run diagnostics of the bound state (P, phi), one pass over the grid; waits
+ * for the result.  out (host, 7 doubles):
+ *   out[0..2]  mean P_x, P_y, P_z (polarization of P-V loops);
+ *   out[3]     fraction of cells with P_x > threshold (switched domains,
+ *              compared in FP64);
+ *   out[4]     sum over cells of the Landau density f(P) (Eq. F_bulk);
+ *   out[5]     gradient energy (g/2) sum over interior faces |P_nb - P_c|^2/dx^2
+ *              (Eq. F_grad; z faces of a non-periodic film excluded);
+ *   out[6]     -1/2 sum over cells P . E(phi), E = -grad phi from face values
+ *              with the face voltages (Eq. F_elec).
+ * Energies are sums over cells (multiply by dx^3 for a volume integral).
+ * With the electrodes at 0 V and phi the potential of P (pf_solve_potential
+ * first), out[4] + out[5] + out[6] is the discrete free energy that the TDGL
+ * step descends.  Sums are reduced in a fixed order (reproducible). */
+pf_status pf_diagnostics(pf_ctx* ctx, double threshold, double* out);
+
 /* Turn per-kernel timing on (1) or off (0); turning it on clears the
  * counters.  While on, every launch is bracketed by CUDA events on the
  * context's stream (no extra synchronisation: the events are read at the

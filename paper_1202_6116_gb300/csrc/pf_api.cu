@@ -75,7 +75,7 @@ std::vector<MgLevelHost> mg_levels(const pf_params* p) {
 }
 
 struct Layout {
-  size_t P_alt, r, p0, p1, q, invd, tlo, thi, vlo, vhi, part, S, z, zt, total;
+  size_t P_alt, r, p0, p1, q, invd, tlo, thi, vlo, vhi, part, S, diag, z, zt, total;
   bool adj = false;               // psi and vzero exist (PF_FLAG_ADJOINT)
   size_t psi = 0, vzero = 0;      // adjoint potential; zero face voltages
   std::vector<MgLevelHost> mg;
@@ -137,6 +137,7 @@ Layout layout_of(const pf_params* p) {
   const size_t max_tiles = (size_t)((p->nx + pf::MTX - 1) / pf::MTX) * ((p->ny + pf::MTY - 1) / pf::MTY) * p->nz;
   L.part = take(sizeof(double) * std::max<size_t>((size_t)pf::MAX_GRID * pf::MAX_NV, pf::MAX_NV * max_tiles));
   L.S = take(sizeof(Scalars));
+  L.diag = take(8 * sizeof(double));
   if (p->flags & PF_FLAG_ADJOINT) {
     L.adj = true;
     L.psi = take(n * w);
@@ -248,12 +249,12 @@ struct pf_ctx {
 namespace {
 
 enum Fam {
-  F_RHS_MEAN, F_RHS, F_CG_P, F_CG_R, F_FINISH, F_SUB_MEAN, F_TDGL, F_INVDIAG, F_TDGL_ADJ,
+  F_RHS_MEAN, F_RHS, F_CG_P, F_CG_R, F_FINISH, F_SUB_MEAN, F_TDGL, F_INVDIAG, F_TDGL_ADJ, F_DIAG,
   F_MG_PRE, F_MG_RR, F_MG_COARSE, F_MG_POST1, F_MG_POST2, F_COUNT
 };
-const char* const FAM_NAMES[F_COUNT] = {"rhs_mean", "rhs",    "cg_p",      "cg_r",     "cg_finish",
-                                        "sub_mean", "tdgl",   "invdiag",   "tdgl_adj", "mg_pre",
-                                        "mg_rr",    "mg_coarse", "mg_post1", "mg_post2"};
+const char* const FAM_NAMES[F_COUNT] = {"rhs_mean", "rhs",      "cg_p",     "cg_r",     "cg_finish",
+                                        "sub_mean", "tdgl",     "invdiag",  "tdgl_adj", "diag",
+                                        "mg_pre",   "mg_rr",    "mg_coarse", "mg_post1", "mg_post2"};
 
 // Multigrid families are kept per level: family id F_COUNT + level * 5 + kind.
 int mg_fam(int kind, size_t level) { return F_COUNT + (int)level * 5 + (kind - F_MG_PRE); }
@@ -957,6 +958,37 @@ pf_status pf_adjoint_step(pf_ctx* ctx, const void* lam_in, void* lam_out, double
   after_launch(ctx, F_TDGL_ADJ, 10.0 * (double)n * w);
   PF_CUDA(cudaGetLastError());
   return finish_info(ctx, 0, info);
+}
+
+pf_status pf_diagnostics(pf_ctx* ctx, double threshold, double* out) {
+  pf_status st = check_ready(ctx);
+  if (st != PF_OK) return st;
+  if (!out) return ctx->fail(PF_ERR_ARG, "out is NULL");
+  if (!std::isfinite(threshold)) return ctx->fail(PF_ERR_ARG, "threshold must be finite");
+  if (ctx->cur != 0) return ctx->fail(PF_ERR_STATE, "internal: state not in the bound P buffer");
+  const double coef[4] = {ctx->prm.a1, ctx->prm.a11, ctx->prm.a12, threshold};
+  double* dsum = (double*)(ctx->ws + ctx->lay.diag);
+  ctx->launches = 0;
+  before_launch(ctx);
+  if (ctx->prm.precision == PF_FP32)
+    pf::launch_diag<float>(ctx->L, ctx->geo, dev_view<float>(ctx), (const float*)ctx->P_user, coef, dsum);
+  else
+    pf::launch_diag<double>(ctx->L, ctx->geo, dev_view<double>(ctx), (const double*)ctx->P_user, coef, dsum);
+  after_launch(ctx, F_DIAG, 4.0 * (double)ctx->geo.n * (ctx->prm.precision == PF_FP32 ? 4 : 8));
+  PF_CUDA(cudaGetLastError());
+  double h[8];
+  PF_CUDA(cudaMemcpyAsync(h, dsum, 7 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  PF_CUDA(cudaStreamSynchronize(ctx->stream));
+  prof_harvest(ctx, 0, 1);
+  const double n = (double)ctx->geo.n;
+  out[0] = h[0] / n;
+  out[1] = h[1] / n;
+  out[2] = h[2] / n;
+  out[3] = h[3] / n;
+  out[4] = h[4];
+  out[5] = 0.5 * ctx->prm.g * h[5] * ctx->geo.ih2;
+  out[6] = -0.5 * h[6];
+  return PF_OK;
 }
 
 pf_status pf_profile_enable(pf_ctx* ctx, int32_t enable) {

@@ -12,7 +12,7 @@
 namespace pf {
 
 constexpr int MAX_GRID = 4096;   // reduction partials are sized for this many blocks
-constexpr int MAX_NV = 4;        // values reduced per block
+constexpr int MAX_NV = 8;        // values reduced per block or tile
 constexpr int MG_MAX_LEVELS = 24;
 constexpr int MG_MAX_COARSE = 1024;   // cells of the coarsest multigrid level (one block)
 
@@ -81,6 +81,11 @@ void launch_invdiag(const LaunchCfg& L, const Geo& g, const Dev<T>& d);
 template <typename T>
 void launch_tdgl_adj(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* lam, T* lam_out, const T* psi,
                      const T* P, const double* coef, double* grad, double* gv_lo, double* gv_hi);
+
+// Diagnostics (pf_diag.cu): out[0..6] = sums of P_x, P_y, P_z, [P_x > thr],
+// f(P), the squared face differences of P, and P.E(phi); coef = {a1, a11, a12, thr}.
+template <typename T>
+void launch_diag(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, const double* coef, double* out);
 
 // Tiling of a plane-march launch on an nx x ny x nz grid: the deepest z
 // chunk that still gives about three tiles per resident block.

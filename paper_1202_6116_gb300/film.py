@@ -69,6 +69,10 @@ class Film:
         st, info = pf.pf_solve_potential(self.ctx, ok)
         return st, info.as_dict()
 
+    def diagnostics(self, threshold=0.3):
+        """Mean P, switched fraction and energy terms of the current state."""
+        return pf.pf_diagnostics(self.ctx, threshold)
+
     def numpy(self):
         return (self.P.double().cpu().numpy(), self.phi.double().cpu().numpy())
 

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_CUDA", 3: "PF_ERR_NOCONV
 
 # Every symbol the header declares.
 EXPORTS = ["pf_workspace_bytes", "pf_create", "pf_bind", "pf_set_bc", "pf_step", "pf_step_host",
-           "pf_solve_potential", "pf_adjoint_step", "pf_profile_enable", "pf_profile_read", "pf_destroy",
+           "pf_solve_potential", "pf_adjoint_step", "pf_diagnostics", "pf_profile_enable", "pf_profile_read", "pf_destroy",
            "pf_last_error", "pf_solve_potential_noalloc"]
 
 
@@ -86,6 +86,8 @@ def lib():
         L.pf_step_host.argtypes = [vp, vp, vp, i32, C.POINTER(pf_step_info)]
         L.pf_solve_potential.restype = i32
         L.pf_solve_potential.argtypes = [vp, C.POINTER(pf_step_info)]
+        L.pf_diagnostics.restype = i32
+        L.pf_diagnostics.argtypes = [vp, C.c_double, vp]
         L.pf_adjoint_step.restype = i32
         L.pf_adjoint_step.argtypes = [vp, vp, vp, vp, vp, vp]
         L.pf_profile_enable.restype = i32
@@ -176,6 +178,16 @@ def pf_adjoint_step(ctx, lam_in, lam_out, grad_params, grad_volts=None, ok=(PF_O
                                C.byref(info))
     check(st, ctx, ok)
     return st, info
+
+
+DIAG_NAMES = ("mean_px", "mean_py", "mean_pz", "switched_fraction", "f_landau", "f_grad", "f_elec")
+
+
+def pf_diagnostics(ctx, threshold=0.3):
+    """Diagnostics of the bound state as a dict (names in DIAG_NAMES)."""
+    out = (C.c_double * 7)()
+    check(lib().pf_diagnostics(ctx, float(threshold), C.cast(out, C.c_void_p)), ctx)
+    return dict(zip(DIAG_NAMES, list(out)))
 
 
 def pf_profile_enable(ctx, enable=1):

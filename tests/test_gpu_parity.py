@@ -182,7 +182,11 @@ def test_bad_arguments_on_gpu():
         pf.pf_set_bc(f.ctx, 5, np.zeros(64, np.int8), None)
     with pytest.raises(pf.PfError):
         pf.pf_bind(f.ctx, f.P, f.phi, None, f.workspace, 16)
-    assert pf.pf_adjoint_step(f.ctx, None, None, None, None) == pf.PF_ERR_NOTIMPL
+    # the failed bind leaves the context unbound: every call reports it
+    with pytest.raises(pf.PfError):
+        pf.pf_step(f.ctx, 1)
+    with pytest.raises(pf.PfError):
+        pf.pf_adjoint_step(f.ctx, f.P, f.phi, None, None)
     f.close()
 
 
