@@ -55,6 +55,8 @@ def lib():
         L.or_solve.argtypes = [vp, vp, vp, d, i, vp, vp]
         L.or_solve_potential.argtypes = [vp, vp, vp, d, i, vp, vp]
         L.or_step.argtypes = [vp, vp, vp, vp, i, vp]
+        L.or_rate.argtypes = [vp, vp, vp, vp, vp]
+        L.or_step_ex.argtypes = [vp, vp, i, i, l, vp, vp, i, vp]
         L.or_energy.restype = d
         L.or_energy.argtypes = [vp, vp, vp, d]
         L.or_adjoint_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -204,6 +206,35 @@ def step(G: Grid, prm: Params, P, phi=None, nsteps=1):
     info = _Info()
     g, p = G._c(), prm._c()
     st = lib().or_step(C.byref(g), C.byref(p), _ptr(P), _ptr(phi), int(nsteps), C.byref(info))
+    d = dict(steps_done=info.steps_done, last_iters=info.last_iters,
+             total_iters=info.total_iters, last_relres=info.last_relres,
+             nonconverged=info.nonconverged)
+    return P, phi, st, d
+
+
+INTEGRATORS = {"euler": 0, "heun": 1}
+
+
+def rate(G: Grid, prm: Params, P, phi):
+    """TDGL rate L(-df/dP + g Lap P + E(phi)) at state P with potential phi."""
+    P = _f64(P).reshape((3,) + G.shape)
+    phi = _f64(phi).reshape(G.shape)
+    out = np.empty_like(P)
+    g, p = G._c(), prm._c()
+    lib().or_rate(C.byref(g), C.byref(p), _ptr(P), _ptr(phi), _ptr(out))
+    return out
+
+
+def step_ex(G: Grid, prm: Params, P, phi=None, nsteps=1, integrator="euler", every=1, n0=0):
+    """nsteps steps of forward Euler or of the paper's predictor-corrector
+    ("heun"), the potential solved only on global steps n0 + s that are
+    multiples of every.  Returns (P, phi, status, info dict)."""
+    P = _f64(P).reshape((3,) + G.shape).copy()
+    phi = np.zeros(G.shape) if phi is None else _f64(phi).reshape(G.shape).copy()
+    info = _Info()
+    g, p = G._c(), prm._c()
+    st = lib().or_step_ex(C.byref(g), C.byref(p), INTEGRATORS[integrator], int(every), int(n0), _ptr(P),
+                          _ptr(phi), int(nsteps), C.byref(info))
     d = dict(steps_done=info.steps_done, last_iters=info.last_iters,
              total_iters=info.total_iters, last_relres=info.last_relres,
              nonconverged=info.nonconverged)

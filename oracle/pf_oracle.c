@@ -11,7 +11,8 @@
  *   Eqs. rho, Poisson     rho = div P,  eps Lap phi = rho  (Section
  *                         Electrostatics Calculation), boundary kinds listed
  *                         in the same section
- *   Section Time Integration: explicit forward Euler
+ *   Section Time Integration: explicit forward Euler and the
+ *                         predictor-corrector ("velocity Verlet") scheme
  *   Section Numerical Performance: the Krylov solve is warm-started from the
  *                         previous step's potential
  */
@@ -344,6 +345,76 @@ int or_step(const or_grid* G, const or_params* prm, double* P, double* phi, int 
   }
   if (info) *info = inf;
   free(b); free(h); free(lap); free(E);
+  return status;
+}
+
+/* TDGL rate dP/dt = L (-df/dP + g Lap P + E(phi)) at the state P with the
+ * potential phi (Eq. TDGL with Eqs. F_bulk, dF_grad/dP and F_elec). */
+void or_rate(const or_grid* G, const or_params* prm, const double* P, const double* phi, double* R) {
+  long n = ncells(G);
+  double* h = (double*)malloc(sizeof(double) * 3 * n);
+  double* lap = (double*)malloc(sizeof(double) * 3 * n);
+  double* E = (double*)malloc(sizeof(double) * 3 * n);
+  or_field(G, phi, E);
+  or_landau_force(P, n, prm->a1, prm->a11, prm->a12, h);
+  for (int c = 0; c < 3; ++c) or_laplacian(G, P + (long)c * n, lap + (long)c * n);
+  for (long i = 0; i < 3 * n; ++i) R[i] = prm->L * (-h[i] + prm->g * lap[i] + E[i]);
+  free(h); free(lap); free(E);
+}
+
+/* One potential solve for the state P, warm-started from phi, booked in inf. */
+static int solve_booked(const or_grid* G, const or_params* prm, const double* P, double* phi, double* b,
+                        or_info* inf) {
+  int it = 0;
+  double rel = 0.0;
+  or_rhs(G, P, b);
+  int st = or_solve(G, b, phi, prm->rtol, prm->maxit, &it, &rel);
+  if (st != OR_OK) inf->nonconverged++;
+  inf->last_iters = it;
+  inf->total_iters += it;
+  inf->last_relres = rel;
+  return st;
+}
+
+/* Time integration with the options of Sections Time Integration and
+ * Numerical Performance.
+ *   integrator OR_EULER: P_{n+1} = P_n + dt R(P_n, phi(P_n)).
+ *   integrator OR_HEUN, the paper's predictor-corrector: the predictor
+ *     P^p = P^c_n + dt R(P^c_n) takes the rate at the corrected state, the
+ *     rate used for the step is the mean of that rate and the rate at the
+ *     predicted state, and the corrected state is P^c_{n+1} = P^c_n + dt times
+ *     that mean.  Each rate has the potential of its own state.
+ *   every: the long-range (electrostatic) potential is solved only on steps
+ *     whose global index n0 + s is a multiple of every; the other steps, both
+ *     Heun stages included, keep the last potential solved.
+ * On return phi is the last potential solved (warm start of the next one). */
+int or_step_ex(const or_grid* G, const or_params* prm, int integrator, int every, long n0, double* P,
+               double* phi, int nsteps, or_info* info) {
+  long n = ncells(G);
+  double* b = (double*)malloc(sizeof(double) * n);
+  double* R = (double*)malloc(sizeof(double) * 3 * n);
+  double* Rp = (double*)malloc(sizeof(double) * 3 * n);
+  double* Pp = (double*)malloc(sizeof(double) * 3 * n);
+  or_info inf;
+  memset(&inf, 0, sizeof(inf));
+  int status = OR_OK;
+  if (every < 1) every = 1;
+  for (int s = 0; s < nsteps; ++s) {
+    const int refresh = ((n0 + s) % every) == 0;
+    if (refresh && solve_booked(G, prm, P, phi, b, &inf) != OR_OK) status = OR_NOCONV;
+    or_rate(G, prm, P, phi, R);
+    if (integrator == OR_HEUN) {
+      for (long i = 0; i < 3 * n; ++i) Pp[i] = P[i] + prm->dt * R[i];
+      if (refresh && solve_booked(G, prm, Pp, phi, b, &inf) != OR_OK) status = OR_NOCONV;
+      or_rate(G, prm, Pp, phi, Rp);
+      for (long i = 0; i < 3 * n; ++i) P[i] = P[i] + prm->dt * (0.5 * (R[i] + Rp[i]));
+    } else {
+      for (long i = 0; i < 3 * n; ++i) P[i] = P[i] + prm->dt * R[i];
+    }
+    inf.steps_done = s + 1;
+  }
+  if (info) *info = inf;
+  free(b); free(R); free(Rp); free(Pp);
   return status;
 }
 

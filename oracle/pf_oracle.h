@@ -111,6 +111,21 @@ int or_solve_potential(const or_grid* G, const double* P, double* phi, double rt
 int or_step(const or_grid* G, const or_params* prm, double* P, double* phi, int nsteps,
             or_info* info);
 
+/* Integrators of Section Time Integration (or_step_ex). */
+enum { OR_EULER = 0, OR_HEUN = 1 };
+
+/* TDGL rate L(-df/dP + g Lap P + E(phi)) at the state P (3N) and potential phi. */
+void or_rate(const or_grid* G, const or_params* prm, const double* P, const double* phi, double* R);
+
+/* nsteps steps of forward Euler (OR_EULER) or of the paper's predictor-corrector
+ * (OR_HEUN: P^p = P^c + dt R(P^c); P^c <- P^c + dt (R(P^c) + R(P^p))/2, each
+ * rate with the potential of its own state).  The potential is solved only on
+ * steps whose global index n0 + s is a multiple of every (>= 1); other steps
+ * keep the last potential (Section Numerical Performance: long-range terms
+ * every 5 steps).  phi: warm start in, last solved potential out. */
+int or_step_ex(const or_grid* G, const or_params* prm, int integrator, int every, long n0, double* P,
+               double* phi, int nsteps, or_info* info);
+
 /* Total free energy: sum f(P) + (g/2) sum_faces |dP|^2/dx^2 - 1/2 sum P.(E + E_ext),
  * with phi solved to rtol; E_ext is the field of the electrodes with P = 0. */
 double or_energy(const or_grid* G, const or_params* prm, const double* P, double rtol);
