@@ -21,7 +21,7 @@ using CgPipe = Pipe<T, typename FieldOf<T, EPS>::type, MTX, MTY, VX, EPS ? 4 : 2
 // MG = false: z = r/diag (Jacobi), r is the staged input.  MG = true: z comes
 // from the V-cycle and is the staged input.
 template <typename T, bool EPS, bool MG, int VX>
-__global__ void __launch_bounds__(MTX* MTY) k_cg_p(Geo g, Bc<T> bc, const T* __restrict__ eps,
+__global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g, Bc<T> bc, const T* __restrict__ eps,
                                                   const T* __restrict__ invd, const T* __restrict__ r, T* p0,
                                                   T* p1, T* __restrict__ q, T* __restrict__ x, double* part,
                                                   Scalars* S, MarchCfg mc) {

@@ -6,13 +6,14 @@
 // coarse z face is an electrode where any of its fine children is, and the
 // error equation has homogeneous boundary data.  Transfers: restriction is
 // the average of the children, prolongation is piecewise constant (its
-// scaled transpose), smoothing is weighted Jacobi (omega = 6/7) with the same
-// number of sweeps before and after, so the V-cycle is a symmetric positive
-// definite preconditioner.  The coarsest level (<= MG_MAX_COARSE cells) is
+// scaled transpose), smoothing is two Jacobi sweeps with the Chebyshev weights
+// of mg_omega1/mg_omega2 before the coarse correction and the same two in
+// reverse order after it (the adjoint smoother), so the V-cycle is a symmetric
+// positive definite preconditioner.  The coarsest level (<= MG_MAX_COARSE cells) is
 // solved by FP64 conjugate gradients inside one thread block.
 //
 // Per level and V-cycle (nu = 2):
-//   k_mg_pre     e = two Jacobi sweeps from zero (the first sweep omega f/diag
+//   k_mg_pre     e = two Jacobi sweeps from zero (the first sweep w1 f/diag
 //                is formed on the fly, halo included)   reads f, writes e
 //   k_mg_rr      r = f - A e and its restriction to the next level's rhs,
 //                summed over 2 x 2 columns by warp shuffles and over 2 planes
@@ -27,9 +28,21 @@ namespace pf {
 
 constexpr int MG_D = 2;   // planes of cp.async look-ahead
 
+// Jacobi weights of the two smoothing sweeps: the reciprocals of the roots of
+// the degree-2 Chebyshev polynomial on [b/4, b], b = 1.9, which bound the
+// spectrum of diag(A)^-1 A (in [0, 2] for this M-matrix) from below b/4 up,
+// i.e. 1/lambda_k with lambda_k = (b + a)/2 + (b - a)/2 cos((2k - 1) pi / 4),
+// a = b/4.  The pair damps the upper three quarters of the spectrum (the part
+// the coarse grid cannot represent) by |(1 - w1 l)(1 - w2 l)| <= 0.35 on
+// [b/4, 2]; weighted Jacobi with 6/7 twice leaves up to 0.51 there.  The
+// pre-smoother applies w1 then w2, the post-smoother w2 then w1.
 template <typename T>
-__device__ __forceinline__ T mg_omega() {
-  return T(6) / T(7);
+__device__ __forceinline__ T mg_omega1() {
+  return T(0.5912564121058501);
+}
+template <typename T>
+__device__ __forceinline__ T mg_omega2() {
+  return T(1.462658863889015);
 }
 
 // 1/diag of a level's operator at column xy of plane z.
@@ -82,19 +95,19 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_pre(MgView<T> L, Scalars* S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   if (S->done) return;
-  const T om = mg_omega<T>(), inv_int = mg_inv_int(L);
+  const T om1 = mg_omega1<T>(), om2 = mg_omega2<T>(), inv_int = mg_inv_int(L);
   const T* hsrc[1] = {L.f};
   const T* osrc[1] = {nullptr};
   TileGeo<MTX, MTY, VX> s;
   auto val = [&](const T (&h)[1], int xy, int z, int, int, const bool bt) -> T {
-    return om * mg_inv_bt(L, xy, z, inv_int, bt) * h[0];
+    return om1 * mg_inv_bt(L, xy, z, inv_int, bt) * h[0];
   };
   auto emit = [&](int xy, int z, const Stencil7<T>& st, const T (&h)[1], const T (&)[1], const bool bt) -> T {
     const bool B = bt;
     const int dlo = (B && st.zb < 0) ? (int)L.tlo[xy] : 0;
     const int dhi = (B && st.za < 0) ? (int)L.thi[xy] : 0;
     const T Ae = apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az, bt);
-    return st.c + om * mg_inv_bt(L, xy, z, inv_int, bt) * (h[0] - Ae);
+    return st.c + om2 * mg_inv_bt(L, xy, z, inv_int, bt) * (h[0] - Ae);
   };
   auto post = [&](int z, const T (&ov)[VX]) { store_n<T, VX>(L.e + (long long)z * L.g.nxy + s.xy, ov); };
   const TileSched ts{&S->sched_next, &S->sched_done};
@@ -172,11 +185,11 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Sc
 // Prolongation + correction fused into the first post-smoothing sweep: the
 // stencil field is e + e_c(parent), the parents staged with the fine planes.
 template <typename T, int VX>
-__global__ void __launch_bounds__(MTX* MTY) k_mg_post1(MgView<T> L, MgView<T> C, Scalars* S) {
+__global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_mg_post1(MgView<T> L, MgView<T> C, Scalars* S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   if (S->done) return;
-  const T om = mg_omega<T>(), inv_int = mg_inv_int(L);
+  const T om = mg_omega2<T>(), inv_int = mg_inv_int(L);
   const T* hsrc[1] = {L.e};
   const T* osrc[1] = {L.f};
   const ParentSrc<T> par{C.e, L.fx, L.fy, L.fz, C.g.nx, C.g.nxy};
@@ -205,7 +218,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_post2(MgView<T> L, double* part
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   if (S->done) return;
-  const T om = mg_omega<T>(), inv_int = mg_inv_int(L);
+  const T om = mg_omega1<T>(), inv_int = mg_inv_int(L);
   const T* hsrc[1] = {L.et};
   const T* osrc[1] = {L.f};
   Acc<T> arz;
@@ -339,29 +352,57 @@ static void smem_once(K kernel, size_t bytes, bool& flag) {
   }
 }
 
+// Grid of a multigrid launch: every tile of the level, at most as many
+// blocks as this kernel keeps resident on the GPU (its own occupancy, so the
+// lighter sweeps run more blocks per SM than the heavier ones).
+template <class K>
+static int mg_grid(K kernel, size_t bytes, long long ntiles, int& res) {
+  if (res == 0) {
+    int dev = 0, nsm = 1, nb = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      nsm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, MTX * MTY, bytes) != cudaSuccess) nb = 1;
+    cudaGetLastError();
+    res = std::max(1, nb) * std::max(1, nsm);
+  }
+  return (int)std::min<long long>(ntiles, std::min(res, MAX_GRID));
+}
+
 template <typename T, int VX>
 static void pre_v(const LaunchCfg& L, const MgView<T>& lv, Scalars* S) {
   static bool f = false;
-  smem_once(k_mg_pre<T, VX>, MgPipe1<T, VX>::bytes(), f);
-  k_mg_pre<T, VX><<<lv.mc.grid, dim3(MTX, MTY), MgPipe1<T, VX>::bytes(), L.stream>>>(lv, S);
+  static int res = 0;
+  const size_t bytes = MgPipe1<T, VX>::bytes();
+  smem_once(k_mg_pre<T, VX>, bytes, f);
+  const int grid = mg_grid(k_mg_pre<T, VX>, bytes, lv.mc.ntiles, res);
+  k_mg_pre<T, VX><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, S);
 }
 template <typename T, int VX>
 static void rr_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
   static bool f = false;
-  smem_once(k_mg_rr<T, VX>, MgPipe2<T, VX>::bytes(), f);
-  k_mg_rr<T, VX><<<lv.mc.grid, dim3(MTX, MTY), MgPipe2<T, VX>::bytes(), L.stream>>>(lv, cv, S);
+  static int res = 0;
+  const size_t bytes = MgPipe2<T, VX>::bytes();
+  smem_once(k_mg_rr<T, VX>, bytes, f);
+  const int grid = mg_grid(k_mg_rr<T, VX>, bytes, lv.mc.ntiles, res);
+  k_mg_rr<T, VX><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, cv, S);
 }
 template <typename T, int VX>
 static void post1_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
   static bool f = false;
-  smem_once(k_mg_post1<T, VX>, MgPipeP<T, VX>::bytes(), f);
-  k_mg_post1<T, VX><<<lv.mc.grid, dim3(MTX, MTY), MgPipeP<T, VX>::bytes(), L.stream>>>(lv, cv, S);
+  static int res = 0;
+  const size_t bytes = MgPipeP<T, VX>::bytes();
+  smem_once(k_mg_post1<T, VX>, bytes, f);
+  const int grid = mg_grid(k_mg_post1<T, VX>, bytes, lv.mc.ntiles, res);
+  k_mg_post1<T, VX><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, cv, S);
 }
 template <typename T, bool LAST, int VX>
 static void post2_v(const LaunchCfg& L, const MgView<T>& lv, double* part, Scalars* S) {
   static bool f = false;
-  smem_once(k_mg_post2<T, LAST, VX>, MgPipe2<T, VX>::bytes(), f);
-  k_mg_post2<T, LAST, VX><<<lv.mc.grid, dim3(MTX, MTY), MgPipe2<T, VX>::bytes(), L.stream>>>(lv, part, S);
+  static int res = 0;
+  const size_t bytes = MgPipe2<T, VX>::bytes();
+  smem_once(k_mg_post2<T, LAST, VX>, bytes, f);
+  const int grid = mg_grid(k_mg_post2<T, LAST, VX>, bytes, lv.mc.ntiles, res);
+  k_mg_post2<T, LAST, VX><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, part, S);
 }
 
 constexpr int vec_of(size_t bytes) { return (int)(16 / bytes); }
