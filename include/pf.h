@@ -58,6 +58,7 @@ enum { PF_FP64 = 0, PF_FP32 = 1 };              /* storage and arithmetic type o
 enum { PF_PCG_JACOBI = 0, PF_PCG_MG = 1 };      /* Poisson preconditioner */
 enum { PF_ZLO = 0, PF_ZHI = 1 };                /* z faces: z = -1/2 and z = nz - 1/2 */
 enum { PF_NEUMANN = 0, PF_DIRICHLET = 1 };      /* per-(x,y) face type */
+enum { PF_EULER = 0, PF_HEUN = 1 };             /* time integrator (Section Time Integration) */
 
 typedef struct {
   int32_t nx, ny, nz;        /* grid cells (Section Grid); each >= 1 */
@@ -65,7 +66,7 @@ typedef struct {
   double a1, a11, a12;       /* Landau coefficients, Eq. F_bulk */
   double g;                  /* gradient coefficient G11, Eq. dF_grad/dP */
   double L;                  /* mobility multiplying -dF/dP in Eq. TDGL */
-  double dt;                 /* forward-Euler time step */
+  double dt;                 /* time step */
   int32_t precision;         /* PF_FP64 or PF_FP32 (FP32 fields, FP64-accurate dots) */
   int32_t solver;            /* PF_PCG_JACOBI or PF_PCG_MG */
   double poisson_rtol;       /* stop when ||b - A phi||_2 / ||b||_2 < rtol (recursive residual) */
@@ -73,8 +74,22 @@ typedef struct {
   int32_t periodic_z;        /* 1: z periodic too (masks ignored; zero-mean potential) */
   int32_t has_eps;           /* 1: a cell permittivity field is bound; 0: eps = 1 */
   int32_t flags;             /* PF_FLAG_* bits (0 = defaults) */
-  int32_t reserved[6];       /* must be zero */
+  int32_t integrator;        /* PF_EULER (0) or PF_HEUN (the paper's predictor-corrector) */
+  int32_t poisson_every;     /* solve the potential on every k-th step only (0 or 1: every step) */
+  int32_t reserved[4];       /* must be zero */
 } pf_params;
+
+/* pf_params.integrator (Section Time Integration), with R(P) = L(-df/dP +
+ * g Lap P + E) and E the field of the potential of P:
+ *   PF_EULER  P_{n+1} = P_n + dt R(P_n);
+ *   PF_HEUN   the predictor-corrector the paper prints as "velocity Verlet":
+ *             P^p = P_n + dt R(P_n), P_{n+1} = P_n + dt (R(P_n) + R(P^p))/2;
+ *             two Poisson solves per step (the second warm-started from the
+ *             first), computed as P_{n+1} = (P_n + P^p + dt R(P^p))/2.
+ * pf_params.poisson_every = k > 1 (Section Numerical Performance: long-range
+ * terms every 5 steps): the potential is solved only on steps whose index
+ * (counted from pf_bind) is a multiple of k; the other steps, both Heun
+ * stages included, use the last potential solved. */
 
 /* pf_params.flags:
  *   PF_FLAG_NO_GRAPHS  launch every kernel from the host instead of running
@@ -145,10 +160,12 @@ pf_status pf_bind(pf_ctx* ctx, void* P, void* phi, const void* eps, void* worksp
  * may be NULL (0 V).  Ignored when periodic_z = 1. */
 pf_status pf_set_bc(pf_ctx* ctx, int32_t face, const int8_t* type_xy, const double* volts_xy);
 
-/* Advance nsteps forward-Euler steps.  Step n solves A phi = b(P_n) with the
- * current phi as initial guess, then updates
+/* Advance nsteps steps of the chosen integrator.  A forward-Euler step n
+ * solves A phi = b(P_n) with the current phi as initial guess, then updates
  *   P <- P - dt L (df/dP - g Lap P - E),  E = -grad phi.
- * On return P = P_nsteps and phi is the potential of P_{nsteps-1}.  Blocks
+ * On return P = P_nsteps and phi is the last potential solved: with Euler
+ * and poisson_every <= 1 the potential of P_{nsteps-1}, with Heun that of the
+ * last predicted state.  Blocks
  * the host until the work is done.  A solve that hits poisson_maxit does not
  * stop the run: the step completes with the unconverged potential and the
  * call returns PF_ERR_NOCONV with info->nonconverged counting such solves.

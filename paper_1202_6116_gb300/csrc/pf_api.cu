@@ -107,7 +107,9 @@ bool params_valid(const pf_params* p, std::string* why) {
   for (double v : {p->a1, p->a11, p->a12, p->g, p->L, p->dt})
     if (!std::isfinite(v)) return fail("coefficients must be finite");
   if (p->flags & ~(PF_FLAG_NO_GRAPHS | PF_FLAG_ADJOINT)) return fail("unknown bits in flags");
-  for (int i = 0; i < 6; ++i)
+  if (p->integrator != PF_EULER && p->integrator != PF_HEUN) return fail("integrator must be PF_EULER or PF_HEUN");
+  if (p->poisson_every < 0) return fail("poisson_every must be >= 0");
+  for (int i = 0; i < 4; ++i)
     if (p->reserved[i] != 0) return fail("reserved fields must be zero");
   return true;
 }
@@ -201,12 +203,15 @@ struct pf_ctx {
   Scalars* S_host = nullptr;      // pinned host: mirror read back
   std::string err;
   int64_t launches = 0;           // kernels launched by the current call
-  // Whole-step CUDA graphs (one per polarization buffer parity); the Krylov
-  // loop is a conditional while node driven from the device.
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // Whole-step CUDA graphs, one per (polarization buffer parity, with or
+  // without the potential solve); each Krylov loop is a conditional while
+  // node driven from the device.  Captured on first use.
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
   int graph_key = -1;             // singular flag the graphs were captured for
   bool graphs_broken = false;     // capture not possible: host-driven loop
   int64_t graph_steps = 0;        // steps of the current call run as graphs
+  int64_t graph_fixed = 0;        // kernels of those steps outside the Krylov loops
+  int64_t nstep = 0;              // steps since pf_bind (schedules poisson_every)
   cudaStream_t cap_stream = nullptr;
 
   // Profiling: events recorded between consecutive launches; each record
@@ -419,6 +424,7 @@ void recompute_singular(pf_ctx* ctx) {
 pf_status reset_scalars(pf_ctx* ctx) {
   ctx->launches = 0;
   ctx->graph_steps = 0;
+  ctx->graph_fixed = 0;
   Scalars& s = *ctx->S_tmpl;
   std::memset(&s, 0, sizeof(Scalars));
   s.rtol = ctx->prm.poisson_rtol;
@@ -516,92 +522,123 @@ void drop_graphs(pf_ctx* ctx) {
   ctx->graph_key = -1;
 }
 
-// Nodes of g that nothing depends on.
-bool graph_leaves(cudaGraph_t g, std::vector<cudaGraphNode_t>& out) {
-  size_t n = 0;
-  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return false;
-  std::vector<cudaGraphNode_t> nodes(n);
-  if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return false;
-  for (cudaGraphNode_t nd : nodes) {
-    size_t k = 0;
-    if (cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &k) != cudaSuccess) return false;
-    if (k == 0) out.push_back(nd);
-  }
-  return true;
+// Does step ctx->nstep solve the potential (poisson_every, Section Numerical
+// Performance)?
+bool refresh_step(const pf_ctx* ctx) {
+  const int k = ctx->prm.poisson_every;
+  return k <= 1 || ctx->nstep % k == 0;
 }
 
-// Capture one whole time step reading P from buffer cur:
-//   phase 1  [b mean] r0 = b - A phi  (+ first V-cycle)
-//   while    { CG iteration (+ V-cycle) }   -- condition set by the kernels
-//   phase 3  last x update [mean removal], TDGL update into buffer cur ^ 1
+// Kernels of one step outside the Krylov loops, and per Krylov iteration.
+void step_kernel_counts(const pf_ctx* ctx, int refresh, int64_t* fixed, int64_t* per_iter) {
+  const int64_t vc = ctx->prm.solver == PF_PCG_MG ? 4 * ((int64_t)ctx->lay.mg.size() - 1) + 1 : 0;
+  const bool heun = ctx->prm.integrator == PF_HEUN;
+  const int64_t per_solve = (ctx->singular ? 2 : 0) + 2 + vc;
+  *fixed = (refresh ? (heun ? 2 : 1) * per_solve : 0) + (heun ? 2 : 1);
+  *per_iter = 2 + vc;
+}
+
+// Append one whole time step of film ctx, reading P from buffer cur, to
+// graph after the nodes deps (empty: a root); on return deps holds the
+// step's last node.  With refresh = 1 the potential is solved:
+//   solve(P)   [b mean] r0 = b - A phi (+ first V-cycle); while { CG
+//              iteration (+ V-cycle) } with the condition set by the kernels;
+//              last x update [mean removal]
+//   Euler      solve(P_n); TDGL update into buffer cur ^ 1
+//   Heun       solve(P_n); predictor into buffer cur ^ 1; solve(P^p);
+//              corrector back into buffer cur
+// Launches are captured on stream st (capture mode thread-local).
 template <typename T>
-pf_status capture_step(pf_ctx* ctx, int cur, cudaGraphExec_t* out) {
+cudaError_t append_step(pf_ctx* ctx, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps, int cur, int refresh,
+                        cudaStream_t st) {
   const pf::LaunchCfg saved = ctx->L;
   const int64_t saved_launches = ctx->launches;
-  ctx->L.stream = ctx->cap_stream;
+  ctx->L.stream = st;
   pf::Dev<T> d = dev_view<T>(ctx);
   const Geo& g = ctx->geo;
   T* Pbuf[2] = {(T*)ctx->P_user, (T*)(ctx->ws + ctx->lay.P_alt)};
   const double coef[5] = {ctx->prm.a1, ctx->prm.a11, ctx->prm.a12, ctx->prm.g, ctx->prm.dt * ctx->prm.L};
   const int mg = ctx->prm.solver == PF_PCG_MG;
-  cudaStream_t st = ctx->cap_stream;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaGraphConditionalHandle h = 0;
-  std::vector<cudaGraphNode_t> leaves;
-  cudaGraphNode_t cnode = nullptr;
-  cudaGraphNodeParams cp{};
-  cudaError_t e = cudaGraphCreate(&graph, 0);
-  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
-  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(st, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    if (ctx->singular) pf::launch_rhs_mean<T>(ctx->L, g, d, Pbuf[cur]);
-    pf::launch_rhs<T>(ctx->L, g, d, Pbuf[cur], h, 1);
-    if (mg) vcycle<T>(ctx, 0);
-    e = cudaStreamEndCapture(st, &graph);
-  }
-  if (e == cudaSuccess && !graph_leaves(graph, leaves)) e = cudaErrorUnknown;
-  if (e == cudaSuccess) {
+  const bool heun = ctx->prm.integrator == PF_HEUN;
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  cudaError_t e = cudaSuccess;
+  // Capture the launches of body after deps; deps becomes the capture's frontier.
+  auto segment = [&](auto&& body) {
+    if (e != cudaSuccess) return;
+    e = cudaStreamBeginCaptureToGraph(st, graph, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), mode);
+    if (e != cudaSuccess) return;
+    body();
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* fr = nullptr;
+    size_t nfr = 0;
+    e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &fr, nullptr, &nfr);
+    if (e == cudaSuccess) deps.assign(fr, fr + nfr);
+    cudaGraph_t g_out = graph;
+    const cudaError_t e2 = cudaStreamEndCapture(st, &g_out);
+    if (e == cudaSuccess) e = e2;
+  };
+  // One Poisson solve for the state P with its own loop condition.
+  auto solve_nodes = [&](const T* P) {
+    cudaGraphConditionalHandle h = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    segment([&] {
+      if (ctx->singular) pf::launch_rhs_mean<T>(ctx->L, g, d, P);
+      pf::launch_rhs<T>(ctx->L, g, d, P, h, 1);
+      if (mg) vcycle<T>(ctx, 0);
+    });
+    if (e != cudaSuccess) return;
+    cudaGraphNode_t cnode = nullptr;
+    cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    e = cudaGraphAddNode(&cnode, graph, leaves.data(), nullptr, leaves.size(), &cp);
-  }
-  if (e == cudaSuccess) {
+    e = cudaGraphAddNode(&cnode, graph, deps.data(), nullptr, deps.size(), &cp);
+    if (e != cudaSuccess) return;
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      pf::launch_cg_p<T>(ctx->L, g, d, mg);
-      pf::launch_cg_r<T>(ctx->L, g, d, mg, h, 1);
-      if (mg) vcycle<T>(ctx, 1);
-      e = cudaStreamEndCapture(st, &body);
-    }
+    e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, mode);
+    if (e != cudaSuccess) return;
+    pf::launch_cg_p<T>(ctx->L, g, d, mg);
+    pf::launch_cg_r<T>(ctx->L, g, d, mg, h, 1);
+    if (mg) vcycle<T>(ctx, 1);
+    e = cudaStreamEndCapture(st, &body);
+    deps.assign(1, cnode);
+    segment([&] {
+      pf::launch_cg_finish<T>(ctx->L, g, d, ctx->singular);
+      if (ctx->singular) pf::launch_sub_mean<T>(ctx->L, g, d);
+    });
+  };
+  T* Pn = Pbuf[cur];
+  T* Pq = Pbuf[cur ^ 1];
+  if (refresh) solve_nodes(Pn);
+  if (heun) {
+    segment([&] { pf::launch_tdgl<T>(ctx->L, g, d, Pn, Pq, coef, 0); });
+    if (refresh) solve_nodes(Pq);
+    segment([&] { pf::launch_tdgl<T>(ctx->L, g, d, Pq, Pn, coef, 1); });
+  } else {
+    segment([&] { pf::launch_tdgl<T>(ctx->L, g, d, Pn, Pq, coef, 0); });
   }
-  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(st, graph, &cnode, nullptr, 1, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    pf::launch_cg_finish<T>(ctx->L, g, d, ctx->singular);
-    if (ctx->singular) pf::launch_sub_mean<T>(ctx->L, g, d);
-    pf::launch_tdgl<T>(ctx->L, g, d, Pbuf[cur], Pbuf[cur ^ 1], coef);
-    e = cudaStreamEndCapture(st, &graph);
-  }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-  if (graph) cudaGraphDestroy(graph);
   ctx->L = saved;
   ctx->launches = saved_launches;
+  return e;
+}
+
+// Capture one whole time step of this film as its own executable graph.
+template <typename T>
+pf_status capture_step(pf_ctx* ctx, int cur, int refresh, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaGraphNode_t> deps;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  if (e == cudaSuccess) e = append_step<T>(ctx, graph, deps, cur, refresh, ctx->cap_stream);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return ctx->fail(PF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
   }
   *out = exec;
   return PF_OK;
-}
-
-// Kernels one graph-launched step runs: fixed part and per Krylov iteration.
-void graph_kernel_counts(const pf_ctx* ctx, int64_t* fixed, int64_t* per_iter) {
-  const int64_t vc = ctx->prm.solver == PF_PCG_MG ? 4 * ((int64_t)ctx->lay.mg.size() - 1) + 1 : 0;
-  *fixed = (ctx->singular ? 2 : 0) + 3 + vc;
-  *per_iter = 2 + vc;
 }
 
 // Graph-launched steps: no host round trip inside a step.  Returns false
@@ -617,13 +654,14 @@ bool run_steps_graph(pf_ctx* ctx, int nsteps, pf_status* st) {
       ctx->graphs_broken = true;
       return false;
     }
-    for (int c = 0; c < 2; ++c) {
-      if (capture_step<T>(ctx, c, &ctx->gexec[c]) != PF_OK) {
-        drop_graphs(ctx);
-        ctx->graphs_broken = true;
-        ctx->err.clear();
-        return false;
-      }
+    // the graph of the first step is captured here, so that a failing
+    // capture falls back to host-driven steps before anything is launched
+    const int slot = ctx->cur * 2 + (refresh_step(ctx) ? 1 : 0);
+    if (capture_step<T>(ctx, ctx->cur, slot & 1, &ctx->gexec[slot]) != PF_OK) {
+      drop_graphs(ctx);
+      ctx->graphs_broken = true;
+      ctx->err.clear();
+      return false;
     }
     ctx->graph_key = ctx->singular;
   }
@@ -633,15 +671,29 @@ bool run_steps_graph(pf_ctx* ctx, int nsteps, pf_status* st) {
     ctx->launches += 1;
     ctx->invd_dirty = false;
   }
+  const bool heun = ctx->prm.integrator == PF_HEUN;
   for (int s = 0; s < nsteps; ++s) {
-    const cudaError_t e = cudaGraphLaunch(ctx->gexec[ctx->cur], ctx->stream);
+    const int refresh = refresh_step(ctx) ? 1 : 0;
+    const int slot = ctx->cur * 2 + refresh;
+    if (!ctx->gexec[slot]) {
+      const pf_status cs = capture_step<T>(ctx, ctx->cur, refresh, &ctx->gexec[slot]);
+      if (cs != PF_OK) {
+        *st = cs;
+        return true;
+      }
+    }
+    const cudaError_t e = cudaGraphLaunch(ctx->gexec[slot], ctx->stream);
     if (e != cudaSuccess) {
       *st = ctx->cuda_fail(e, "cudaGraphLaunch");
       return true;
     }
-    ctx->cur ^= 1;
+    int64_t fixed = 0, per_iter = 0;
+    step_kernel_counts(ctx, refresh, &fixed, &per_iter);
+    ctx->graph_fixed += fixed;
+    ctx->graph_steps += 1;
+    if (!heun) ctx->cur ^= 1;
+    ctx->nstep += 1;
   }
-  ctx->graph_steps += nsteps;
   return true;
 }
 
@@ -651,20 +703,38 @@ pf_status run_steps(pf_ctx* ctx, int nsteps) {
   const Geo& g = ctx->geo;
   T* Pbuf[2] = {(T*)ctx->P_user, (T*)(ctx->ws + ctx->lay.P_alt)};
   const double coef[5] = {ctx->prm.a1, ctx->prm.a11, ctx->prm.a12, ctx->prm.g, ctx->prm.dt * ctx->prm.L};
+  const bool heun = ctx->prm.integrator == PF_HEUN;
+  const double tdgl_bytes = 7.0 * (double)g.n * sizeof(T);
   pf_status gst;
   if (run_steps_graph<T>(ctx, nsteps, &gst)) {
     if (gst != PF_OK) return gst;
     nsteps = 0;
   }
   for (int s = 0; s < nsteps; ++s) {
+    const bool refresh = refresh_step(ctx);
     T* P = Pbuf[ctx->cur];
-    pf_status st = solve<T>(ctx, P);
-    if (st != PF_OK) return st;
+    T* Q = Pbuf[ctx->cur ^ 1];
+    if (refresh) {
+      pf_status st = solve<T>(ctx, P);
+      if (st != PF_OK) return st;
+    }
     before_launch(ctx);
-    pf::launch_tdgl<T>(ctx->L, g, d, P, Pbuf[ctx->cur ^ 1], coef);
-    after_launch(ctx, F_TDGL, 7.0 * (double)g.n * sizeof(T));
+    pf::launch_tdgl<T>(ctx->L, g, d, P, Q, coef, 0);
+    after_launch(ctx, F_TDGL, tdgl_bytes);
     PF_CUDA(cudaGetLastError());
-    ctx->cur ^= 1;
+    if (heun) {
+      if (refresh) {
+        pf_status st = solve<T>(ctx, Q);
+        if (st != PF_OK) return st;
+      }
+      before_launch(ctx);
+      pf::launch_tdgl<T>(ctx->L, g, d, Q, P, coef, 1);
+      after_launch(ctx, F_TDGL, tdgl_bytes + 3.0 * (double)g.n * sizeof(T));
+      PF_CUDA(cudaGetLastError());
+    } else {
+      ctx->cur ^= 1;
+    }
+    ctx->nstep += 1;
   }
   if (ctx->cur == 1) {
     PF_CUDA(cudaMemcpyAsync(Pbuf[0], Pbuf[1], sizeof(T) * 3 * (size_t)g.n, cudaMemcpyDeviceToDevice,
@@ -725,9 +795,9 @@ pf_status finish_info(pf_ctx* ctx, int nsteps, pf_step_info* info) {
     info->nonconverged = s.nonconv;
     info->status = result;
     int64_t fixed = 0, per_iter = 0;
-    graph_kernel_counts(ctx, &fixed, &per_iter);
+    step_kernel_counts(ctx, 1, &fixed, &per_iter);
     // graph-launched steps: kernels = fixed part + one loop body per iteration
-    info->kernel_launches = ctx->launches + (ctx->graph_steps ? ctx->graph_steps * fixed + s.total_iters * per_iter : 0);
+    info->kernel_launches = ctx->launches + (ctx->graph_steps ? ctx->graph_fixed + s.total_iters * per_iter : 0);
     info->graph_steps = ctx->graph_steps;
   }
   return result;
@@ -816,6 +886,7 @@ pf_status pf_bind(pf_ctx* ctx, void* P, void* phi, const void* eps, void* worksp
   ctx->eps = ctx->prm.has_eps ? eps : nullptr;
   ctx->ws = (char*)workspace;
   ctx->cur = 0;
+  ctx->nstep = 0;
   ctx->invd_dirty = true;
   const Layout& L = ctx->lay;
   PF_CUDA(cudaMemsetAsync(ctx->ws + L.tlo, 0, L.part - L.tlo, ctx->stream));
@@ -915,6 +986,8 @@ pf_status pf_adjoint_step(pf_ctx* ctx, const void* lam_in, void* lam_out, double
   pf_status st = check_ready(ctx);
   if (st != PF_OK) return st;
   if (!ctx->lay.adj) return ctx->fail(PF_ERR_STATE, "the context was created without PF_FLAG_ADJOINT");
+  if (ctx->prm.integrator != PF_EULER || ctx->prm.poisson_every > 1)
+    return ctx->fail(PF_ERR_NOTIMPL, "the adjoint step exists for forward Euler with a solve every step only");
   if (!lam_in || !lam_out || !grad_params) return ctx->fail(PF_ERR_ARG, "lam_in, lam_out and grad_params must be non-NULL");
   if (((uintptr_t)lam_in % 16) || ((uintptr_t)lam_out % 16))
     return ctx->fail(PF_ERR_ARG, "lam_in and lam_out must be 16-byte aligned");

@@ -70,9 +70,11 @@ template <typename T>
 void launch_cg_finish(const LaunchCfg& L, const Geo& g, const Dev<T>& d, int singular);
 template <typename T>
 void launch_sub_mean(const LaunchCfg& L, const Geo& g, const Dev<T>& d);
-// coef = {a1, a11, a12, g, dt*L}
+// coef = {a1, a11, a12, g, dt*L}.  corr = 1: predictor-corrector corrector
+// (P is the predicted state; Pn holds P_n on entry and P_{n+1} on exit).
 template <typename T>
-void launch_tdgl(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, T* Pn, const double* coef);
+void launch_tdgl(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, T* Pn, const double* coef,
+                 int corr = 0);
 template <typename T>
 void launch_invdiag(const LaunchCfg& L, const Geo& g, const Dev<T>& d);
 // Adjoint update (pf_adjoint.cu): lam_out from lam, the adjoint potential psi

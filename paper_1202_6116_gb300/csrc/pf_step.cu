@@ -8,6 +8,10 @@
 //           projection of singular problems).
 //   k_tdgl  P' = P + dt L (-df/dP + g Lap P + E), E = -grad phi from face values
 //           (Eq. TDGL with Eqs. F_bulk, dF_grad/dP, F_elec; Section Time Integration).
+//           CORR = true is the corrector of the predictor-corrector scheme: P is
+//           the predicted state P^p, and the output overwrites the state P_n it
+//           started from with (P_n + P^p + dt R(P^p)) / 2 = P_n + dt (R(P_n) +
+//           R(P^p)) / 2 (each thread reads its own cells of P_n before writing).
 //
 // Both read P (3 components) and phi with their 6 neighbours; the neighbours
 // come straight from the staged planes (march_direct).  Algorithmic traffic
@@ -163,7 +167,7 @@ struct P3 {
   T x, y, z;
 };
 
-template <typename T, int VX>
+template <typename T, bool CORR, int VX>
 __global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __restrict__ P, T* __restrict__ Pn,
                                                   const T* __restrict__ phi, Coef<T> k, Scalars* S, MarchCfg mc) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -211,6 +215,18 @@ __global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __r
       a[i] = ov[i].x;
       b[i] = ov[i].y;
       d[i] = ov[i].z;
+    }
+    if constexpr (CORR) {
+      T ca[VX], cb[VX], cd[VX];
+      load_n<T, VX>(Pn + c, ca);
+      load_n<T, VX>(Pn + g.n + c, cb);
+      load_n<T, VX>(Pn + 2 * g.n + c, cd);
+#pragma unroll
+      for (int i = 0; i < VX; ++i) {
+        a[i] = T(0.5) * (ca[i] + a[i]);
+        b[i] = T(0.5) * (cb[i] + b[i]);
+        d[i] = T(0.5) * (cd[i] + d[i]);
+      }
     }
     store_n<T, VX>(Pn + c, a);
     store_n<T, VX>(Pn + g.n + c, b);
@@ -269,27 +285,33 @@ void launch_rhs(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, c
   rhs_v<T, false>(L, g, d, P, cond, use_cond);
 }
 
-template <typename T, int VX>
+template <typename T, bool CORR, int VX>
 static void tdgl_t(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, T* Pn, const Coef<T>& k) {
   static bool f = false;
   const size_t bytes = StepPipe<T, false, VX>::bytes();
-  smem_attr(k_tdgl<T, VX>, bytes, f);
-  k_tdgl<T, VX><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(g, d.bc, P, Pn, d.phi, k, d.S, L.march);
+  smem_attr(k_tdgl<T, CORR, VX>, bytes, f);
+  k_tdgl<T, CORR, VX><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(g, d.bc, P, Pn, d.phi, k, d.S, L.march);
 }
 
 template <typename T>
-void launch_tdgl(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, T* Pn, const double* coef) {
+void launch_tdgl(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, T* Pn, const double* coef,
+                 int corr) {
   const Coef<T> k{T(coef[0]), T(coef[1]), T(coef[2]), T(coef[3]), T(coef[4])};
   constexpr int V = 16 / sizeof(T);
-  if (L.march.vx == V) tdgl_t<T, V>(L, g, d, P, Pn, k);
-  else tdgl_t<T, 1>(L, g, d, P, Pn, k);
+  if (corr) {
+    if (L.march.vx == V) tdgl_t<T, true, V>(L, g, d, P, Pn, k);
+    else tdgl_t<T, true, 1>(L, g, d, P, Pn, k);
+  } else {
+    if (L.march.vx == V) tdgl_t<T, false, V>(L, g, d, P, Pn, k);
+    else tdgl_t<T, false, 1>(L, g, d, P, Pn, k);
+  }
 }
 
 #define PF_STEP_INSTANTIATE(T)                                                                              \
   template void launch_rhs_mean<T>(const LaunchCfg&, const Geo&, const Dev<T>&, const T*);                  \
   template void launch_rhs<T>(const LaunchCfg&, const Geo&, const Dev<T>&, const T*,                        \
                               cudaGraphConditionalHandle, int);                                             \
-  template void launch_tdgl<T>(const LaunchCfg&, const Geo&, const Dev<T>&, const T*, T*, const double*);
+  template void launch_tdgl<T>(const LaunchCfg&, const Geo&, const Dev<T>&, const T*, T*, const double*, int);
 
 PF_STEP_INSTANTIATE(float)
 PF_STEP_INSTANTIATE(double)

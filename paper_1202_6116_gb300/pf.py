@@ -18,6 +18,7 @@ PF_FP64, PF_FP32 = 0, 1
 PF_PCG_JACOBI, PF_PCG_MG = 0, 1
 PF_ZLO, PF_ZHI = 0, 1
 PF_NEUMANN, PF_DIRICHLET = 0, 1
+PF_EULER, PF_HEUN = 0, 1
 PF_FLAG_NO_GRAPHS = 1
 PF_FLAG_ADJOINT = 2
 
@@ -37,7 +38,8 @@ class pf_params(C.Structure):
                 ("precision", C.c_int32), ("solver", C.c_int32),
                 ("poisson_rtol", C.c_double), ("poisson_maxit", C.c_int32),
                 ("periodic_z", C.c_int32), ("has_eps", C.c_int32), ("flags", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("integrator", C.c_int32), ("poisson_every", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class pf_step_info(C.Structure):
