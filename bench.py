@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 METRIC = "TDGL cell-steps/s incl. Poisson solve"
 UNIT = "cell-steps/s"
 L2_BYTES = 129 * 2 ** 20
-WORKLOADS = ("tip", "strips", "grounded")
+WORKLOADS = ("tip", "strips", "grounded", "batch")
 
 
 def make_workload(name, seed_offset=0, solver=None, size=None):
@@ -292,6 +292,97 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------- batched film sweep
+
+def run_batch(args):
+    """64 independent FP32 films (32^3 .. 128x128x64, Jacobi-PCG to 1e-6,
+    triangular top-electrode ramps) advanced together: one CUDA graph launch
+    per batch step.  Tilings from the autotuner, per film shape."""
+    import numpy as np
+    import torch
+
+    from paper_1202_6116_gb300 import autotune as AT
+    from paper_1202_6116_gb300 import build as B
+    from paper_1202_6116_gb300 import pf
+    from paper_1202_6116_gb300 import workloads as W
+    from paper_1202_6116_gb300.batch import Batch
+    from paper_1202_6116_gb300.film import Film
+
+    B.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ws = W.film_batch_hysteresis(nfilms=args.films, seed=4, steps=args.steps + args.warmup)
+    t0 = time.perf_counter()
+    tuned = {}
+    for w in ws:
+        k = AT.key_of(w)
+        if k not in tuned:
+            tuned[k] = AT.tune(w, steps=3, warmup=1, device=dev)
+    tune_s = time.perf_counter() - t0
+    films = [Film(w, device=dev) for w in ws]
+    for f in films:
+        AT.apply(f, tuned[AT.key_of(f.w)])
+    record_every = 10
+    b = Batch(films, max_records=(args.steps + args.warmup) // record_every + 1, record_every=record_every)
+    for i, w in enumerate(ws):
+        b.set_ramp(i, pf.PF_ZHI, *w.extra["ramp"])
+    stream = films[0].stream
+    b.step(args.warmup)
+    clocks = ClockSampler(0)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st, info = b.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    cells = sum(w.n for w in ws)
+    loops = b.loops()
+    b.close()
+    # the same films stepped one after another (one graph launch per film and step)
+    seq_steps = max(1, min(10, args.steps))
+    torch.cuda.synchronize(dev)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    seq_iters = 0
+    for _ in range(seq_steps):
+        for f in films:
+            _, fi = f.step(1, ok=(pf.PF_OK, pf.PF_ERR_NOCONV))
+            seq_iters += fi["total_iters"]
+    s1.record(stream)
+    s1.synchronize()
+    seq_ms = s0.elapsed_time(s1)
+    for f in films:
+        f.close()
+    value = cells * args.steps / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded SplitMix64 initial states and ramp draws)",
+            "config": {"workload": "batch of %d FP32 films (32^3, 64x64x32, 96x96x48, 128x128x64 drawn with "
+                                   "seed 4), grounded bottom, ramped top electrode, Jacobi-PCG rtol=1e-06 dt=0.01"
+                                   % len(ws), "cells": cells, "films": len(ws),
+                       "l2": "inputs larger than L2 (%.2f GB of film state)" % (cells * 4 * 11 / 1e9)},
+            "poisson_iters_per_step": info["total_iters"] / args.steps / len(ws),
+            "gpu_launches": info["kernel_launches"], "status": pf.STATUS_NAMES[st],
+            "sequential_ms_per_step": seq_ms / seq_steps,
+            "sequential_iters_per_film_step": seq_iters / seq_steps / len(ws),
+            "batch_speedup_vs_sequential": round((seq_ms / seq_steps) / (ms / args.steps), 3),
+            "autotune": {k: {"vx": v["vx"], "tz": v["tz"], "blocks_per_sm": v["blocks_per_sm"],
+                             "us_per_iter": round(1e3 * v["ms_per_iter"], 2),
+                             "default_us_per_iter": round(1e3 * v["default_ms_per_iter"], 2)}
+                         for k, v in tuned.items()},
+            "autotune_seconds": round(tune_s, 1),
+            "loop_records": int(loops.shape[0]),
+            "loop_example": {"film": 0, "volts": [round(x, 4) for x in loops[:, 0, 0][-5:].tolist()],
+                             "mean_pz": [round(x, 5) for x in loops[:, 0, 3][-5:].tolist()]},
+            "clocks": clk, "impl": "ours"}
+    print(json.dumps(line))
+
+
 # -------------------------------------------------------- FP32 against FP64
 
 def precision_check(dev, steps):
@@ -393,6 +484,7 @@ def main():
     ap.add_argument("--precision-steps", type=int, default=200,
                     help="steps of the FP32-against-FP64 comparison on the strip film (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--films", type=int, default=64, help="films of the batch workload")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel from the host (profilers cannot see kernels inside CUDA graphs "
                          "with conditional nodes)")
@@ -401,6 +493,10 @@ def main():
         args.steps = 5 if args.steps is None else args.steps
         args.warmup = 3 if args.warmup is None else args.warmup
         run_reference(args)
+    elif args.workload == "batch":
+        args.steps = 300 if args.steps is None else args.steps
+        args.warmup = 5 if args.warmup is None else max(3, args.warmup)
+        run_batch(args)
     else:
         args.steps = 30 if args.steps is None else args.steps
         args.warmup = 5 if args.warmup is None else max(3, args.warmup)

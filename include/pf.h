@@ -267,6 +267,83 @@ pf_status pf_solve_potential_noalloc(const pf_params* params, void* cuda_stream,
                                      const int8_t* type_lo, const double* volt_lo, const int8_t* type_hi,
                                      const double* volt_hi, pf_step_info* info);
 
+/* ------------------------------------------------------------------ tiling
+ * Tiling of the fine-grid plane-march kernels (Poisson right-hand side, CG
+ * operator, TDGL update, diagnostics, adjoint): the hook the autotuner uses.
+ * The paper has no counterpart (its code tiles by MPI subdomain). */
+typedef struct {
+  int32_t vx;                /* cells per thread along x: 1, or 16 bytes of cells (4 in
+                                FP32, 2 in FP64; then nx must be a multiple of it).
+                                A block is 16 x 16 threads: tiles of 16 vx x 16 columns */
+  int32_t tz;                /* z planes per tile (z-block depth), 1 .. 64 */
+  int32_t blocks_per_sm;     /* resident blocks per SM the grid is sized for
+                                (0: as many as fit); tiles are handed out dynamically */
+  int32_t reserved;          /* must be zero */
+} pf_tiling;
+
+/* Current tiling (the default picks vx = 16 bytes when nx allows it and the
+ * deepest tz that still gives about three tiles per resident block). */
+pf_status pf_get_tiling(const pf_ctx* ctx, pf_tiling* out);
+
+/* Replace the tiling; results are unchanged up to the order of the reduction
+ * sums (dot products and norms are summed per tile).  Drops captured graphs. */
+pf_status pf_set_tiling(pf_ctx* ctx, const pf_tiling* tiling);
+
+/* ------------------------------------------------------------------- batch
+ * Many independent films advanced together: every batch step is ONE CUDA
+ * graph launch holding, per film, its whole time step (its device-driven
+ * Krylov loops included) as an independent branch, so small films run
+ * concurrently and fill the GPU.  Before the branches one kernel applies the
+ * films' electrode voltage ramps; after them one kernel records the
+ * polarization-voltage loops (the switching observable of Section Results).
+ * The films keep their own contexts, buffers and boundary masks; the batch
+ * borrows them.  All films must use the same CUDA stream, integrator and
+ * poisson_every, and be at the same step since pf_bind.  The paper runs one
+ * film per job; the batch is this library's throughput mode. */
+typedef struct pf_batch pf_batch;
+
+/* Device workspace of a batch of nfilms films keeping up to max_records loop
+ * records (0 on invalid arguments). */
+size_t pf_batch_workspace_bytes(int32_t nfilms, int64_t max_records);
+
+/* Create a batch over films[0 .. nfilms-1] (bound contexts, borrowed: keep
+ * them alive until pf_batch_destroy).  workspace: device, 256-byte aligned,
+ * pf_batch_workspace_bytes bytes, owned by the caller.  A loop record is
+ * taken after every record_every-th batch step (>= 1).  No ramps at first. */
+pf_status pf_batch_create(pf_ctx* const* films, int32_t nfilms, void* workspace, size_t workspace_bytes,
+                          int64_t max_records, int32_t record_every, pf_batch** out);
+
+/* Drive face PF_ZLO or PF_ZHI of film i by a triangular voltage ramp: during
+ * batch step s (counted from pf_batch_create) every electrode cell of that
+ * face is at V(s) = amplitude * tri(s / period), with tri the unit triangle
+ * wave (tri(0) = 0, tri(1/4) = 1, tri(3/4) = -1, period 1).  period in steps
+ * (> 0); period = 0 removes the ramp (the face keeps its last voltages).  One
+ * ramped face per film. */
+pf_status pf_batch_set_ramp(pf_batch* batch, int32_t film, int32_t face, double amplitude, double period);
+
+/* Advance every film by nsteps steps (blocks until done).  info (may be
+ * NULL) sums the films' solver statistics (last_iters, last_relres: the
+ * largest over the films); the result is the worst film status
+ * (PF_ERR_NONFINITE before PF_ERR_NOCONV before PF_OK). */
+pf_status pf_batch_step(pf_batch* batch, int32_t nsteps, pf_step_info* info);
+
+/* Statistics of film i over the last pf_batch_step call. */
+pf_status pf_batch_film_info(const pf_batch* batch, int32_t film, pf_step_info* info);
+
+/* Copy the loop records to host memory: out[(r * nfilms + i) * 4 + k] for
+ * record r of film i, k = 0: the ramp voltage V(s) applied during the
+ * recorded step s (0 without a ramp), k = 1..3: mean P_x, P_y, P_z after
+ * it.  At most max_out records are copied; *nrecords receives the number
+ * stored (records beyond the batch's max_records are not kept). */
+pf_status pf_batch_read_loops(pf_batch* batch, double* out, int64_t max_out, int64_t* nrecords);
+
+/* Release the batch (not the films or the workspace).  Safe on NULL. */
+pf_status pf_batch_destroy(pf_batch* batch);
+
+/* Message of the last failing call on this batch ("" if none); with batch =
+ * NULL, the message of the last failing pf_batch_create. */
+const char* pf_batch_last_error(const pf_batch* batch);
+
 /* Release the context (not the bound buffers).  Safe on NULL. */
 pf_status pf_destroy(pf_ctx* ctx);
 

@@ -212,6 +212,8 @@ struct pf_ctx {
   int64_t graph_steps = 0;        // steps of the current call run as graphs
   int64_t graph_fixed = 0;        // kernels of those steps outside the Krylov loops
   int64_t nstep = 0;              // steps since pf_bind (schedules poisson_every)
+  uint64_t gen = 0;               // bumped by every change that invalidates captured graphs
+  int tile_bps = 0;               // blocks per SM requested by pf_set_tiling (0: as many as fit)
   cudaStream_t cap_stream = nullptr;
 
   // Profiling: events recorded between consecutive launches; each record
@@ -881,6 +883,7 @@ pf_status pf_bind(pf_ctx* ctx, void* P, void* phi, const void* eps, void* worksp
       (ctx->prm.has_eps && !is_device_ptr(eps)))
     return ctx->fail(PF_ERR_ARG, "P, phi, eps and workspace must be device pointers");
   drop_graphs(ctx);
+  ctx->gen += 1;
   ctx->P_user = P;
   ctx->phi = phi;
   ctx->eps = ctx->prm.has_eps ? eps : nullptr;
@@ -935,6 +938,7 @@ pf_status pf_set_bc(pf_ctx* ctx, int32_t face, const int8_t* type_xy, const doub
   std::memcpy(h.data(), type_xy, nxy);
   recompute_singular(ctx);
   ctx->invd_dirty = true;
+  ctx->gen += 1;
   return upload_masks(ctx);
 }
 
@@ -1079,6 +1083,44 @@ int32_t pf_profile_read(const pf_ctx* ctx, pf_kernel_stat* out, int32_t max) {
   return n;
 }
 
+
+pf_status pf_get_tiling(const pf_ctx* ctx, pf_tiling* out) {
+  if (!ctx) return PF_ERR_ARG;
+  if (!out) return const_cast<pf_ctx*>(ctx)->fail(PF_ERR_ARG, "out is NULL");
+  out->vx = ctx->L.march.vx;
+  out->tz = ctx->L.march.tz;
+  out->blocks_per_sm = ctx->tile_bps;
+  out->reserved = 0;
+  return PF_OK;
+}
+
+pf_status pf_set_tiling(pf_ctx* ctx, const pf_tiling* t) {
+  if (!ctx) return PF_ERR_ARG;
+  if (!t) return ctx->fail(PF_ERR_ARG, "tiling is NULL");
+  const int fp32 = ctx->prm.precision == PF_FP32;
+  const int vmax = fp32 ? 4 : 2;
+  if (t->vx != 1 && t->vx != vmax) return ctx->fail(PF_ERR_ARG, "vx must be 1 or %d", vmax);
+  if (t->vx > 1 && ctx->prm.nx % t->vx != 0) return ctx->fail(PF_ERR_ARG, "nx is not a multiple of vx = %d", t->vx);
+  if (t->tz < 1 || t->tz > 64) return ctx->fail(PF_ERR_ARG, "tz must be in 1 .. 64");
+  if (t->blocks_per_sm < 0 || t->blocks_per_sm > 64) return ctx->fail(PF_ERR_ARG, "blocks_per_sm must be in 0 .. 64");
+  if (t->reserved != 0) return ctx->fail(PF_ERR_ARG, "reserved must be zero");
+  const Geo& g = ctx->geo;
+  const int occ = pf::march_blocks_per_sm(fp32, ctx->prm.has_eps);
+  const int bps = t->blocks_per_sm > 0 ? std::min(t->blocks_per_sm, occ) : occ;
+  pf::MarchCfg m{};
+  m.vx = t->vx;
+  m.tiles_x = (g.nx + pf::MTX * m.vx - 1) / (pf::MTX * m.vx);
+  m.tiles_y = (g.ny + pf::MTY - 1) / pf::MTY;
+  m.tz = std::min(t->tz, g.nz);
+  m.ntiles = (long long)m.tiles_x * m.tiles_y * ((g.nz + m.tz - 1) / m.tz);
+  m.grid = (int)std::min<long long>(m.ntiles, std::min<long long>(pf::MAX_GRID, (long long)bps * ctx->nsm));
+  drop_graphs(ctx);
+  ctx->L.march = m;
+  ctx->tile_bps = t->blocks_per_sm;
+  ctx->gen += 1;
+  return PF_OK;
+}
+
 pf_status pf_destroy(pf_ctx* ctx) {
   if (!ctx) return PF_OK;
   drop_graphs(ctx);
@@ -1092,6 +1134,342 @@ pf_status pf_destroy(pf_ctx* ctx) {
 const char* pf_last_error(const pf_ctx* ctx) {
   if (!ctx) return g_create_error;
   return ctx->err.c_str();
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batch
+
+struct pf_batch {
+  std::vector<pf_ctx*> films;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  char* ws = nullptr;
+  size_t off_state = 0, off_table = 0, off_part = 0, off_hist = 0;
+  int64_t max_records = 0;
+  int record_every = 1;
+  long long max_nxy = 0;
+  std::vector<pf::BatchFilm> table;
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<uint64_t> gen;         // film generations the graphs were captured for
+  std::vector<pf_step_info> infos;
+  std::string err;
+
+  pf_status fail(pf_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    err = buf;
+    return st;
+  }
+};
+
+namespace {
+
+thread_local char g_batch_error[512];
+
+struct BatchLayout {
+  size_t state, table, part, hist, total;
+};
+
+BatchLayout batch_layout(int nfilms, int64_t max_records) {
+  BatchLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align_up(bytes);
+    return o;
+  };
+  L.state = take(sizeof(pf::BatchState));
+  L.table = take(sizeof(pf::BatchFilm) * (size_t)nfilms);
+  L.part = take(sizeof(double) * 3 * pf::BATCH_REC_BLOCKS * (size_t)nfilms);
+  L.hist = take(sizeof(double) * 4 * (size_t)nfilms * (size_t)max_records);
+  L.total = off;
+  return L;
+}
+
+void batch_drop_graphs(pf_batch* b) {
+  for (cudaGraphExec_t& e : b->gexec) {
+    if (e) cudaGraphExecDestroy(e);
+    e = nullptr;
+  }
+}
+
+pf_status batch_upload_table(pf_batch* b) {
+  if (cudaMemcpyAsync(b->ws + b->off_table, b->table.data(), sizeof(pf::BatchFilm) * b->table.size(),
+                      cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    const cudaError_t e = cudaGetLastError();
+    return b->fail(PF_ERR_CUDA, "batch table upload: %s", cudaGetErrorString(e));
+  }
+  return PF_OK;
+}
+
+// One batch step as a graph: the ramp kernel, every film's step as an
+// independent branch after it, the loop record after all of them.
+pf_status batch_capture(pf_batch* b, int cur, int refresh, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  const pf::BatchFilm* table = (const pf::BatchFilm*)(b->ws + b->off_table);
+  pf::BatchState* bs = (pf::BatchState*)(b->ws + b->off_state);
+  const int nf = (int)b->films.size();
+  auto segment = [&](std::vector<cudaGraphNode_t>& deps, auto&& body) {
+    if (e != cudaSuccess) return;
+    e = cudaStreamBeginCaptureToGraph(b->cap, graph, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                                      mode);
+    if (e != cudaSuccess) return;
+    body();
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* fr = nullptr;
+    size_t nfr = 0;
+    e = cudaStreamGetCaptureInfo(b->cap, &cs, nullptr, nullptr, &fr, nullptr, &nfr);
+    if (e == cudaSuccess) deps.assign(fr, fr + nfr);
+    cudaGraph_t g_out = graph;
+    const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g_out);
+    if (e == cudaSuccess) e = e2;
+  };
+  std::vector<cudaGraphNode_t> ramp;
+  segment(ramp, [&] { pf::launch_batch_ramp(table, nf, b->max_nxy, bs, b->cap); });
+  std::vector<cudaGraphNode_t> joined;
+  for (pf_ctx* c : b->films) {
+    if (e != cudaSuccess) break;
+    std::vector<cudaGraphNode_t> deps = ramp;
+    e = c->prm.precision == PF_FP32 ? append_step<float>(c, graph, deps, cur, refresh, b->cap)
+                                    : append_step<double>(c, graph, deps, cur, refresh, b->cap);
+    joined.insert(joined.end(), deps.begin(), deps.end());
+  }
+  const int buf = b->films[0]->prm.integrator == PF_HEUN ? cur : cur ^ 1;
+  double* part = (double*)(b->ws + b->off_part);
+  double* hist = (double*)(b->ws + b->off_hist);
+  segment(joined, [&] { pf::launch_batch_record(table, nf, buf, bs, part, hist, b->cap); });
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return b->fail(PF_ERR_CUDA, "batch graph capture: %s", cudaGetErrorString(e));
+  }
+  *out = exec;
+  return PF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pf_batch_workspace_bytes(int32_t nfilms, int64_t max_records) {
+  if (nfilms < 1 || max_records < 0) return 0;
+  return batch_layout(nfilms, max_records).total;
+}
+
+pf_status pf_batch_create(pf_ctx* const* films, int32_t nfilms, void* workspace, size_t workspace_bytes,
+                          int64_t max_records, int32_t record_every, pf_batch** out) {
+  auto gfail = [&](pf_status st, const char* m) {
+    std::snprintf(g_batch_error, sizeof(g_batch_error), "%s", m);
+    return st;
+  };
+  if (!out) return gfail(PF_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!films || nfilms < 1) return gfail(PF_ERR_ARG, "need at least one film");
+  if (max_records < 0 || record_every < 1) return gfail(PF_ERR_ARG, "max_records must be >= 0, record_every >= 1");
+  const BatchLayout L = batch_layout(nfilms, max_records);
+  if (!workspace || workspace_bytes < L.total) return gfail(PF_ERR_ARG, "workspace missing or too small");
+  if (((uintptr_t)workspace % ALIGN) != 0) return gfail(PF_ERR_ARG, "workspace must be 256-byte aligned");
+  if (!is_device_ptr(workspace)) return gfail(PF_ERR_ARG, "workspace must be a device pointer");
+  for (int i = 0; i < nfilms; ++i) {
+    pf_ctx* c = films[i];
+    if (!c || !c->bound) return gfail(PF_ERR_ARG, "every film must be a bound context");
+    for (int j = 0; j < i; ++j)
+      if (films[j] == c) return gfail(PF_ERR_ARG, "a film appears twice");
+    const pf_ctx* f0 = films[0];
+    if (c->stream != f0->stream) return gfail(PF_ERR_ARG, "all films must use the same CUDA stream");
+    if (c->prm.integrator != f0->prm.integrator || std::max(1, c->prm.poisson_every) != std::max(1, f0->prm.poisson_every))
+      return gfail(PF_ERR_ARG, "all films must use the same integrator and poisson_every");
+    if (c->nstep != f0->nstep || c->cur != 0) return gfail(PF_ERR_STATE, "all films must be at the same step");
+  }
+  pf_batch* b = new pf_batch();
+  b->films.assign(films, films + nfilms);
+  b->stream = films[0]->stream;
+  b->ws = (char*)workspace;
+  b->off_state = L.state;
+  b->off_table = L.table;
+  b->off_part = L.part;
+  b->off_hist = L.hist;
+  b->max_records = max_records;
+  b->record_every = record_every;
+  b->gen.assign(nfilms, 0);
+  b->infos.assign(nfilms, pf_step_info{});
+  b->table.resize(nfilms);
+  for (int i = 0; i < nfilms; ++i) {
+    pf_ctx* c = films[i];
+    pf::BatchFilm& f = b->table[i];
+    f = pf::BatchFilm{};
+    f.P[0] = c->P_user;
+    f.P[1] = c->ws + c->lay.P_alt;
+    f.volt = nullptr;
+    f.n = c->geo.n;
+    f.nxy = c->geo.nxy;
+    f.amp = 0.0;
+    f.period = 1.0;
+    f.fp32 = c->prm.precision == PF_FP32;
+    b->max_nxy = std::max(b->max_nxy, (long long)c->geo.nxy);
+  }
+  pf::BatchState st{};
+  st.record_every = record_every;
+  st.max_records = max_records;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->ws + b->off_state, &st, sizeof(st), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    std::snprintf(g_batch_error, sizeof(g_batch_error), "CUDA: %s", cudaGetErrorString(e));
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return PF_ERR_CUDA;
+  }
+  if (batch_upload_table(b) != PF_OK) {
+    std::snprintf(g_batch_error, sizeof(g_batch_error), "%s", b->err.c_str());
+    cudaStreamDestroy(b->cap);
+    delete b;
+    return PF_ERR_CUDA;
+  }
+  *out = b;
+  return PF_OK;
+}
+
+pf_status pf_batch_set_ramp(pf_batch* b, int32_t film, int32_t face, double amplitude, double period) {
+  if (!b) return PF_ERR_ARG;
+  if (film < 0 || film >= (int)b->films.size()) return b->fail(PF_ERR_ARG, "film index out of range");
+  if (face != PF_ZLO && face != PF_ZHI) return b->fail(PF_ERR_ARG, "face must be PF_ZLO or PF_ZHI");
+  if (!std::isfinite(amplitude) || !std::isfinite(period) || period < 0.0)
+    return b->fail(PF_ERR_ARG, "amplitude must be finite and period >= 0");
+  pf_ctx* c = b->films[film];
+  pf::BatchFilm& f = b->table[film];
+  if (period == 0.0) {
+    f.volt = nullptr;
+  } else {
+    f.volt = c->ws + (face == PF_ZLO ? c->lay.vlo : c->lay.vhi);
+    f.amp = amplitude;
+    f.period = period;
+  }
+  return batch_upload_table(b);
+}
+
+pf_status pf_batch_step(pf_batch* b, int32_t nsteps, pf_step_info* info) {
+  if (!b) return PF_ERR_ARG;
+  if (nsteps < 0) return b->fail(PF_ERR_ARG, "nsteps must be >= 0");
+  const int nf = (int)b->films.size();
+  pf_ctx* f0 = b->films[0];
+  for (pf_ctx* c : b->films) {
+    if (!c->bound) return b->fail(PF_ERR_STATE, "a film is no longer bound");
+    if (c->nstep != f0->nstep || c->cur != 0) return b->fail(PF_ERR_STATE, "films are no longer at the same step");
+  }
+  bool stale = false;
+  for (int i = 0; i < nf; ++i) stale |= b->gen[i] != b->films[i]->gen;
+  if (stale) {
+    batch_drop_graphs(b);
+    for (int i = 0; i < nf; ++i) b->gen[i] = b->films[i]->gen;
+  }
+  for (pf_ctx* c : b->films) {
+    pf_status st = reset_scalars(c);
+    if (st != PF_OK) return b->fail(st, "film: %s", c->err.c_str());
+    if (c->prm.has_eps && c->invd_dirty) {
+      if (c->prm.precision == PF_FP32) pf::launch_invdiag<float>(c->L, c->geo, dev_view<float>(c));
+      else pf::launch_invdiag<double>(c->L, c->geo, dev_view<double>(c));
+      c->launches += 1;
+      c->invd_dirty = false;
+    }
+  }
+  const bool heun = f0->prm.integrator == PF_HEUN;
+  for (int s = 0; s < nsteps; ++s) {
+    const int refresh = refresh_step(f0) ? 1 : 0;
+    const int cur = f0->cur;
+    const int slot = cur * 2 + refresh;
+    if (!b->gexec[slot]) {
+      pf_status st = batch_capture(b, cur, refresh, &b->gexec[slot]);
+      if (st != PF_OK) return st;
+    }
+    const cudaError_t e = cudaGraphLaunch(b->gexec[slot], b->stream);
+    if (e != cudaSuccess) return b->fail(PF_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+    for (pf_ctx* c : b->films) {
+      int64_t fixed = 0, per_iter = 0;
+      step_kernel_counts(c, refresh, &fixed, &per_iter);
+      c->graph_fixed += fixed;
+      c->graph_steps += 1;
+      if (!heun) c->cur ^= 1;
+      c->nstep += 1;
+    }
+  }
+  pf_status worst = PF_OK;
+  pf_step_info sum{};
+  sum.steps_done = nsteps;
+  for (int i = 0; i < nf; ++i) {
+    pf_ctx* c = b->films[i];
+    if (c->cur == 1) {
+      const size_t w = c->prm.precision == PF_FP32 ? 4 : 8;
+      if (cudaMemcpyAsync(c->P_user, c->ws + c->lay.P_alt, 3 * (size_t)c->geo.n * w, cudaMemcpyDeviceToDevice,
+                          c->stream) != cudaSuccess)
+        return b->fail(PF_ERR_CUDA, "copy back: %s", cudaGetErrorString(cudaGetLastError()));
+      c->cur = 0;
+    }
+    pf_step_info& fi = b->infos[i];
+    fi = pf_step_info{};
+    const pf_status st = finish_info(c, nsteps, &fi);
+    if (st == PF_ERR_CUDA || st == PF_ERR_STATE) return b->fail(st, "film %d: %s", i, c->err.c_str());
+    if (st == PF_ERR_NONFINITE || (st == PF_ERR_NOCONV && worst == PF_OK)) worst = st;
+    sum.last_iters = std::max(sum.last_iters, fi.last_iters);
+    sum.total_iters += fi.total_iters;
+    sum.last_relres = std::max(sum.last_relres, fi.last_relres);
+    sum.nonconverged += fi.nonconverged;
+    sum.kernel_launches += fi.kernel_launches;
+    sum.graph_steps = nsteps;
+  }
+  sum.kernel_launches += 2LL * nsteps;   // the ramp and record kernels
+  sum.status = worst;
+  if (info) *info = sum;
+  if (worst != PF_OK) b->fail(worst, "%s", worst == PF_ERR_NONFINITE ? "a film went non-finite" : "a Poisson solve hit poisson_maxit");
+  return worst;
+}
+
+pf_status pf_batch_film_info(const pf_batch* b, int32_t film, pf_step_info* info) {
+  if (!b || !info || film < 0 || film >= (int)b->films.size()) return PF_ERR_ARG;
+  *info = b->infos[film];
+  return PF_OK;
+}
+
+pf_status pf_batch_read_loops(pf_batch* b, double* out, int64_t max_out, int64_t* nrecords) {
+  if (!b) return PF_ERR_ARG;
+  if (!nrecords || max_out < 0 || (max_out > 0 && !out)) return b->fail(PF_ERR_ARG, "bad output arguments");
+  pf::BatchState st{};
+  cudaError_t e = cudaMemcpyAsync(&st, b->ws + b->off_state, sizeof(st), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return b->fail(PF_ERR_CUDA, "read loops: %s", cudaGetErrorString(e));
+  const int64_t stored = std::min<int64_t>(st.records, b->max_records);
+  const int64_t n = std::min<int64_t>(stored, max_out);
+  const size_t bytes = sizeof(double) * 4 * b->films.size() * (size_t)n;
+  if (bytes) {
+    e = cudaMemcpyAsync(out, b->ws + b->off_hist, bytes, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return b->fail(PF_ERR_CUDA, "read loops: %s", cudaGetErrorString(e));
+  }
+  *nrecords = stored;
+  return PF_OK;
+}
+
+pf_status pf_batch_destroy(pf_batch* b) {
+  if (!b) return PF_OK;
+  batch_drop_graphs(b);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+  return PF_OK;
+}
+
+const char* pf_batch_last_error(const pf_batch* b) {
+  if (!b) return g_batch_error;
+  return b->err.c_str();
 }
 
 }  // extern "C"

@@ -89,6 +89,33 @@ void launch_tdgl_adj(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T*
 template <typename T>
 void launch_diag(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, const double* coef, double* out);
 
+// One film of a batch as the batch kernels see it (device table).
+struct BatchFilm {
+  const void* P[2];        // the film's two polarization buffers (3N each)
+  void* volt;              // voltages of the ramped z face (nullptr: no ramp)
+  long long n, nxy;
+  double amp, period;      // V(s) = amp tri(s / period), s = batch step
+  int fp32;
+  int pad;
+};
+
+// Device state of a batch (in the batch workspace).
+struct BatchState {
+  long long step;          // batch steps completed
+  long long records;       // loop records written (or dropped beyond max_records)
+  long long record_every;
+  long long max_records;
+  unsigned ticket;
+  unsigned pad;
+};
+
+constexpr int BATCH_REC_BLOCKS = 16;   // blocks per film of the loop record
+
+void launch_batch_ramp(const BatchFilm* films, int nfilms, long long max_nxy, const BatchState* bs,
+                       cudaStream_t st);
+void launch_batch_record(const BatchFilm* films, int nfilms, int buf, BatchState* bs, double* part, double* hist,
+                         cudaStream_t st);
+
 // Tiling of a plane-march launch on an nx x ny x nz grid: the deepest z
 // chunk that still gives about three tiles per resident block.
 // Resident plane-march blocks (MTX x MTY threads) per SM for this precision.

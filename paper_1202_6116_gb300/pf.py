@@ -28,7 +28,9 @@ STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_CUDA", 3: "PF_ERR_NOCONV
 # Every symbol the header declares.
 EXPORTS = ["pf_workspace_bytes", "pf_create", "pf_bind", "pf_set_bc", "pf_step", "pf_step_host",
            "pf_solve_potential", "pf_adjoint_step", "pf_diagnostics", "pf_profile_enable", "pf_profile_read", "pf_destroy",
-           "pf_last_error", "pf_solve_potential_noalloc"]
+           "pf_last_error", "pf_solve_potential_noalloc", "pf_get_tiling", "pf_set_tiling",
+           "pf_batch_workspace_bytes", "pf_batch_create", "pf_batch_set_ramp", "pf_batch_step",
+           "pf_batch_film_info", "pf_batch_read_loops", "pf_batch_destroy", "pf_batch_last_error"]
 
 
 class pf_params(C.Structure):
@@ -54,6 +56,10 @@ class pf_step_info(C.Structure):
 class pf_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("idle_launches", C.c_int64),
                 ("total_ms", C.c_double), ("bytes", C.c_double)]
+
+
+class pf_tiling(C.Structure):
+    _fields_ = [("vx", C.c_int32), ("tz", C.c_int32), ("blocks_per_sm", C.c_int32), ("reserved", C.c_int32)]
 
 
 class PfError(RuntimeError):
@@ -99,6 +105,26 @@ def lib():
         L.pf_solve_potential_noalloc.restype = i32
         L.pf_solve_potential_noalloc.argtypes = [C.POINTER(pf_params), vp, vp, vp, vp, vp, vp, vp,
                                                  C.POINTER(pf_step_info)]
+        L.pf_get_tiling.restype = i32
+        L.pf_get_tiling.argtypes = [vp, C.POINTER(pf_tiling)]
+        L.pf_set_tiling.restype = i32
+        L.pf_set_tiling.argtypes = [vp, C.POINTER(pf_tiling)]
+        L.pf_batch_workspace_bytes.restype = sz
+        L.pf_batch_workspace_bytes.argtypes = [i32, C.c_int64]
+        L.pf_batch_create.restype = i32
+        L.pf_batch_create.argtypes = [vp, i32, vp, sz, C.c_int64, i32, C.POINTER(vp)]
+        L.pf_batch_set_ramp.restype = i32
+        L.pf_batch_set_ramp.argtypes = [vp, i32, i32, C.c_double, C.c_double]
+        L.pf_batch_step.restype = i32
+        L.pf_batch_step.argtypes = [vp, i32, C.POINTER(pf_step_info)]
+        L.pf_batch_film_info.restype = i32
+        L.pf_batch_film_info.argtypes = [vp, i32, C.POINTER(pf_step_info)]
+        L.pf_batch_read_loops.restype = i32
+        L.pf_batch_read_loops.argtypes = [vp, vp, C.c_int64, C.POINTER(C.c_int64)]
+        L.pf_batch_destroy.restype = i32
+        L.pf_batch_destroy.argtypes = [vp]
+        L.pf_batch_last_error.restype = C.c_char_p
+        L.pf_batch_last_error.argtypes = [vp]
         L.pf_destroy.restype = i32
         L.pf_destroy.argtypes = [vp]
         L.pf_last_error.restype = C.c_char_p
@@ -218,3 +244,67 @@ def pf_solve_potential_noalloc(params: pf_params, stream, P, phi, type_lo=None, 
 
 def pf_destroy(ctx):
     return lib().pf_destroy(ctx)
+
+
+def pf_get_tiling(ctx) -> pf_tiling:
+    t = pf_tiling()
+    check(lib().pf_get_tiling(ctx, C.byref(t)), ctx)
+    return t
+
+
+def pf_set_tiling(ctx, vx, tz, blocks_per_sm=0):
+    t = pf_tiling(int(vx), int(tz), int(blocks_per_sm), 0)
+    return check(lib().pf_set_tiling(ctx, C.byref(t)), ctx)
+
+
+def pf_batch_last_error(batch=None) -> str:
+    return lib().pf_batch_last_error(batch).decode()
+
+
+def _bcheck(status, batch=None, ok=(PF_OK,)):
+    if status not in ok:
+        raise PfError(status, pf_batch_last_error(batch))
+    return status
+
+
+def pf_batch_workspace_bytes(nfilms, max_records) -> int:
+    return lib().pf_batch_workspace_bytes(int(nfilms), int(max_records))
+
+
+def pf_batch_create(ctxs, workspace, workspace_bytes, max_records, record_every=1):
+    """ctxs: list of context handles.  Returns the batch handle (an int)."""
+    arr = (C.c_void_p * len(ctxs))(*ctxs)
+    b = C.c_void_p()
+    st = lib().pf_batch_create(C.cast(arr, C.c_void_p), len(ctxs), _addr(workspace), int(workspace_bytes),
+                               int(max_records), int(record_every), C.byref(b))
+    _bcheck(st, None)
+    return b.value
+
+
+def pf_batch_set_ramp(batch, film, face, amplitude, period):
+    return _bcheck(lib().pf_batch_set_ramp(batch, int(film), int(face), float(amplitude), float(period)), batch)
+
+
+def pf_batch_step(batch, nsteps, ok=(PF_OK,)):
+    info = pf_step_info()
+    st = lib().pf_batch_step(batch, int(nsteps), C.byref(info))
+    _bcheck(st, batch, ok)
+    return st, info
+
+
+def pf_batch_film_info(batch, film):
+    info = pf_step_info()
+    _bcheck(lib().pf_batch_film_info(batch, int(film), C.byref(info)), batch)
+    return info
+
+
+def pf_batch_read_loops(batch, out, max_out):
+    """out: float64 host array of at least max_out * nfilms * 4 entries.
+    Returns the number of records stored on the device."""
+    n = C.c_int64(0)
+    _bcheck(lib().pf_batch_read_loops(batch, _addr(out), int(max_out), C.byref(n)), batch)
+    return n.value
+
+
+def pf_batch_destroy(batch):
+    return lib().pf_batch_destroy(batch)

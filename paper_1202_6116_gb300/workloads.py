@@ -187,3 +187,49 @@ def film_adjoint_fp64(nx=128, ny=128, nz=32, steps=500, seed=3, v=2.0) -> Worklo
     tl, vl, th, vh = strip_electrodes(nx, ny, v)
     return Workload("fp64_adjoint_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, P0, tl, vl, th, vh,
                     dt=0.01, steps=steps, rtol=1e-12, precision="fp64", solver="pcg", seed=seed)
+
+
+# ------------------------------------------------------ batched hysteresis sweep
+
+BATCH_SHAPES = ((32, 32, 32), (64, 64, 32), (96, 96, 48), (128, 128, 64))
+
+
+def tri_wave(s):
+    """Unit triangle wave of period 1: 0 at 0, 1 at 1/4, -1 at 3/4 (the shape of
+    the electrode voltage ramps of a hysteresis sweep; an input schedule)."""
+    f = np.asarray(s, dtype=np.float64)
+    f = f - np.floor(f)
+    return np.where(f < 0.25, 4.0 * f, np.where(f < 0.75, 2.0 - 4.0 * f, 4.0 * f - 4.0))
+
+
+def ramp_volts(amplitude, period, step):
+    """Electrode voltage during step `step` of a triangular ramp."""
+    return float(amplitude * tri_wave(step / period))
+
+
+def batch_draws(nfilms=64, seed=4, shapes=BATCH_SHAPES):
+    """Per film: (grid shape, ramp amplitude A ~ U[1.5, 4.0], period T ~
+    U[500, 2000] steps), from stream `seed` (three draws per film)."""
+    u = uniform(seed, 3 * nfilms).reshape(nfilms, 3)
+    return [(shapes[min(int(u[i, 0] * len(shapes)), len(shapes) - 1)], 1.5 + 2.5 * u[i, 1],
+             500.0 + 1500.0 * u[i, 2]) for i in range(nfilms)]
+
+
+def film_batch_hysteresis(nfilms=64, seed=4, steps=4000, shapes=BATCH_SHAPES, precision="fp32",
+                          rtol=1e-6):
+    """Independent films of a batched hysteresis sweep.  Film i: grid drawn
+    uniformly from `shapes` (32^3, 64x64x32, 96x96x48, 128x128x64), the
+    grounded-film physics (P ~ U[-0.01, 0.01], stream seed * 1000 + i), a
+    grounded bottom electrode and a whole-face top electrode driven by the
+    ramp V(s) = A tri(s / T) with A ~ U[1.5, 4.0] and T ~ U[500, 2000] steps
+    (extra["ramp"] = (A, T)); dt 0.01, Jacobi-PCG to 1e-6.  The draws of
+    stream `seed` are (shape, A, T) per film."""
+    films = []
+    for i, ((nx, ny, nz), amp, period) in enumerate(batch_draws(nfilms, seed, shapes)):
+        fseed = seed * 1000 + i
+        P0 = random_film(nx, ny, nz, fseed)
+        tl, vl, th, vh = grounded_both(nx, ny)
+        films.append(Workload("batch%d_%dx%dx%d" % (i, nx, ny, nz), nx, ny, nz, P0, tl, vl, th, vh,
+                              dt=0.01, steps=steps, rtol=rtol, maxit=20000, precision=precision,
+                              solver="pcg", seed=fseed, extra={"ramp": (amp, period)}))
+    return films
