@@ -261,7 +261,7 @@ enum Fam {
 };
 const char* const FAM_NAMES[F_COUNT] = {"rhs_mean", "rhs",      "cg_p",     "cg_r",     "cg_finish",
                                         "sub_mean", "tdgl",     "invdiag",  "tdgl_adj", "diag",
-                                        "mg_pre",   "mg_rr",    "mg_coarse", "mg_post1", "mg_post2"};
+                                        "mg_pre",   "mg_rr",    "mg_bottom", "mg_post1", "mg_post2"};
 
 // Multigrid families are kept per level: family id F_COUNT + level * 5 + kind.
 int mg_fam(int kind, size_t level) { return F_COUNT + (int)level * 5 + (kind - F_MG_PRE); }
@@ -378,14 +378,31 @@ pf::MgView<T> mg_view(pf_ctx* ctx, size_t k) {
   return v;
 }
 
-// One V-cycle z = M^-1 r (number j of its solve, for the profiler).
+// First level of the one-block V-cycle tail: the first level after the
+// finest with at most MG_TAIL_CELLS cells, or the coarsest level (no tail)
+// when that leaves fewer than two levels for the tail.
+size_t mg_tail_start(const Layout& lay) {
+  const size_t nl = lay.mg.size();
+  size_t k0 = nl - 1;
+  for (size_t k = 1; k < nl; ++k)
+    if (lay.mg[k].n() <= pf::MG_TAIL_CELLS) {
+      k0 = k;
+      break;
+    }
+  if (k0 + 1 >= nl || nl - k0 > (size_t)pf::MG_TAIL_LEVELS) k0 = nl - 1;
+  return k0;
+}
+
+// One V-cycle z = M^-1 r (number j of its solve, for the profiler): one
+// kernel per phase down to level k0, the rest of the cycle in one block.
 template <typename T>
 void vcycle(pf_ctx* ctx, int j) {
   const size_t nl = ctx->lay.mg.size();
+  const size_t k0 = mg_tail_start(ctx->lay);
   const double w = sizeof(T);
   pf::Scalars* S = (pf::Scalars*)(ctx->ws + ctx->lay.S);
   double* part = (double*)(ctx->ws + ctx->lay.part);
-  for (size_t k = 0; k + 1 < nl; ++k) {
+  for (size_t k = 0; k < k0; ++k) {
     const pf::MgView<T> lv = mg_view<T>(ctx, k), cv = mg_view<T>(ctx, k + 1);
     const double N = (double)lv.g.n;
     before_launch(ctx);
@@ -394,13 +411,24 @@ void vcycle(pf_ctx* ctx, int j) {
     pf::launch_mg_rr<T>(ctx->L, lv, cv, S);
     after_launch(ctx, mg_fam(F_MG_RR, k), (2 + 1.0 / (lv.fx * lv.fy * lv.fz)) * N * w, 2, j);
   }
-  {
+  if (k0 + 1 < nl) {
+    pf::MgTail<T> t{};
+    t.nl = (int)(nl - k0);
+    double cells = 0.0;
+    for (size_t k = k0; k < nl; ++k) {
+      t.lv[k - k0] = mg_view<T>(ctx, k);
+      cells += (double)t.lv[k - k0].g.n;
+    }
+    before_launch(ctx);
+    pf::launch_mg_tail<T>(ctx->L, t, ctx->singular, S);
+    after_launch(ctx, mg_fam(F_MG_COARSE, k0), 2.0 * cells * w, 2, j);
+  } else {
     const pf::MgView<T> cv = mg_view<T>(ctx, nl - 1);
     before_launch(ctx);
     pf::launch_mg_coarse<T>(ctx->L, cv, ctx->singular, S);
     after_launch(ctx, mg_fam(F_MG_COARSE, nl - 1), 2.0 * (double)cv.g.n * w, 2, j);
   }
-  for (size_t k = nl - 1; k-- > 0;) {
+  for (size_t k = k0; k-- > 0;) {
     const pf::MgView<T> lv = mg_view<T>(ctx, k), cv = mg_view<T>(ctx, k + 1);
     const double N = (double)lv.g.n;
     before_launch(ctx);
@@ -533,7 +561,7 @@ bool refresh_step(const pf_ctx* ctx) {
 
 // Kernels of one step outside the Krylov loops, and per Krylov iteration.
 void step_kernel_counts(const pf_ctx* ctx, int refresh, int64_t* fixed, int64_t* per_iter) {
-  const int64_t vc = ctx->prm.solver == PF_PCG_MG ? 4 * ((int64_t)ctx->lay.mg.size() - 1) + 1 : 0;
+  const int64_t vc = ctx->prm.solver == PF_PCG_MG ? 4 * (int64_t)mg_tail_start(ctx->lay) + 1 : 0;
   const bool heun = ctx->prm.integrator == PF_HEUN;
   const int64_t per_solve = (ctx->singular ? 2 : 0) + 2 + vc;
   *fixed = (refresh ? (heun ? 2 : 1) * per_solve : 0) + (heun ? 2 : 1);

@@ -15,6 +15,8 @@ constexpr int MAX_GRID = 4096;   // reduction partials are sized for this many b
 constexpr int MAX_NV = 8;        // values reduced per block or tile
 constexpr int MG_MAX_LEVELS = 24;
 constexpr int MG_MAX_COARSE = 1024;   // cells of the coarsest multigrid level (one block)
+constexpr int MG_TAIL_CELLS = 4096;   // levels at most this large run in the one-block V-cycle tail
+constexpr int MG_TAIL_LEVELS = 16;
 
 struct LaunchCfg {
   int grid;            // simple per-cell kernels (TX x TY blocks over tiles)
@@ -52,6 +54,14 @@ struct MgView {
   T* e;               // correction (level 0: z = M^-1 r)
   T* et;              // second buffer of the Jacobi sweeps
   MarchCfg mc;
+};
+
+// The small levels of the V-cycle (lv[0] .. lv[nl - 1], the last one the
+// coarsest) handled by one block.
+template <typename T>
+struct MgTail {
+  MgView<T> lv[MG_TAIL_LEVELS];
+  int nl;
 };
 
 template <typename T>
@@ -188,6 +198,8 @@ template <typename T>
 void launch_mg_rr(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S);
 template <typename T>
 void launch_mg_coarse(const LaunchCfg& L, const MgView<T>& cv, int singular, Scalars* S);
+template <typename T>
+void launch_mg_tail(const LaunchCfg& L, const MgTail<T>& t, int singular, Scalars* S);
 template <typename T>
 void launch_mg_post1(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S);
 template <typename T>

@@ -42,10 +42,11 @@ template <int TXT, int TYT, int VX>
 __device__ __forceinline__ TileGeo<TXT, TYT, VX> tile_geo(const Geo& g, long long t, const MarchCfg& mc) {
   constexpr int BX = TXT * VX;
   TileGeo<TXT, TYT, VX> s;
-  const int ix = (int)(t % mc.tiles_x);
-  const long long r = t / mc.tiles_x;
-  const int iy = (int)(r % mc.tiles_y);
-  const int iz = (int)(r / mc.tiles_y);
+  const int tt = (int)t;                 // tile counts stay far below 2^31
+  const int ix = tt % mc.tiles_x;
+  const int r = tt / mc.tiles_x;
+  const int iy = r % mc.tiles_y;
+  const int iz = r / mc.tiles_y;
   const int x0 = ix * BX, y0 = iy * TYT;
   s.z0 = iz * mc.tz;
   s.z1 = min(s.z0 + mc.tz, g.nz);
@@ -203,11 +204,15 @@ __device__ __forceinline__ void sched_finish(const TileSched& ts) {
 
 // Coarse-grid parent of every fine cell (multigrid prolongation): the value
 // of field ec at (z/fz, y/fy, x/fx) of a grid with row nxc and plane nxyc.
+// The factors are 1 or 2, so the divisions are shifts by f - 1.
 template <typename T>
 struct ParentSrc {
   const T* ec;
   int fx, fy, fz, nxc;
   long long nxyc;
+  __device__ __forceinline__ long long at(int x, int y, int z) const {
+    return (long long)(z >> (fz - 1)) * nxyc + (long long)(y >> (fy - 1)) * nxc + (x >> (fx - 1));
+  }
 };
 
 // The staging ring of one tile: virtual plane v = 0 .. nt+1 is z0-1 .. z1
@@ -243,7 +248,7 @@ struct Stager {
   __device__ __forceinline__ int pslot(int i) const { return col + (i >> (par.fx - 1)); }
   // copy the parents of a vector starting at fine (x, y) of plane z into slot (rw, col)
   __device__ __forceinline__ void issue_parent_vec(int st, int rw, int x, int y, int z) const {
-    const T* src = par.ec + (long long)(z / par.fz) * par.nxyc + (long long)(y / par.fy) * par.nxc + x / par.fx;
+    const T* src = par.ec + par.at(x, y, z);
     if (par.fx == 2) {
       if constexpr (VX >= 2) cp_async<(VX / 2) * sizeof(T)>(PA(st, rw, col), src);
       else cp_async<sizeof(T)>(PA(st, rw, col), src);
@@ -252,8 +257,7 @@ struct Stager {
     }
   }
   __device__ __forceinline__ void issue_parent_one(int st, int rw, int cl, int x, int y, int z) const {
-    cp_async<sizeof(T)>(PA(st, rw, cl),
-                        par.ec + (long long)(z / par.fz) * par.nxyc + (long long)(y / par.fy) * par.nxc + x / par.fx);
+    cp_async<sizeof(T)>(PA(st, rw, cl), par.ec + par.at(x, y, z));
   }
   __device__ __forceinline__ int plane(int v) const { return v == 0 ? zlo : (v == nt + 1 ? zhi : s.z0 + v - 1); }
   __device__ __forceinline__ T* H(int st, int k, int rw, int cl) const {
@@ -358,10 +362,10 @@ __device__ __forceinline__ void march(const Geo& g, const TileGeo<TXT, TYT, VX>&
       fv[i] = val_at(h1, xy + i, z, colid, i, st, rw, NP > 0 ? sg.pslot(i) : 0, bt);
     }
   };
-  // Stencil field of plane v: own vector, plus the halo cells for in-tile planes.
-  auto form_t = [&](int v, int z, const bool bt) {
-    const int st = v % NS, b = v % 3;
-    F fv[VX];
+  // Stencil field of plane v (into field buffer b = v mod 3): own vector,
+  // plus the halo cells for in-tile planes.
+  auto form_t = [&](int v, int b, int z, F (&fv)[VX], const bool bt) {
+    const int st = v % NS;
     form_vec(st, row, col, s.xy, z, 0, fv, bt);
     store_n<F, VX>(PN(b, row, col), fv);
     if (v < 1 || v > nt) return;
@@ -377,39 +381,49 @@ __device__ __forceinline__ void march(const Geo& g, const TileGeo<TXT, TYT, VX>&
       *PN(b, row, OFF + s.w) = val_at(h1, s.xy_r, z, 2, 0, st, row, OFF + s.w, bt);
     }
     if (s.xy_t >= 0) {
-      form_vec(st, 0, col, s.xy_t, z, 3, fv, bt);
-      store_n<F, VX>(PN(b, 0, col), fv);
+      F hv[VX];
+      form_vec(st, 0, col, s.xy_t, z, 3, hv, bt);
+      store_n<F, VX>(PN(b, 0, col), hv);
     }
     if (s.xy_b >= 0) {
-      form_vec(st, s.h + 1, col, s.xy_b, z, 4, fv, bt);
-      store_n<F, VX>(PN(b, s.h + 1, col), fv);
+      F hv[VX];
+      form_vec(st, s.h + 1, col, s.xy_b, z, 4, hv, bt);
+      store_n<F, VX>(PN(b, s.h + 1, col), hv);
     }
   };
-  auto form = [&](int v) {
+  // Form plane v into field buffer b; own receives the thread's own vector.
+  auto form = [&](int v, int b, F (&own)[VX]) {
     const int z = sg.plane(v);
     if (!s.act || z < 0) return;
-    if (z_below(g, z) < 0 || z_above(g, z) < 0) form_t(v, z, true);
-    else form_t(v, z, false);
+    if (z_below(g, z) < 0 || z_above(g, z) < 0) form_t(v, b, z, own, true);
+    else form_t(v, b, z, own, false);
   };
 
+  // The own column's field values of planes v - 1, v, v + 1 stay in
+  // registers; only the in-plane neighbours are read from the shared buffer
+  // of plane v.  The buffer written at iteration v (plane v + 1) is then
+  // never one that a thread still in iteration v - 1 reads (plane v - 1), so
+  // one barrier per plane orders every shared access.
+  F zmr[VX], cvr[VX], zpr[VX];
+#pragma unroll
+  for (int i = 0; i < VX; ++i) zmr[i] = cvr[i] = zpr[i] = F{};
   for (int v = 0; v <= D; ++v) sg.issue(v);
   cp_wait<D - 1>();                 // planes 0 and 1 have landed
-  form(0);
-  form(1);
+  form(0, 0, zmr);
+  form(1, 1, cvr);
+  int bp = 0, b = 1, bn = 2;        // field buffers of planes v - 1, v, v + 1 (v mod 3)
   for (int v = 1; v <= nt; ++v) {
     sg.issue(v + D);
     cp_wait<D - 1>();               // plane v + 1 has landed
-    form(v + 1);
+    form(v + 1, bn, zpr);
     __syncthreads();
-    const int b = v % 3;
     const int zb = sg.plane(v - 1), za = sg.plane(v + 1);
-    F cv[VX], ym[VX], yp[VX], zm[VX], zp[VX];
+    F cv[VX], ym[VX], yp[VX];
     if (s.act) {
-      load_n<F, VX>(PN(b, row, col), cv);
+#pragma unroll
+      for (int i = 0; i < VX; ++i) cv[i] = cvr[i];
       load_n<F, VX>(PN(b, row - 1, col), ym);
       load_n<F, VX>(PN(b, row + 1, col), yp);
-      if (zb >= 0) load_n<F, VX>(PN((v + 2) % 3, row, col), zm);
-      if (za >= 0) load_n<F, VX>(PN((v + 1) % 3, row, col), zp);
     } else {
 #pragma unroll
       for (int i = 0; i < VX; ++i) cv[i] = F{};
@@ -438,8 +452,8 @@ __device__ __forceinline__ void march(const Geo& g, const TileGeo<TXT, TYT, VX>&
           sc.xp = i == VX - 1 ? rgt : cv[i + 1];
           sc.ym = ym[i];
           sc.yp = yp[i];
-          sc.zm = (!B || zb >= 0) ? zm[i] : F{};
-          sc.zp = (!B || za >= 0) ? zp[i] : F{};
+          sc.zm = (!B || zb >= 0) ? zmr[i] : F{};
+          sc.zp = (!B || za >= 0) ? zpr[i] : F{};
           sc.zb = B ? zb : 0;
           sc.za = B ? za : 0;
           T h1[NH], o1[NO > 0 ? NO : 1];
@@ -454,6 +468,15 @@ __device__ __forceinline__ void march(const Geo& g, const TileGeo<TXT, TYT, VX>&
       if (zb < 0 || za < 0) emit_all(true);
       else emit_all(false);
     }
+#pragma unroll
+    for (int i = 0; i < VX; ++i) {
+      zmr[i] = cvr[i];
+      cvr[i] = zpr[i];
+    }
+    const int t3 = bp;
+    bp = b;
+    b = bn;
+    bn = t3;
   }
   cp_wait<0>();
 }
@@ -475,28 +498,42 @@ __device__ __forceinline__ void march_direct(const Geo& g, const TileGeo<TXT, TY
   const bool left_in_warp = s.tx > 0;
   const bool right_in_warp = s.tx < TXT - 1 && (s.tx + 1) * VX < s.w;
 
+  // The own column's raw values of planes v - 1, v, v + 1 stay in registers
+  // (each thread reads back only its own cells of planes v - 1 and v + 1);
+  // other threads' cells are read from the stage of plane v alone, so the
+  // stage a thread refills at iteration v (plane v + D, D >= 2) is never one
+  // that a thread still in iteration v - 1 reads, and one barrier per plane
+  // orders every shared access.
+  static_assert(D >= 2 && NS >= D + 2, "stage ring too short for one barrier per plane");
+  T zmr[NH][VX], cr[NH][VX], zpr[NH][VX];
+#pragma unroll
+  for (int k = 0; k < NH; ++k)
+#pragma unroll
+    for (int i = 0; i < VX; ++i) zmr[k][i] = cr[k][i] = zpr[k][i] = T(0);
   for (int v = 0; v <= D; ++v) sg.issue(v);
   for (int v = 1; v <= nt; ++v) {
     sg.issue(v + D);
     cp_wait<D - 1>();               // planes <= v + 1 of this thread have landed
     __syncthreads();                // ... and of every thread
-    const int st = v % NS, sb = (v + NS - 1) % NS, sa = (v + 1) % NS;
+    const int st = v % NS, sa = (v + 1) % NS;
     const int zb = sg.plane(v - 1), za = sg.plane(v + 1);
-    T c[NH][VX], ym[NH][VX], yp[NH][VX], zm[NH][VX], zp[NH][VX], lft[NH], rgt[NH];
+    if (v == 1 && s.act) {
+#pragma unroll
+      for (int k = 0; k < NH; ++k) {
+        if (zb >= 0) load_n<T, VX>(sg.H(0, k, row, col), zmr[k]);
+        load_n<T, VX>(sg.H(st, k, row, col), cr[k]);
+      }
+    }
+    T ym[NH][VX], yp[NH][VX], lft[NH], rgt[NH];
 #pragma unroll
     for (int k = 0; k < NH; ++k) {
       if (s.act) {
-        load_n<T, VX>(sg.H(st, k, row, col), c[k]);
         load_n<T, VX>(sg.H(st, k, row - 1, col), ym[k]);
         load_n<T, VX>(sg.H(st, k, row + 1, col), yp[k]);
-        if (zb >= 0) load_n<T, VX>(sg.H(sb, k, row, col), zm[k]);
-        if (za >= 0) load_n<T, VX>(sg.H(sa, k, row, col), zp[k]);
-      } else {
-#pragma unroll
-        for (int i = 0; i < VX; ++i) c[k][i] = T(0);
+        if (za >= 0) load_n<T, VX>(sg.H(sa, k, row, col), zpr[k]);
       }
-      lft[k] = shfl_up1(c[k][VX - 1]);
-      rgt[k] = shfl_down1(c[k][0]);
+      lft[k] = shfl_up1(s.act ? cr[k][VX - 1] : T(0));
+      rgt[k] = shfl_down1(s.act ? cr[k][0] : T(0));
       if (s.act) {
         if (!left_in_warp) lft[k] = *sg.H(st, k, row, col - 1);
         if (!right_in_warp) rgt[k] = *sg.H(st, k, row, col + VX);
@@ -514,13 +551,13 @@ __device__ __forceinline__ void march_direct(const Geo& g, const TileGeo<TXT, TY
           Stencil7<R> sc;
 #pragma unroll
           for (int k = 0; k < NH; ++k) {
-            sc.c.v[k] = c[k][i];
-            sc.xm.v[k] = i == 0 ? lft[k] : c[k][i - 1];
-            sc.xp.v[k] = i == VX - 1 ? rgt[k] : c[k][i + 1];
+            sc.c.v[k] = cr[k][i];
+            sc.xm.v[k] = i == 0 ? lft[k] : cr[k][i - 1];
+            sc.xp.v[k] = i == VX - 1 ? rgt[k] : cr[k][i + 1];
             sc.ym.v[k] = ym[k][i];
             sc.yp.v[k] = yp[k][i];
-            sc.zm.v[k] = (!B || zb >= 0) ? zm[k][i] : T(0);
-            sc.zp.v[k] = (!B || za >= 0) ? zp[k][i] : T(0);
+            sc.zm.v[k] = (!B || zb >= 0) ? zmr[k][i] : T(0);
+            sc.zp.v[k] = (!B || za >= 0) ? zpr[k][i] : T(0);
           }
           sc.zb = B ? zb : 0;
           sc.za = B ? za : 0;
@@ -534,6 +571,13 @@ __device__ __forceinline__ void march_direct(const Geo& g, const TileGeo<TXT, TY
       if (zb < 0 || za < 0) emit_all(true);
       else emit_all(false);
     }
+#pragma unroll
+    for (int k = 0; k < NH; ++k)
+#pragma unroll
+      for (int i = 0; i < VX; ++i) {
+        zmr[k][i] = cr[k][i];
+        cr[k][i] = zpr[k][i];
+      }
   }
   cp_wait<0>();
 }

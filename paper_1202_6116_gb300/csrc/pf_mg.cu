@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Sc
   auto post = [&](int z, const T (&rv)[VX]) {
 #pragma unroll
     for (int i = 0; i < VX; ++i) racc[i] += rv[i];
-    if (z % L.fz != L.fz - 1) return;
+    if ((z & (L.fz - 1)) != L.fz - 1) return;      // factors are 1 or 2
     T v[VX];
 #pragma unroll
     for (int i = 0; i < VX; ++i) {
@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Sc
     const bool lead_y = L.fy == 1 || (s.y & 1) == 0;
     const bool lead_x = VX >= 2 || L.fx == 1 || (s.x & 1) == 0;
     if (lead_y && lead_x) {
-      T* dst = C.f + (long long)(z / L.fz) * C.g.nxy + (long long)(s.y / L.fy) * C.g.nx + s.x / L.fx;
+      T* dst = C.f + (long long)(z >> (L.fz - 1)) * C.g.nxy + (long long)(s.y >> (L.fy - 1)) * C.g.nx +
+               (s.x >> (L.fx - 1));
       for (int j = 0; j < cnt; ++j) dst[j] = v[j] * scale;
     }
   };
@@ -279,14 +280,11 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // Conjugate gradients on the coarsest level, FP64, one block, one cell per
-// thread (n <= MG_MAX_COARSE), to a relative residual of 1e-12.  With no
-// electrode the level is singular: the right-hand side and the solution are
-// projected to zero mean.
+// thread (n <= MG_MAX_COARSE <= blockDim.x), to a relative residual of 1e-12.
+// With no electrode the level is singular: the right-hand side and the
+// solution are projected to zero mean.  Every thread of the block calls it.
 template <typename T>
-__global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_coarse(MgView<T> C, int singular, Scalars* S) {
-  __shared__ double ps[MG_MAX_COARSE];
-  __shared__ double red[32];
-  if (S->done) return;
+__device__ __forceinline__ void mg_coarse_solve(const MgView<T>& C, int singular, double* ps, double* red) {
   const int n = (int)C.g.n, tid = threadIdx.x;
   const bool on = tid < n;
   int x = 0, y = 0, z = 0;
@@ -324,6 +322,7 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_coarse(MgView<T> C, int si
   if (bb > 0.0) {
     double p = r;
     for (int it = 0; it < 4 * n + 20; ++it) {
+      __syncthreads();             // ps[] may still be read from the previous iteration
       if (on) ps[tid] = p;
       __syncthreads();
       const double q = on ? apply(ps) : 0.0;
@@ -340,6 +339,109 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_coarse(MgView<T> C, int si
   }
   if (singular) xv -= block_sum(on ? xv : 0.0, red) / n;
   if (on) C.e[tid] = (T)xv;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_coarse(MgView<T> C, int singular, Scalars* S) {
+  __shared__ double ps[MG_MAX_COARSE];
+  __shared__ double red[32];
+  if (S->done) return;
+  mg_coarse_solve(C, singular, ps, red);
+}
+
+// ------------------------------------------------------------ the V-cycle tail
+
+// A v at cell c of a small level, neighbours read from global memory.
+template <typename T>
+__device__ __forceinline__ T tail_apply(const MgView<T>& L, const T* v, int c, T& inv) {
+  const int nx = L.g.nx, ny = L.g.ny, nz = L.g.nz, nxy = (int)L.g.nxy;
+  const int x = c % nx, y = (c / nx) % ny, z = c / nxy;
+  const int r0 = c - x, p0 = c - y * nx - x;
+  const T vc = v[c];
+  const T sx = (vc - v[r0 + (x == 0 ? nx - 1 : x - 1)]) + (vc - v[r0 + (x == nx - 1 ? 0 : x + 1)]);
+  const T sy = (vc - v[p0 + (y == 0 ? ny - 1 : y - 1) * nx + x]) + (vc - v[p0 + (y == ny - 1 ? 0 : y + 1) * nx + x]);
+  T sz = T(0);
+  const int xy = y * nx + x;
+  int cz = 2;
+  if (z > 0) sz += vc - v[c - nxy];
+  else if (L.g.periodic_z) sz += vc - v[c + (nz - 1) * nxy];
+  else { cz += 2 * (int)L.tlo[xy] - 1; if (L.tlo[xy]) sz += T(2) * vc; }
+  if (z < nz - 1) sz += vc - v[c + nxy];
+  else if (L.g.periodic_z) sz += vc - v[c - (nz - 1) * nxy];
+  else { cz += 2 * (int)L.thi[xy] - 1; if (L.thi[xy]) sz += T(2) * vc; }
+  if (L.g.periodic_z) cz = 2;
+  inv = T(1) / (T(2) * L.ax + T(2) * L.ay + T(cz) * L.az);
+  return L.ax * sx + L.ay * sy + L.az * sz;
+}
+
+// The V-cycle below level k0 (all levels small) in one block: per level two
+// pre-smoothing sweeps from zero, residual and restriction, the coarsest
+// solve, then prolongation and two post-smoothing sweeps, each phase a loop
+// over the level's cells followed by a block barrier.  Same operators,
+// weights and transfers as the one-kernel-per-phase path above it.
+template <typename T>
+__global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int singular, Scalars* S) {
+  __shared__ double ps[MG_MAX_COARSE];
+  __shared__ double red[32];
+  if (S->done) return;
+  const T om1 = mg_omega1<T>(), om2 = mg_omega2<T>();
+  const int nt = blockDim.x;
+  for (int k = 0; k + 1 < t.nl; ++k) {
+    const MgView<T>& L = t.lv[k];
+    const MgView<T>& C = t.lv[k + 1];
+    const int n = (int)L.g.n;
+    for (int c = threadIdx.x; c < n; c += nt) {
+      T inv;
+      tail_apply(L, L.f, c, inv);                      // only the diagonal is needed here
+      L.et[c] = om1 * inv * L.f[c];
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += nt) {
+      T inv;
+      const T Ae = tail_apply(L, L.et, c, inv);
+      L.e[c] = L.et[c] + om2 * inv * (L.f[c] - Ae);
+    }
+    __syncthreads();
+    const int nc = (int)C.g.n;
+    const T scale = T(1) / T(L.fx * L.fy * L.fz);
+    for (int cc = threadIdx.x; cc < nc; cc += nt) {
+      const int X = cc % C.g.nx, Y = (cc / C.g.nx) % C.g.ny, Z = cc / (int)C.g.nxy;
+      T acc = T(0);
+      for (int dz = 0; dz < L.fz; ++dz)
+        for (int dy = 0; dy < L.fy; ++dy)
+          for (int dx = 0; dx < L.fx; ++dx) {
+            const int c = ((Z * L.fz + dz) * L.g.ny + Y * L.fy + dy) * L.g.nx + X * L.fx + dx;
+            T inv;
+            acc += L.f[c] - tail_apply(L, L.e, c, inv);
+          }
+      C.f[cc] = acc * scale;
+    }
+    __syncthreads();
+  }
+  mg_coarse_solve(t.lv[t.nl - 1], singular, ps, red);
+  __syncthreads();
+  for (int k = t.nl - 2; k >= 0; --k) {
+    const MgView<T>& L = t.lv[k];
+    const MgView<T>& C = t.lv[k + 1];
+    const int n = (int)L.g.n;
+    for (int c = threadIdx.x; c < n; c += nt) {
+      const int x = c % L.g.nx, y = (c / L.g.nx) % L.g.ny, z = c / (int)L.g.nxy;
+      L.e[c] += C.e[((z >> (L.fz - 1)) * C.g.ny + (y >> (L.fy - 1))) * C.g.nx + (x >> (L.fx - 1))];
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += nt) {
+      T inv;
+      const T Ae = tail_apply(L, L.e, c, inv);
+      L.et[c] = L.e[c] + om2 * inv * (L.f[c] - Ae);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += nt) {
+      T inv;
+      const T Ae = tail_apply(L, L.et, c, inv);
+      L.e[c] = L.et[c] + om1 * inv * (L.f[c] - Ae);
+    }
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -444,6 +546,11 @@ void launch_mg_post2(const LaunchCfg& L, const MgView<T>& lv, int last, double* 
 }
 
 template <typename T>
+void launch_mg_tail(const LaunchCfg& L, const MgTail<T>& t, int singular, Scalars* S) {
+  k_mg_tail<T><<<1, MG_MAX_COARSE, 0, L.stream>>>(t, singular, S);
+}
+
+template <typename T>
 int mg_blocks_per_sm() {
   constexpr int V = vec_of(sizeof(T));
   allow_smem(k_mg_post1<T, V>, MgPipeP<T, V>::bytes());
@@ -460,6 +567,7 @@ int mg_blocks_per_sm() {
   template void launch_mg_pre<T>(const LaunchCfg&, const MgView<T>&, Scalars*);                  \
   template void launch_mg_rr<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*); \
   template void launch_mg_coarse<T>(const LaunchCfg&, const MgView<T>&, int, Scalars*);          \
+  template void launch_mg_tail<T>(const LaunchCfg&, const MgTail<T>&, int, Scalars*);            \
   template void launch_mg_post1<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*); \
   template void launch_mg_post2<T>(const LaunchCfg&, const MgView<T>&, int, double*, Scalars*);        \
   template int mg_blocks_per_sm<T>();
