@@ -56,7 +56,9 @@ def lib():
         L.or_solve_potential.argtypes = [vp, vp, vp, d, i, vp, vp]
         L.or_step.argtypes = [vp, vp, vp, vp, i, vp]
         L.or_rate.argtypes = [vp, vp, vp, vp, vp]
-        L.or_step_ex.argtypes = [vp, vp, i, i, l, vp, vp, i, vp]
+        L.or_step_ex.argtypes = [vp, vp, i, i, l, vp, vp, i, d, C.c_ulonglong, vp]
+        L.or_philox.argtypes = [C.c_ulonglong, C.c_ulonglong, C.c_ulonglong, vp]
+        L.or_gauss4.argtypes = [C.c_ulonglong, C.c_ulonglong, C.c_ulonglong, vp]
         L.or_energy.restype = d
         L.or_energy.argtypes = [vp, vp, vp, d]
         L.or_adjoint_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -225,20 +227,36 @@ def rate(G: Grid, prm: Params, P, phi):
     return out
 
 
-def step_ex(G: Grid, prm: Params, P, phi=None, nsteps=1, integrator="euler", every=1, n0=0):
+def step_ex(G: Grid, prm: Params, P, phi=None, nsteps=1, integrator="euler", every=1, n0=0, sigma=0.0, seed=0):
     """nsteps steps of forward Euler or of the paper's predictor-corrector
     ("heun"), the potential solved only on global steps n0 + s that are
-    multiples of every.  Returns (P, phi, status, info dict)."""
+    multiples of every; sigma > 0 adds the thermal random force (sigma
+    sqrt(dt) standard normal draws per cell, component and step).  Returns
+    (P, phi, status, info dict)."""
     P = _f64(P).reshape((3,) + G.shape).copy()
     phi = np.zeros(G.shape) if phi is None else _f64(phi).reshape(G.shape).copy()
     info = _Info()
     g, p = G._c(), prm._c()
     st = lib().or_step_ex(C.byref(g), C.byref(p), INTEGRATORS[integrator], int(every), int(n0), _ptr(P),
-                          _ptr(phi), int(nsteps), C.byref(info))
+                          _ptr(phi), int(nsteps), float(sigma), int(seed), C.byref(info))
     d = dict(steps_done=info.steps_done, last_iters=info.last_iters,
              total_iters=info.total_iters, last_relres=info.last_relres,
              nonconverged=info.nonconverged)
     return P, phi, st, d
+
+
+def philox(seed, step, cell):
+    """The four 32-bit Philox4x32-10 words for counter (cell, step), key seed."""
+    out = (C.c_uint * 4)()
+    lib().or_philox(int(seed), int(step), int(cell), C.cast(out, C.c_void_p))
+    return list(out)
+
+
+def gauss4(seed, step, cell):
+    """Four standard normal variates (Box-Muller of the Philox words)."""
+    out = np.zeros(4)
+    lib().or_gauss4(int(seed), int(step), int(cell), _ptr(out))
+    return out
 
 
 def energy(G: Grid, prm: Params, P, rtol=1e-14) -> float:

@@ -362,6 +362,68 @@ void or_rate(const or_grid* G, const or_params* prm, const double* P, const doub
   free(h); free(lap); free(E);
 }
 
+/* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC 2011): ten rounds on a 4 x 32-bit counter with a
+ * 2 x 32-bit key.  A round multiplies counter words 0 and 2 by the two
+ * round multipliers into 64-bit products and recombines the high and low
+ * halves with words 1 and 3 and the key; between rounds the key is bumped
+ * by the two Weyl constants. */
+static void philox4x32_10(const unsigned ctr_in[4], const unsigned key_in[2], unsigned out[4]) {
+  unsigned c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+  unsigned k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    unsigned long long p0 = (unsigned long long)0xD2511F53u * c[0];
+    unsigned long long p2 = (unsigned long long)0xCD9E8D57u * c[2];
+    unsigned hi0 = (unsigned)(p0 >> 32), lo0 = (unsigned)p0;
+    unsigned hi2 = (unsigned)(p2 >> 32), lo2 = (unsigned)p2;
+    unsigned n0 = hi2 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo2;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+  out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+void or_philox(unsigned long long seed, unsigned long long step, unsigned long long cell, unsigned out[4]) {
+  const unsigned ctr[4] = {(unsigned)cell, (unsigned)(cell >> 32), (unsigned)step, (unsigned)(step >> 32)};
+  const unsigned key[2] = {(unsigned)seed, (unsigned)(seed >> 32)};
+  philox4x32_10(ctr, key, out);
+}
+
+/* Four standard normal variates for (seed, step, cell): the Box-Muller
+ * transform (Box & Muller 1958) of the two pairs of Philox words, with the
+ * first word of a pair mapped to (0, 1] and the second to [0, 1). */
+void or_gauss4(unsigned long long seed, unsigned long long step, unsigned long long cell, double g[4]) {
+  unsigned x[4];
+  or_philox(seed, step, cell, x);
+  const double two32 = 4294967296.0, twopi = 6.283185307179586;
+  for (int j = 0; j < 2; ++j) {
+    double u1 = ((double)x[2 * j] + 1.0) / two32;
+    double u2 = (double)x[2 * j + 1] / two32;
+    double r = sqrt(-2.0 * log(u1));
+    g[2 * j] = r * cos(twopi * u2);
+    g[2 * j + 1] = r * sin(twopi * u2);
+  }
+}
+
+/* The thermal random force of Eq. TDGL over one step: zeta_i(r, t) dt has
+ * zero mean and Gaussian variance; sigma sqrt(dt) g with g standard normal,
+ * one draw per cell, component and step (components: the first three of
+ * or_gauss4 at the cell's linear index). */
+static void add_noise(const or_grid* G, double* P, double amp, unsigned long long seed, unsigned long long step) {
+  long n = ncells(G);
+  for (long c = 0; c < n; ++c) {
+    double g[4];
+    or_gauss4(seed, step, (unsigned long long)c, g);
+    for (int i = 0; i < 3; ++i) P[(long)i * n + c] += amp * g[i];
+  }
+}
+
 /* One potential solve for the state P, warm-started from phi, booked in inf. */
 static int solve_booked(const or_grid* G, const or_params* prm, const double* P, double* phi, double* b,
                         or_info* inf) {
@@ -387,9 +449,13 @@ static int solve_booked(const or_grid* G, const or_params* prm, const double* P,
  *   every: the long-range (electrostatic) potential is solved only on steps
  *     whose global index n0 + s is a multiple of every; the other steps, both
  *     Heun stages included, keep the last potential solved.
+ *   sigma: the thermal random force of Eq. TDGL (zero mean, Gaussian): every
+ *     step adds sigma sqrt(dt) g to each component of each cell, g standard
+ *     normal from or_gauss4(seed, n0 + s, cell) (Euler-Maruyama; the
+ *     predictor-corrector adds the same increment to both stages).
  * On return phi is the last potential solved (warm start of the next one). */
 int or_step_ex(const or_grid* G, const or_params* prm, int integrator, int every, long n0, double* P,
-               double* phi, int nsteps, or_info* info) {
+               double* phi, int nsteps, double sigma, unsigned long long seed, or_info* info) {
   long n = ncells(G);
   double* b = (double*)malloc(sizeof(double) * n);
   double* R = (double*)malloc(sizeof(double) * 3 * n);
@@ -403,14 +469,19 @@ int or_step_ex(const or_grid* G, const or_params* prm, int integrator, int every
     const int refresh = ((n0 + s) % every) == 0;
     if (refresh && solve_booked(G, prm, P, phi, b, &inf) != OR_OK) status = OR_NOCONV;
     or_rate(G, prm, P, phi, R);
+    const double amp = sigma * sqrt(prm->dt);
+    const unsigned long long step = (unsigned long long)(n0 + s);
     if (integrator == OR_HEUN) {
+      /* the same random increment in the predictor and the corrector */
       for (long i = 0; i < 3 * n; ++i) Pp[i] = P[i] + prm->dt * R[i];
+      if (sigma != 0.0) add_noise(G, Pp, amp, seed, step);
       if (refresh && solve_booked(G, prm, Pp, phi, b, &inf) != OR_OK) status = OR_NOCONV;
       or_rate(G, prm, Pp, phi, Rp);
       for (long i = 0; i < 3 * n; ++i) P[i] = P[i] + prm->dt * (0.5 * (R[i] + Rp[i]));
     } else {
       for (long i = 0; i < 3 * n; ++i) P[i] = P[i] + prm->dt * R[i];
     }
+    if (sigma != 0.0) add_noise(G, P, amp, seed, step);
     inf.steps_done = s + 1;
   }
   if (info) *info = inf;

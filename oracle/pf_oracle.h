@@ -122,9 +122,18 @@ void or_rate(const or_grid* G, const or_params* prm, const double* P, const doub
  * rate with the potential of its own state).  The potential is solved only on
  * steps whose global index n0 + s is a multiple of every (>= 1); other steps
  * keep the last potential (Section Numerical Performance: long-range terms
- * every 5 steps).  phi: warm start in, last solved potential out. */
+ * every 5 steps).  phi: warm start in, last solved potential out.  sigma > 0
+ * adds the thermal random force of Eq. TDGL: sigma sqrt(dt) times standard
+ * normal draws or_gauss4(seed, n0 + s, cell) per step (the same draw in both
+ * predictor-corrector stages). */
 int or_step_ex(const or_grid* G, const or_params* prm, int integrator, int every, long n0, double* P,
-               double* phi, int nsteps, or_info* info);
+               double* phi, int nsteps, double sigma, unsigned long long seed, or_info* info);
+
+/* Philox4x32-10 output for counter (cell, step) and key seed, and four
+ * standard normal variates from it by Box-Muller (the thermal noise of
+ * or_step_ex: components 0..2 of cell c at step n are or_gauss4(seed, n, c)). */
+void or_philox(unsigned long long seed, unsigned long long step, unsigned long long cell, unsigned out[4]);
+void or_gauss4(unsigned long long seed, unsigned long long step, unsigned long long cell, double g[4]);
 
 /* Total free energy: sum f(P) + (g/2) sum_faces |dP|^2/dx^2 - 1/2 sum P.(E + E_ext),
  * with phi solved to rtol; E_ext is the field of the electrodes with P = 0. */
