@@ -126,13 +126,31 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    """Hash of the device-code sources (host-only driver files excluded)."""
+# Device-code sources of each kernel family (the files that define it; the
+# shared march, reduction and layout headers belong to every family).
+FAMILY_SOURCES = {
+    "cg": ("pf_cg.cu",),
+    "mg": ("pf_mg.cu",),
+    "step": ("pf_step.cu", "pf_rng.cuh"),
+}
+COMMON_SOURCES = ("pf_march.cuh", "pf_common.cuh", "pf_internal.h")
+
+
+def family_of(kernel):
+    name = kernel.split(".")[0]
+    if name.startswith("mg_"):
+        return "mg"
+    if name in ("cg_p", "cg_r", "cg_finish"):
+        return "cg"
+    return "step"
+
+
+def kernel_source_hash(kernel):
+    """Hash of the device sources that define a kernel family."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1202_6116_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")) and f not in ("pf_api.cu", "pf_noalloc.cu"):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in sorted(FAMILY_SOURCES[family_of(kernel)] + COMMON_SOURCES):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -144,12 +162,27 @@ def ncu_traffic(kernel, workload, cells):
         d = json.load(open(path))
     except Exception:
         return None
-    if d.get("source_hash") != kernel_source_hash():
-        return None
     e = d.get("kernels", {}).get(kernel)
-    if not e or e.get("workload") != workload:
+    if not e or e.get("workload") != workload or e.get("source_hash") != kernel_source_hash(kernel):
         return None
     return e["dram_bytes_per_cell"] * cells
+
+
+# ------------------------------------------------------------ replicas (N > 1)
+
+def replica_throughput(ms_local, cell_steps_local, world, device=None):
+    """Whole-job throughput of N independent replicas (one film per rank, no
+    collective on the data path): every rank did the same work, so value =
+    N x local cell-steps / the slowest rank's time.  Returns (max ms, value);
+    with world > 1 the MAX is an all-reduce over the default process group."""
+    ms_max = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_max], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    return ms_max, cell_steps_local * world / (ms_max / 1e3)
 
 
 # ------------------------------------------------------------------ our impl
@@ -205,12 +238,7 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = w.n * args.steps * world / (ms_max / 1e3)
+    ms_max, value = replica_throughput(ms, w.n * args.steps, world, dev)
 
     # per-kernel device times: a second pass of the same steps with the
     # library's CUDA-event profiler on (kept out of the headline timing)
@@ -242,11 +270,8 @@ def run_ours(args):
     pf.pf_step_host(film.ctx, Ph, phih, e2e_steps)
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": w.n * e2e_steps * world / e2e_s, "unit": UNIT,
+    e2e_ms, e2e_value = replica_throughput(1e3 * e2e_s, w.n * e2e_steps, world, dev)
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": 4 * w.n * w_bytes, "d2h_bytes_per_step": 4 * w.n * w_bytes,
            "steps": e2e_steps}
 

@@ -267,6 +267,18 @@ pf_status pf_solve_potential_noalloc(const pf_params* params, void* cuda_stream,
                                      const int8_t* type_lo, const double* volt_lo, const int8_t* type_hi,
                                      const double* volt_hi, pf_step_info* info);
 
+/* Thermal random force of Eq. TDGL (the paper's zeta_i(r, t): zero mean,
+ * Gaussian variance).  With sigma > 0 every step adds sigma sqrt(dt) g to
+ * each component of each cell's P, after the deterministic update
+ * (Euler-Maruyama; the predictor-corrector adds the same increment in both
+ * stages, so the corrected state carries it once).  g is standard normal:
+ * components 0..2 of the Box-Muller transform of the Philox4x32-10 block
+ * (Salmon et al. 2011) with counter (cell index, step index since pf_bind)
+ * and key seed -- the same stream for any tiling, graph or host-driven
+ * launch and any split of the steps over calls.  sigma = 0 (the default)
+ * turns it off.  Contexts with noise have no adjoint step (PF_ERR_NOTIMPL). */
+pf_status pf_set_noise(pf_ctx* ctx, double sigma, uint64_t seed);
+
 /* ------------------------------------------------------------------ tiling
  * Tiling of the fine-grid plane-march kernels (Poisson right-hand side, CG
  * operator, TDGL update, diagnostics, adjoint): the hook the autotuner uses.

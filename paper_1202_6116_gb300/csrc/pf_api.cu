@@ -75,7 +75,7 @@ std::vector<MgLevelHost> mg_levels(const pf_params* p) {
 }
 
 struct Layout {
-  size_t P_alt, r, p0, p1, q, invd, tlo, thi, vlo, vhi, part, S, diag, z, zt, total;
+  size_t P_alt, r, p0, p1, q, invd, tlo, thi, vlo, vhi, ctr, part, S, diag, z, zt, total;
   bool adj = false;               // psi and vzero exist (PF_FLAG_ADJOINT)
   size_t psi = 0, vzero = 0;      // adjoint potential; zero face voltages
   std::vector<MgLevelHost> mg;
@@ -134,6 +134,7 @@ Layout layout_of(const pf_params* p) {
   L.thi = take(nxy);
   L.vlo = take(nxy * w);
   L.vhi = take(nxy * w);
+  L.ctr = take(sizeof(long long));   // step counter of the thermal noise (zeroed by pf_bind)
   // reduction partials: per block (flat kernels) or per tile (plane-march
   // kernels; at most one tile per column group of MTX x MTY and plane)
   const size_t max_tiles = (size_t)((p->nx + pf::MTX - 1) / pf::MTX) * ((p->ny + pf::MTY - 1) / pf::MTY) * p->nz;
@@ -213,6 +214,8 @@ struct pf_ctx {
   int64_t graph_fixed = 0;        // kernels of those steps outside the Krylov loops
   int64_t nstep = 0;              // steps since pf_bind (schedules poisson_every)
   uint64_t gen = 0;               // bumped by every change that invalidates captured graphs
+  double noise_sigma = 0.0;       // thermal random force (pf_set_noise)
+  unsigned long long noise_seed = 0;
   int tile_bps = 0;               // blocks per SM requested by pf_set_tiling (0: as many as fit)
   cudaStream_t cap_stream = nullptr;
 
@@ -353,6 +356,16 @@ pf::Dev<T> dev_view(pf_ctx* ctx) {
   return d;
 }
 
+// Thermal-noise arguments of a TDGL launch; advance: the step's last update.
+pf::Noise noise_of(pf_ctx* ctx, int advance) {
+  pf::Noise nz{};
+  nz.amp = ctx->noise_sigma * std::sqrt(ctx->prm.dt);
+  nz.seed = ctx->noise_seed;
+  nz.step = (long long*)(ctx->ws + ctx->lay.ctr);
+  nz.advance = advance;
+  return nz;
+}
+
 template <typename T>
 pf::MgView<T> mg_view(pf_ctx* ctx, size_t k) {
   const MgLevelHost& l = ctx->lay.mg[k];
@@ -381,7 +394,7 @@ pf::MgView<T> mg_view(pf_ctx* ctx, size_t k) {
 // First level of the one-block V-cycle tail: the first level after the
 // finest with at most MG_TAIL_CELLS cells, or the coarsest level (no tail)
 // when that leaves fewer than two levels for the tail.
-size_t mg_tail_start(const Layout& lay) {
+size_t mg_tail_start(const Layout& lay, size_t word) {
   const size_t nl = lay.mg.size();
   size_t k0 = nl - 1;
   for (size_t k = 1; k < nl; ++k)
@@ -389,7 +402,12 @@ size_t mg_tail_start(const Layout& lay) {
       k0 = k;
       break;
     }
-  if (k0 + 1 >= nl || nl - k0 > (size_t)pf::MG_TAIL_LEVELS) k0 = nl - 1;
+  // the tail's level arrays must fit in shared memory
+  for (; k0 + 1 < nl; ++k0) {
+    size_t cells = 0;
+    for (size_t k = k0; k < nl; ++k) cells += (size_t)lay.mg[k].n();
+    if (3 * cells * word <= (size_t)pf::MG_TAIL_SMEM && nl - k0 <= (size_t)pf::MG_TAIL_LEVELS) break;
+  }
   return k0;
 }
 
@@ -398,7 +416,7 @@ size_t mg_tail_start(const Layout& lay) {
 template <typename T>
 void vcycle(pf_ctx* ctx, int j) {
   const size_t nl = ctx->lay.mg.size();
-  const size_t k0 = mg_tail_start(ctx->lay);
+  const size_t k0 = mg_tail_start(ctx->lay, sizeof(T));
   const double w = sizeof(T);
   pf::Scalars* S = (pf::Scalars*)(ctx->ws + ctx->lay.S);
   double* part = (double*)(ctx->ws + ctx->lay.part);
@@ -414,11 +432,14 @@ void vcycle(pf_ctx* ctx, int j) {
   if (k0 + 1 < nl) {
     pf::MgTail<T> t{};
     t.nl = (int)(nl - k0);
-    double cells = 0.0;
+    int off = 0;
     for (size_t k = k0; k < nl; ++k) {
       t.lv[k - k0] = mg_view<T>(ctx, k);
-      cells += (double)t.lv[k - k0].g.n;
+      t.off[k - k0] = off;
+      off += 3 * (int)t.lv[k - k0].g.n;
     }
+    t.smem_elems = off;
+    const double cells = (double)t.lv[0].g.n;
     before_launch(ctx);
     pf::launch_mg_tail<T>(ctx->L, t, ctx->singular, S);
     after_launch(ctx, mg_fam(F_MG_COARSE, k0), 2.0 * cells * w, 2, j);
@@ -561,7 +582,9 @@ bool refresh_step(const pf_ctx* ctx) {
 
 // Kernels of one step outside the Krylov loops, and per Krylov iteration.
 void step_kernel_counts(const pf_ctx* ctx, int refresh, int64_t* fixed, int64_t* per_iter) {
-  const int64_t vc = ctx->prm.solver == PF_PCG_MG ? 4 * (int64_t)mg_tail_start(ctx->lay) + 1 : 0;
+  const int64_t vc = ctx->prm.solver == PF_PCG_MG
+                         ? 4 * (int64_t)mg_tail_start(ctx->lay, ctx->prm.precision == PF_FP32 ? 4 : 8) + 1
+                         : 0;
   const bool heun = ctx->prm.integrator == PF_HEUN;
   const int64_t per_solve = (ctx->singular ? 2 : 0) + 2 + vc;
   *fixed = (refresh ? (heun ? 2 : 1) * per_solve : 0) + (heun ? 2 : 1);
@@ -642,11 +665,11 @@ cudaError_t append_step(pf_ctx* ctx, cudaGraph_t graph, std::vector<cudaGraphNod
   T* Pq = Pbuf[cur ^ 1];
   if (refresh) solve_nodes(Pn);
   if (heun) {
-    segment([&] { pf::launch_tdgl<T>(ctx->L, g, d, Pn, Pq, coef, 0); });
+    segment([&] { pf::launch_tdgl<T>(ctx->L, g, d, Pn, Pq, coef, 0, noise_of(ctx, 0)); });
     if (refresh) solve_nodes(Pq);
-    segment([&] { pf::launch_tdgl<T>(ctx->L, g, d, Pq, Pn, coef, 1); });
+    segment([&] { pf::launch_tdgl<T>(ctx->L, g, d, Pq, Pn, coef, 1, noise_of(ctx, 1)); });
   } else {
-    segment([&] { pf::launch_tdgl<T>(ctx->L, g, d, Pn, Pq, coef, 0); });
+    segment([&] { pf::launch_tdgl<T>(ctx->L, g, d, Pn, Pq, coef, 0, noise_of(ctx, 1)); });
   }
   ctx->L = saved;
   ctx->launches = saved_launches;
@@ -749,7 +772,7 @@ pf_status run_steps(pf_ctx* ctx, int nsteps) {
       if (st != PF_OK) return st;
     }
     before_launch(ctx);
-    pf::launch_tdgl<T>(ctx->L, g, d, P, Q, coef, 0);
+    pf::launch_tdgl<T>(ctx->L, g, d, P, Q, coef, 0, noise_of(ctx, heun ? 0 : 1));
     after_launch(ctx, F_TDGL, tdgl_bytes);
     PF_CUDA(cudaGetLastError());
     if (heun) {
@@ -758,7 +781,7 @@ pf_status run_steps(pf_ctx* ctx, int nsteps) {
         if (st != PF_OK) return st;
       }
       before_launch(ctx);
-      pf::launch_tdgl<T>(ctx->L, g, d, Q, P, coef, 1);
+      pf::launch_tdgl<T>(ctx->L, g, d, Q, P, coef, 1, noise_of(ctx, 1));
       after_launch(ctx, F_TDGL, tdgl_bytes + 3.0 * (double)g.n * sizeof(T));
       PF_CUDA(cudaGetLastError());
     } else {
@@ -1018,8 +1041,9 @@ pf_status pf_adjoint_step(pf_ctx* ctx, const void* lam_in, void* lam_out, double
   pf_status st = check_ready(ctx);
   if (st != PF_OK) return st;
   if (!ctx->lay.adj) return ctx->fail(PF_ERR_STATE, "the context was created without PF_FLAG_ADJOINT");
-  if (ctx->prm.integrator != PF_EULER || ctx->prm.poisson_every > 1)
-    return ctx->fail(PF_ERR_NOTIMPL, "the adjoint step exists for forward Euler with a solve every step only");
+  if (ctx->prm.integrator != PF_EULER || ctx->prm.poisson_every > 1 || ctx->noise_sigma != 0.0)
+    return ctx->fail(PF_ERR_NOTIMPL,
+                     "the adjoint step exists for forward Euler with a solve every step and no thermal noise only");
   if (!lam_in || !lam_out || !grad_params) return ctx->fail(PF_ERR_ARG, "lam_in, lam_out and grad_params must be non-NULL");
   if (((uintptr_t)lam_in % 16) || ((uintptr_t)lam_out % 16))
     return ctx->fail(PF_ERR_ARG, "lam_in and lam_out must be 16-byte aligned");
@@ -1111,6 +1135,16 @@ int32_t pf_profile_read(const pf_ctx* ctx, pf_kernel_stat* out, int32_t max) {
   return n;
 }
 
+
+pf_status pf_set_noise(pf_ctx* ctx, double sigma, uint64_t seed) {
+  if (!ctx) return PF_ERR_ARG;
+  if (!std::isfinite(sigma) || sigma < 0.0) return ctx->fail(PF_ERR_ARG, "sigma must be finite and >= 0");
+  drop_graphs(ctx);
+  ctx->noise_sigma = sigma;
+  ctx->noise_seed = (unsigned long long)seed;
+  ctx->gen += 1;
+  return PF_OK;
+}
 
 pf_status pf_get_tiling(const pf_ctx* ctx, pf_tiling* out) {
   if (!ctx) return PF_ERR_ARG;

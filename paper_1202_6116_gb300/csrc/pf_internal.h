@@ -17,6 +17,7 @@ constexpr int MG_MAX_LEVELS = 24;
 constexpr int MG_MAX_COARSE = 1024;   // cells of the coarsest multigrid level (one block)
 constexpr int MG_TAIL_CELLS = 4096;   // levels at most this large run in the one-block V-cycle tail
 constexpr int MG_TAIL_LEVELS = 16;
+constexpr int MG_TAIL_SMEM = 192 * 1024;   // shared-memory limit of the tail's level arrays (bytes)
 
 struct LaunchCfg {
   int grid;            // simple per-cell kernels (TX x TY blocks over tiles)
@@ -61,7 +62,9 @@ struct MgView {
 template <typename T>
 struct MgTail {
   MgView<T> lv[MG_TAIL_LEVELS];
+  int off[MG_TAIL_LEVELS];   // shared-memory offset (elements) of level k's f, e, e_tmp
   int nl;
+  int smem_elems;            // 3 x the cells of all tail levels
 };
 
 template <typename T>
@@ -80,11 +83,21 @@ template <typename T>
 void launch_cg_finish(const LaunchCfg& L, const Geo& g, const Dev<T>& d, int singular);
 template <typename T>
 void launch_sub_mean(const LaunchCfg& L, const Geo& g, const Dev<T>& d);
+// Thermal random force of one TDGL launch: amp = sigma sqrt(dt) (0: off),
+// the Philox key, the device step counter, and whether this launch (the
+// last update of a step) advances the counter.
+struct Noise {
+  double amp;
+  unsigned long long seed;
+  long long* step;
+  int advance;
+};
+
 // coef = {a1, a11, a12, g, dt*L}.  corr = 1: predictor-corrector corrector
 // (P is the predicted state; Pn holds P_n on entry and P_{n+1} on exit).
 template <typename T>
 void launch_tdgl(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, T* Pn, const double* coef,
-                 int corr = 0);
+                 int corr, const Noise& nz);
 template <typename T>
 void launch_invdiag(const LaunchCfg& L, const Geo& g, const Dev<T>& d);
 // Adjoint update (pf_adjoint.cu): lam_out from lam, the adjoint potential psi

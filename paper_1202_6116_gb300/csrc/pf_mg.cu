@@ -84,9 +84,10 @@ __device__ __forceinline__ T mg_inv_bt(const MgView<T>& L, int xy, int z, T inv_
 template <typename T, int VX>
 using MgPipe1 = Pipe<T, T, MTX, MTY, VX, 1, 0, MG_D>;
 template <typename T, int VX>
-using MgPipe2 = Pipe<T, T, MTX, MTY, VX, 1, 1, MG_D>;
-template <typename T, int VX>
 using MgPipeP = Pipe<T, T, MTX, MTY, VX, 1, 1, MG_D, 1>;
+// stencil read straight from the staged planes (no field buffer)
+template <typename T, int VX>
+using MgPipeD = Pipe<T, void, MTX, MTY, VX, 1, 1, MG_D>;
 
 // ------------------------------------------------------------------ kernels
 
@@ -135,8 +136,8 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Sc
   T racc[VX];
 #pragma unroll
   for (int i = 0; i < VX; ++i) racc[i] = T(0);
-  auto val = [&](const T (&h)[1], int, int, int, int, bool) -> T { return h[0]; };
-  auto emit = [&](int xy, int, const Stencil7<T>& st, const T (&)[1], const T (&o)[1], const bool bt) -> T {
+  auto emit = [&](int xy, int, const Stencil7<Raw<T, 1>>& sr, const T (&o)[1], const bool bt) -> T {
+    const Stencil7<T> st = pick(sr, 0);
     const bool B = bt;
     const int dlo = (B && st.zb < 0) ? (int)L.tlo[xy] : 0;
     const int dhi = (B && st.za < 0) ? (int)L.thi[xy] : 0;
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Sc
   const TileSched ts{&S->sched_next, &S->sched_done};
   for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
-    march<T, T, T, MTX, MTY, VX, 1, 1, MG_D>(L.g, s, smem, hsrc, osrc, val, emit, post);
+    march_direct<T, T, MTX, MTY, VX, 1, 1, MG_D>(L.g, s, smem, hsrc, osrc, emit, post);
   }
   sched_finish(ts);
 }
@@ -224,8 +225,8 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_post2(MgView<T> L, double* part
   const T* osrc[1] = {L.f};
   Acc<T> arz;
   TileGeo<MTX, MTY, VX> s;
-  auto val = [&](const T (&h)[1], int, int, int, int, bool) -> T { return h[0]; };
-  auto emit = [&](int xy, int z, const Stencil7<T>& st, const T (&)[1], const T (&o)[1], const bool bt) -> T {
+  auto emit = [&](int xy, int z, const Stencil7<Raw<T, 1>>& sr, const T (&o)[1], const bool bt) -> T {
+    const Stencil7<T> st = pick(sr, 0);
     const bool B = bt;
     const int dlo = (B && st.zb < 0) ? (int)L.tlo[xy] : 0;
     const int dhi = (B && st.za < 0) ? (int)L.thi[xy] : 0;
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_post2(MgView<T> L, double* part
   for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
     arz = Acc<T>();
-    march<T, T, T, MTX, MTY, VX, 1, 1, MG_D>(L.g, s, smem, hsrc, osrc, val, emit, post);
+    march_direct<T, T, MTX, MTY, VX, 1, 1, MG_D>(L.g, s, smem, hsrc, osrc, emit, post);
     if (LAST) {
       double v[1] = {arz.value()};
       tile_partials<1, MTX * MTY>(v, part, t);
@@ -284,7 +285,8 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // With no electrode the level is singular: the right-hand side and the
 // solution are projected to zero mean.  Every thread of the block calls it.
 template <typename T>
-__device__ __forceinline__ void mg_coarse_solve(const MgView<T>& C, int singular, double* ps, double* red) {
+__device__ __forceinline__ void mg_coarse_solve(const MgView<T>& C, const T* cf, T* ce, int singular, double* ps,
+                                                double* red) {
   const int n = (int)C.g.n, tid = threadIdx.x;
   const bool on = tid < n;
   int x = 0, y = 0, z = 0;
@@ -314,7 +316,7 @@ __device__ __forceinline__ void mg_coarse_solve(const MgView<T>& C, int singular
     else if (dhi) sz += 2.0 * c;
     return ax * ((c - v[xm]) + (c - v[xp])) + ay * ((c - v[ym]) + (c - v[yp])) + az * sz;
   };
-  double b = on ? (double)C.f[tid] : 0.0;
+  double b = on ? (double)cf[tid] : 0.0;
   if (singular) b -= block_sum(b, red) / n;
   double xv = 0.0, r = b;
   double rr = block_sum(r * r, red);
@@ -338,7 +340,7 @@ __device__ __forceinline__ void mg_coarse_solve(const MgView<T>& C, int singular
     }
   }
   if (singular) xv -= block_sum(on ? xv : 0.0, red) / n;
-  if (on) C.e[tid] = (T)xv;
+  if (on) ce[tid] = (T)xv;
 }
 
 template <typename T>
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_coarse(MgView<T> C, int si
   __shared__ double ps[MG_MAX_COARSE];
   __shared__ double red[32];
   if (S->done) return;
-  mg_coarse_solve(C, singular, ps, red);
+  mg_coarse_solve(C, C.f, C.e, singular, ps, red);
 }
 
 // ------------------------------------------------------------ the V-cycle tail
@@ -378,32 +380,48 @@ __device__ __forceinline__ T tail_apply(const MgView<T>& L, const T* v, int c, T
 // pre-smoothing sweeps from zero, residual and restriction, the coarsest
 // solve, then prolongation and two post-smoothing sweeps, each phase a loop
 // over the level's cells followed by a block barrier.  Same operators,
-// weights and transfers as the one-kernel-per-phase path above it.
+// weights and transfers as the one-kernel-per-phase path above it.  Every
+// level's f, e, e_tmp live in shared memory (t.off[k]: offset of level k's
+// three arrays, in elements); the first level's f comes from and its e goes
+// back to global memory.
 template <typename T>
 __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int singular, Scalars* S) {
+  extern __shared__ __align__(16) unsigned char tail_smem[];
   __shared__ double ps[MG_MAX_COARSE];
   __shared__ double red[32];
   if (S->done) return;
+  T* sm = reinterpret_cast<T*>(tail_smem);
+  auto F = [&](int k) { return sm + t.off[k]; };
+  auto E = [&](int k) { return sm + t.off[k] + t.lv[k].g.n; };
+  auto ET = [&](int k) { return sm + t.off[k] + 2 * t.lv[k].g.n; };
   const T om1 = mg_omega1<T>(), om2 = mg_omega2<T>();
   const int nt = blockDim.x;
+  {
+    const int n0 = (int)t.lv[0].g.n;
+    T* f0 = F(0);
+    for (int c = threadIdx.x; c < n0; c += nt) f0[c] = t.lv[0].f[c];
+    __syncthreads();
+  }
   for (int k = 0; k + 1 < t.nl; ++k) {
     const MgView<T>& L = t.lv[k];
     const MgView<T>& C = t.lv[k + 1];
+    T *f = F(k), *e = E(k), *et = ET(k);
     const int n = (int)L.g.n;
     for (int c = threadIdx.x; c < n; c += nt) {
       T inv;
-      tail_apply(L, L.f, c, inv);                      // only the diagonal is needed here
-      L.et[c] = om1 * inv * L.f[c];
+      tail_apply(L, f, c, inv);                        // only the diagonal is needed here
+      et[c] = om1 * inv * f[c];
     }
     __syncthreads();
     for (int c = threadIdx.x; c < n; c += nt) {
       T inv;
-      const T Ae = tail_apply(L, L.et, c, inv);
-      L.e[c] = L.et[c] + om2 * inv * (L.f[c] - Ae);
+      const T Ae = tail_apply(L, et, c, inv);
+      e[c] = et[c] + om2 * inv * (f[c] - Ae);
     }
     __syncthreads();
     const int nc = (int)C.g.n;
     const T scale = T(1) / T(L.fx * L.fy * L.fz);
+    T* fc = F(k + 1);
     for (int cc = threadIdx.x; cc < nc; cc += nt) {
       const int X = cc % C.g.nx, Y = (cc / C.g.nx) % C.g.ny, Z = cc / (int)C.g.nxy;
       T acc = T(0);
@@ -412,33 +430,36 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int sing
           for (int dx = 0; dx < L.fx; ++dx) {
             const int c = ((Z * L.fz + dz) * L.g.ny + Y * L.fy + dy) * L.g.nx + X * L.fx + dx;
             T inv;
-            acc += L.f[c] - tail_apply(L, L.e, c, inv);
+            acc += f[c] - tail_apply(L, e, c, inv);
           }
-      C.f[cc] = acc * scale;
+      fc[cc] = acc * scale;
     }
     __syncthreads();
   }
-  mg_coarse_solve(t.lv[t.nl - 1], singular, ps, red);
+  mg_coarse_solve(t.lv[t.nl - 1], F(t.nl - 1), E(t.nl - 1), singular, ps, red);
   __syncthreads();
   for (int k = t.nl - 2; k >= 0; --k) {
     const MgView<T>& L = t.lv[k];
     const MgView<T>& C = t.lv[k + 1];
+    T *f = F(k), *e = E(k), *et = ET(k);
+    const T* ec = E(k + 1);
     const int n = (int)L.g.n;
     for (int c = threadIdx.x; c < n; c += nt) {
       const int x = c % L.g.nx, y = (c / L.g.nx) % L.g.ny, z = c / (int)L.g.nxy;
-      L.e[c] += C.e[((z >> (L.fz - 1)) * C.g.ny + (y >> (L.fy - 1))) * C.g.nx + (x >> (L.fx - 1))];
+      e[c] += ec[((z >> (L.fz - 1)) * C.g.ny + (y >> (L.fy - 1))) * C.g.nx + (x >> (L.fx - 1))];
     }
     __syncthreads();
     for (int c = threadIdx.x; c < n; c += nt) {
       T inv;
-      const T Ae = tail_apply(L, L.e, c, inv);
-      L.et[c] = L.e[c] + om2 * inv * (L.f[c] - Ae);
+      const T Ae = tail_apply(L, e, c, inv);
+      et[c] = e[c] + om2 * inv * (f[c] - Ae);
     }
     __syncthreads();
+    T* eo = k == 0 ? t.lv[0].e : e;                    // the first level's result goes to global memory
     for (int c = threadIdx.x; c < n; c += nt) {
       T inv;
-      const T Ae = tail_apply(L, L.et, c, inv);
-      L.e[c] = L.et[c] + om1 * inv * (L.f[c] - Ae);
+      const T Ae = tail_apply(L, et, c, inv);
+      eo[c] = et[c] + om1 * inv * (f[c] - Ae);
     }
     __syncthreads();
   }
@@ -483,7 +504,7 @@ template <typename T, int VX>
 static void rr_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
   static bool f = false;
   static int res = 0;
-  const size_t bytes = MgPipe2<T, VX>::bytes();
+  const size_t bytes = MgPipeD<T, VX>::bytes();
   smem_once(k_mg_rr<T, VX>, bytes, f);
   const int grid = mg_grid(k_mg_rr<T, VX>, bytes, lv.mc.ntiles, res);
   k_mg_rr<T, VX><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, cv, S);
@@ -501,7 +522,7 @@ template <typename T, bool LAST, int VX>
 static void post2_v(const LaunchCfg& L, const MgView<T>& lv, double* part, Scalars* S) {
   static bool f = false;
   static int res = 0;
-  const size_t bytes = MgPipe2<T, VX>::bytes();
+  const size_t bytes = MgPipeD<T, VX>::bytes();
   smem_once(k_mg_post2<T, LAST, VX>, bytes, f);
   const int grid = mg_grid(k_mg_post2<T, LAST, VX>, bytes, lv.mc.ntiles, res);
   k_mg_post2<T, LAST, VX><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, part, S);
@@ -547,7 +568,9 @@ void launch_mg_post2(const LaunchCfg& L, const MgView<T>& lv, int last, double* 
 
 template <typename T>
 void launch_mg_tail(const LaunchCfg& L, const MgTail<T>& t, int singular, Scalars* S) {
-  k_mg_tail<T><<<1, MG_MAX_COARSE, 0, L.stream>>>(t, singular, S);
+  static bool f = false;
+  smem_once(k_mg_tail<T>, MG_TAIL_SMEM, f);
+  k_mg_tail<T><<<1, MG_MAX_COARSE, (size_t)t.smem_elems * sizeof(T), L.stream>>>(t, singular, S);
 }
 
 template <typename T>

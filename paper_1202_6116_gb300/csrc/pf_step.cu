@@ -18,6 +18,7 @@
 // per cell: k_rhs reads 4 words and writes 1; k_tdgl reads 4 and writes 3.
 #include "pf_internal.h"
 #include "pf_march.cuh"
+#include "pf_rng.cuh"
 
 namespace pf {
 
@@ -160,6 +161,10 @@ __global__ void __launch_bounds__(MTX* MTY) k_rhs(Geo g, Bc<T> bc, const T* __re
 template <typename T>
 struct Coef {
   T a1, a11, a12, g, dtL;
+  T amp;                         // thermal random force: sigma sqrt(dt) (0: off)
+  unsigned long long seed;
+  long long* step;               // device step counter (steps since pf_bind)
+  int advance;                   // 1: the last block advances the step counter
 };
 
 template <typename T>
@@ -167,16 +172,18 @@ struct P3 {
   T x, y, z;
 };
 
-template <typename T, bool CORR, int VX>
+template <typename T, bool CORR, bool NOISE, int VX>
 __global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __restrict__ P, T* __restrict__ Pn,
                                                   const T* __restrict__ phi, Coef<T> k, Scalars* S, MarchCfg mc) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   const T h = T(0.5), ih = T(g.ih), ih2 = T(g.ih2);
+  // every block reads the step before the last block to finish advances it
+  const unsigned long long nstep = (unsigned long long)*k.step;
   const T* hsrc[4] = {P, P + g.n, P + 2 * g.n, phi};
   const T* osrc[1] = {nullptr};
   TileGeo<MTX, MTY, VX> s;
-  auto emit = [&](int xy, int, const Stencil7<Raw<T, 4>>& st, const T (&)[1], bool) -> P3<T> {
+  auto emit = [&](int xy, int z, const Stencil7<Raw<T, 4>>& st, const T (&)[1], bool) -> P3<T> {
     // E = -grad phi from face values (mean inside, V at an electrode, phi_cell at an open face)
     const T fc = st.c.v[3];
     T E[3];
@@ -205,6 +212,12 @@ __global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __r
       lap *= ih2;
       out[i] = p[i] + k.dtL * (-hi + k.g * lap + E[i]);
     }
+    if constexpr (NOISE && !CORR) {
+      T gz[3];
+      gauss3<T>((unsigned long long)z * g.nxy + xy, nstep, k.seed, gz);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) out[i] += k.amp * gz[i];
+    }
     return P3<T>{out[0], out[1], out[2]};
   };
   auto post = [&](int z, const P3<T> (&ov)[VX]) {
@@ -227,6 +240,19 @@ __global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __r
         b[i] = T(0.5) * (cb[i] + b[i]);
         d[i] = T(0.5) * (cd[i] + d[i]);
       }
+      if constexpr (NOISE) {
+        // the predictor carried the increment amp g; the corrected state needs
+        // it whole: (P_n + P^p + dt R(P^p)) / 2 holds half of it
+#pragma unroll
+        for (int i = 0; i < VX; ++i) {
+          T gz[3];
+          gauss3<T>((unsigned long long)c + i, nstep, k.seed, gz);
+          const T half = T(0.5) * k.amp;
+          a[i] += half * gz[0];
+          b[i] += half * gz[1];
+          d[i] += half * gz[2];
+        }
+      }
     }
     store_n<T, VX>(Pn + c, a);
     store_n<T, VX>(Pn + g.n + c, b);
@@ -237,7 +263,16 @@ __global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __r
     s = tile_geo<MTX, MTY, VX>(g, t, mc);
     march_direct<T, P3<T>, MTX, MTY, VX, 4, 0, STEP_D>(g, s, smem, hsrc, osrc, emit, post);
   }
-  sched_finish(ts);
+  // sched_finish, with the step counter advanced by the last block to finish
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    __threadfence();
+    if (atomicAdd(ts.done, 1u) == gridDim.x - 1) {
+      *ts.next = 0ull;
+      *ts.done = 0u;
+      if (k.advance) *k.step = (long long)nstep + 1;
+      __threadfence();
+    }
+  }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -285,25 +320,33 @@ void launch_rhs(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, c
   rhs_v<T, false>(L, g, d, P, cond, use_cond);
 }
 
-template <typename T, bool CORR, int VX>
+template <typename T, bool CORR, bool NOISE, int VX>
 static void tdgl_t(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, T* Pn, const Coef<T>& k) {
   static bool f = false;
   const size_t bytes = StepPipe<T, false, VX>::bytes();
-  smem_attr(k_tdgl<T, CORR, VX>, bytes, f);
-  k_tdgl<T, CORR, VX><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(g, d.bc, P, Pn, d.phi, k, d.S, L.march);
+  smem_attr(k_tdgl<T, CORR, NOISE, VX>, bytes, f);
+  k_tdgl<T, CORR, NOISE, VX><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(g, d.bc, P, Pn, d.phi, k, d.S,
+                                                                               L.march);
+}
+
+template <typename T, bool CORR, bool NOISE>
+static void tdgl_v(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, T* Pn, const Coef<T>& k) {
+  constexpr int V = 16 / sizeof(T);
+  if (L.march.vx == V) tdgl_t<T, CORR, NOISE, V>(L, g, d, P, Pn, k);
+  else tdgl_t<T, CORR, NOISE, 1>(L, g, d, P, Pn, k);
 }
 
 template <typename T>
 void launch_tdgl(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, T* Pn, const double* coef,
-                 int corr) {
-  const Coef<T> k{T(coef[0]), T(coef[1]), T(coef[2]), T(coef[3]), T(coef[4])};
-  constexpr int V = 16 / sizeof(T);
+                 int corr, const Noise& nz) {
+  Coef<T> k{T(coef[0]), T(coef[1]), T(coef[2]), T(coef[3]), T(coef[4]), T(nz.amp), nz.seed, nz.step, nz.advance};
+  const bool noise = nz.amp != 0.0;
   if (corr) {
-    if (L.march.vx == V) tdgl_t<T, true, V>(L, g, d, P, Pn, k);
-    else tdgl_t<T, true, 1>(L, g, d, P, Pn, k);
+    if (noise) tdgl_v<T, true, true>(L, g, d, P, Pn, k);
+    else tdgl_v<T, true, false>(L, g, d, P, Pn, k);
   } else {
-    if (L.march.vx == V) tdgl_t<T, false, V>(L, g, d, P, Pn, k);
-    else tdgl_t<T, false, 1>(L, g, d, P, Pn, k);
+    if (noise) tdgl_v<T, false, true>(L, g, d, P, Pn, k);
+    else tdgl_v<T, false, false>(L, g, d, P, Pn, k);
   }
 }
 
@@ -311,7 +354,8 @@ void launch_tdgl(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, 
   template void launch_rhs_mean<T>(const LaunchCfg&, const Geo&, const Dev<T>&, const T*);                  \
   template void launch_rhs<T>(const LaunchCfg&, const Geo&, const Dev<T>&, const T*,                        \
                               cudaGraphConditionalHandle, int);                                             \
-  template void launch_tdgl<T>(const LaunchCfg&, const Geo&, const Dev<T>&, const T*, T*, const double*, int);
+  template void launch_tdgl<T>(const LaunchCfg&, const Geo&, const Dev<T>&, const T*, T*, const double*, int,  \
+                               const Noise&);
 
 PF_STEP_INSTANTIATE(float)
 PF_STEP_INSTANTIATE(double)

@@ -61,6 +61,10 @@ class Film:
         v = np.ascontiguousarray(volts, dtype=np.float64).reshape(-1)
         pf.pf_set_bc(self.ctx, face, t, v)
 
+    def set_noise(self, sigma, seed=0):
+        """Thermal random force of the TDGL equation (sigma = 0: off)."""
+        pf.pf_set_noise(self.ctx, sigma, seed)
+
     def step(self, nsteps=1, ok=(pf.PF_OK,)):
         st, info = pf.pf_step(self.ctx, nsteps, ok)
         return st, info.as_dict()

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_CUDA", 3: "PF_ERR_NOCONV
 # Every symbol the header declares.
 EXPORTS = ["pf_workspace_bytes", "pf_create", "pf_bind", "pf_set_bc", "pf_step", "pf_step_host",
            "pf_solve_potential", "pf_adjoint_step", "pf_diagnostics", "pf_profile_enable", "pf_profile_read", "pf_destroy",
-           "pf_last_error", "pf_solve_potential_noalloc", "pf_get_tiling", "pf_set_tiling",
+           "pf_last_error", "pf_solve_potential_noalloc", "pf_set_noise", "pf_get_tiling", "pf_set_tiling",
            "pf_batch_workspace_bytes", "pf_batch_create", "pf_batch_set_ramp", "pf_batch_step",
            "pf_batch_film_info", "pf_batch_read_loops", "pf_batch_destroy", "pf_batch_last_error"]
 
@@ -105,6 +105,8 @@ def lib():
         L.pf_solve_potential_noalloc.restype = i32
         L.pf_solve_potential_noalloc.argtypes = [C.POINTER(pf_params), vp, vp, vp, vp, vp, vp, vp,
                                                  C.POINTER(pf_step_info)]
+        L.pf_set_noise.restype = i32
+        L.pf_set_noise.argtypes = [vp, C.c_double, C.c_uint64]
         L.pf_get_tiling.restype = i32
         L.pf_get_tiling.argtypes = [vp, C.POINTER(pf_tiling)]
         L.pf_set_tiling.restype = i32
@@ -244,6 +246,12 @@ def pf_solve_potential_noalloc(params: pf_params, stream, P, phi, type_lo=None, 
 
 def pf_destroy(ctx):
     return lib().pf_destroy(ctx)
+
+
+def pf_set_noise(ctx, sigma, seed=0):
+    """Thermal random force: sigma sqrt(dt) standard normal draws per cell,
+    component and step (sigma = 0: off)."""
+    return check(lib().pf_set_noise(ctx, float(sigma), int(seed)), ctx)
 
 
 def pf_get_tiling(ctx) -> pf_tiling:
