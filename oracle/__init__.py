@@ -25,7 +25,7 @@ class _Grid(C.Structure):
                 ("periodic_z", C.c_int),
                 ("type_lo", C.c_void_p), ("volt_lo", C.c_void_p),
                 ("type_hi", C.c_void_p), ("volt_hi", C.c_void_p),
-                ("eps", C.c_void_p)]
+                ("eps", C.c_void_p), ("n_air", C.c_int)]
 
 
 class _Params(C.Structure):
@@ -89,6 +89,7 @@ class Grid:
     type_hi: np.ndarray | None = None
     volt_hi: np.ndarray | None = None
     eps: np.ndarray | None = None
+    n_air: int = 0                      # top layers that are air (P = 0, no wall energy across)
 
     def __post_init__(self):
         m = (self.ny, self.nx)
@@ -112,7 +113,7 @@ class Grid:
     def _c(self):
         g = _Grid(self.nx, self.ny, self.nz, float(self.dx), int(bool(self.periodic_z)),
                   _ptr(self.type_lo), _ptr(self.volt_lo), _ptr(self.type_hi), _ptr(self.volt_hi),
-                  _ptr(self.eps))
+                  _ptr(self.eps), int(self.n_air))
         return g
 
 

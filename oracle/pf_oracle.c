@@ -85,8 +85,34 @@ void or_landau_force(const double* P, long n, double a1, double a11, double a12,
   }
 }
 
+/* Air layers (Section Results, open-circuit device: the top layers of the
+ * grid are air, with permittivity 1 against 100 in the film): a cell is
+ * ferroelectric below z = nz - n_air.  Air cells carry no polarization, and
+ * the film's surface under the air is a free surface for P (zero normal
+ * flux in the gradient term, like a z face of the grid). */
+static int is_film(const or_grid* G, int z) { return z < G->nz - G->n_air; }
+
+/* Face of cell (x,y,z) in direction d, side s, that carries gradient (wall)
+ * energy: an interior face between two film cells. */
+static int wall_face(const or_grid* G, int x, int y, int z, int d, int s, long* nb) {
+  int bt;
+  double bv;
+  if (!is_film(G, z) || !face_of(G, x, y, z, d, s, nb, &bt, &bv)) return 0;
+  if (d == 2 && !G->periodic_z && !is_film(G, z + s)) return 0;
+  return 1;
+}
+
+/* P = 0 in the air cells. */
+static void zero_air(const or_grid* G, double* P) {
+  if (G->n_air <= 0) return;
+  long n = ncells(G), nxy = (long)G->nx * G->ny;
+  for (int i = 0; i < 3; ++i)
+    for (long c = (long)(G->nz - G->n_air) * nxy; c < n; ++c) P[(long)i * n + c] = 0.0;
+}
+
 /* Eq. dF_grad/dP: Lap f as the sum over the cell's interior faces of
- * (f_nb - f_c)/dx^2.  A non-periodic z face is dropped (zero normal flux). */
+ * (f_nb - f_c)/dx^2.  A non-periodic z face is dropped (zero normal flux),
+ * and so is a film/air face; air cells get 0. */
 void or_laplacian(const or_grid* G, const double* f, double* out) {
   double h2 = 1.0 / (G->dx * G->dx);
   for (int z = 0; z < G->nz; ++z)
@@ -97,9 +123,7 @@ void or_laplacian(const or_grid* G, const double* f, double* out) {
         for (int d = 0; d < 3; ++d)
           for (int s = -1; s <= 1; s += 2) {
             long nb;
-            int bt;
-            double bv;
-            if (face_of(G, x, y, z, d, s, &nb, &bt, &bv)) acc += f[nb] - f[c];
+            if (wall_face(G, x, y, z, d, s, &nb)) acc += f[nb] - f[c];
           }
         out[c] = acc * h2;
       }
@@ -341,6 +365,7 @@ int or_step(const or_grid* G, const or_params* prm, double* P, double* phi, int 
     for (int c = 0; c < 3; ++c) or_laplacian(G, P + (long)c * n, lap + (long)c * n);
     for (long i = 0; i < 3 * n; ++i)
       P[i] = P[i] + prm->dt * prm->L * (-h[i] + prm->g * lap[i] + E[i]);
+    zero_air(G, P);
     inf.steps_done = s + 1;
   }
   if (info) *info = inf;
@@ -359,6 +384,7 @@ void or_rate(const or_grid* G, const or_params* prm, const double* P, const doub
   or_landau_force(P, n, prm->a1, prm->a11, prm->a12, h);
   for (int c = 0; c < 3; ++c) or_laplacian(G, P + (long)c * n, lap + (long)c * n);
   for (long i = 0; i < 3 * n; ++i) R[i] = prm->L * (-h[i] + prm->g * lap[i] + E[i]);
+  zero_air(G, R);
   free(h); free(lap); free(E);
 }
 
@@ -475,6 +501,7 @@ int or_step_ex(const or_grid* G, const or_params* prm, int integrator, int every
       /* the same random increment in the predictor and the corrector */
       for (long i = 0; i < 3 * n; ++i) Pp[i] = P[i] + prm->dt * R[i];
       if (sigma != 0.0) add_noise(G, Pp, amp, seed, step);
+      zero_air(G, Pp);
       if (refresh && solve_booked(G, prm, Pp, phi, b, &inf) != OR_OK) status = OR_NOCONV;
       or_rate(G, prm, Pp, phi, Rp);
       for (long i = 0; i < 3 * n; ++i) P[i] = P[i] + prm->dt * (0.5 * (R[i] + Rp[i]));
@@ -482,6 +509,7 @@ int or_step_ex(const or_grid* G, const or_params* prm, int integrator, int every
       for (long i = 0; i < 3 * n; ++i) P[i] = P[i] + prm->dt * R[i];
     }
     if (sigma != 0.0) add_noise(G, P, amp, seed, step);
+    zero_air(G, P);
     inf.steps_done = s + 1;
   }
   if (info) *info = inf;
@@ -504,9 +532,7 @@ double or_energy(const or_grid* G, const or_params* prm, const double* P, double
         long c = cell_index(G, x, y, z);
         for (int d = 0; d < 3; ++d) {
           long nb;
-          int bt;
-          double bv;
-          if (!face_of(G, x, y, z, d, +1, &nb, &bt, &bv)) continue;
+          if (!wall_face(G, x, y, z, d, +1, &nb)) continue;
           for (int i = 0; i < 3; ++i) {
             double dp = P[(long)i * n + nb] - P[(long)i * n + c];
             fg += dp * dp;
@@ -630,9 +656,7 @@ void or_diagnostics(const or_grid* G, const or_params* prm, const double* P, con
         long c = cell_index(G, x, y, z);
         for (int d = 0; d < 3; ++d) {
           long nb;
-          int bt;
-          double bv;
-          if (!face_of(G, x, y, z, d, +1, &nb, &bt, &bv)) continue;
+          if (!wall_face(G, x, y, z, d, +1, &nb)) continue;
           for (int i = 0; i < 3; ++i) {
             double dp = P[(long)i * n + nb] - P[(long)i * n + c];
             fg += dp * dp;

@@ -55,6 +55,8 @@ typedef struct {
   const signed char* type_hi;     /* nx*ny, face z = nz - 1/2 */
   const double* volt_hi;
   const double* eps;              /* N cell permittivities, or NULL for eps = 1 */
+  int n_air;                      /* top layers z >= nz - n_air are air: P = 0 there, and the
+                                     film/air faces carry no gradient (wall) energy */
 } or_grid;
 
 typedef struct {
@@ -139,7 +141,8 @@ void or_gauss4(unsigned long long seed, unsigned long long step, unsigned long l
  * with phi solved to rtol; E_ext is the field of the electrodes with P = 0. */
 double or_energy(const or_grid* G, const or_params* prm, const double* P, double rtol);
 
-/* Discrete adjoint of one or_step step at the state P (= P_n): from
+/* Discrete adjoint of one or_step step at the state P (= P_n) of a grid
+ * without air layers (n_air = 0): from
  * lam = dJ/dP_{n+1} computes lam_out = dJ/dP_n, and adds this step's
  * sensitivities to grad[4] (a1, a11, a12, g) and to the per-face-cell
  * voltage sensitivities gv_lo, gv_hi (nx*ny each).  psi is the warm start of
