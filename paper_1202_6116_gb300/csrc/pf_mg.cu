@@ -82,7 +82,7 @@ __device__ __forceinline__ T mg_inv_bt(const MgView<T>& L, int xy, int z, T inv_
 }
 
 template <typename T, int VX>
-using MgPipe1 = Pipe<T, T, MTX, MTY, VX, 1, 0, MG_D>;
+using MgPipeD0 = Pipe<T, void, MTX, MTY, VX, 1, 0, MG_D>;
 template <typename T, int VX>
 using MgPipeP = Pipe<T, T, MTX, MTY, VX, 1, 1, MG_D, 1>;
 // stencil read straight from the staged planes (no field buffer)
@@ -91,30 +91,62 @@ using MgPipeD = Pipe<T, void, MTX, MTY, VX, 1, 1, MG_D>;
 
 // ------------------------------------------------------------------ kernels
 
+// Two pre-smoothing sweeps from zero, read straight from the staged planes of
+// f.  The first sweep is e1 = w1 diag^-1 f; the second e = e1 + w2 diag^-1 (f -
+// A e1).  Away from the z faces the diagonal is one constant, so A e1 =
+// w1 diag^-1 A f there; on the planes next to a z face and their neighbour
+// planes e1 is formed per neighbour with its own diagonal.
 template <typename T, int VX>
 __global__ void __launch_bounds__(MTX* MTY) k_mg_pre(MgView<T> L, Scalars* S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   if (S->done) return;
   const T om1 = mg_omega1<T>(), om2 = mg_omega2<T>(), inv_int = mg_inv_int(L);
+  const T w1 = om1 * inv_int;
   const T* hsrc[1] = {L.f};
   const T* osrc[1] = {nullptr};
+  const int nx = L.g.nx, nz = L.g.nz;
+  const bool zfaces = !L.g.periodic_z;
   TileGeo<MTX, MTY, VX> s;
-  auto val = [&](const T (&h)[1], int xy, int z, int, int, const bool bt) -> T {
-    return om1 * mg_inv_bt(L, xy, z, inv_int, bt) * h[0];
-  };
-  auto emit = [&](int xy, int z, const Stencil7<T>& st, const T (&h)[1], const T (&)[1], const bool bt) -> T {
-    const bool B = bt;
-    const int dlo = (B && st.zb < 0) ? (int)L.tlo[xy] : 0;
-    const int dhi = (B && st.za < 0) ? (int)L.thi[xy] : 0;
-    const T Ae = apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az, bt);
-    return st.c + om2 * mg_inv_bt(L, xy, z, inv_int, bt) * (h[0] - Ae);
+  auto emit = [&](int xy, int z, const Stencil7<Raw<T, 1>>& sr, const T (&)[1], const bool bt) -> T {
+    const Stencil7<T> f = pick(sr, 0);
+    const bool near = zfaces && (z == 1 || z == nz - 2);
+    if (!bt && !near) {
+      const T Ae1 = w1 * apply_aniso(f, 0, 0, L.ax, L.ay, L.az, false);
+      return w1 * f.c + om2 * inv_int * (f.c - Ae1);
+    }
+    Stencil7<T> e1;
+    const T ic = mg_inv(L, xy, z, inv_int);
+    e1.c = om1 * ic * f.c;
+    if (bt) {
+      const int x = xy % nx, rb = xy - x;
+      const int xm = rb + (x == 0 ? nx - 1 : x - 1), xp = rb + (x == nx - 1 ? 0 : x + 1);
+      const int y = xy / nx;
+      const int ym = (y == 0 ? L.g.ny - 1 : y - 1) * nx + x, yp = (y == L.g.ny - 1 ? 0 : y + 1) * nx + x;
+      e1.xm = om1 * mg_inv(L, xm, z, inv_int) * f.xm;
+      e1.xp = om1 * mg_inv(L, xp, z, inv_int) * f.xp;
+      e1.ym = om1 * mg_inv(L, ym, z, inv_int) * f.ym;
+      e1.yp = om1 * mg_inv(L, yp, z, inv_int) * f.yp;
+    } else {
+      e1.xm = w1 * f.xm;
+      e1.xp = w1 * f.xp;
+      e1.ym = w1 * f.ym;
+      e1.yp = w1 * f.yp;
+    }
+    e1.zm = f.zb >= 0 ? om1 * mg_inv(L, xy, z - 1, inv_int) * f.zm : T(0);
+    e1.zp = f.za >= 0 ? om1 * mg_inv(L, xy, z + 1, inv_int) * f.zp : T(0);
+    e1.zb = f.zb;
+    e1.za = f.za;
+    const int dlo = (bt && f.zb < 0) ? (int)L.tlo[xy] : 0;
+    const int dhi = (bt && f.za < 0) ? (int)L.thi[xy] : 0;
+    const T Ae1 = apply_aniso(e1, dlo, dhi, L.ax, L.ay, L.az, bt);
+    return e1.c + om2 * ic * (f.c - Ae1);
   };
   auto post = [&](int z, const T (&ov)[VX]) { store_n<T, VX>(L.e + (long long)z * L.g.nxy + s.xy, ov); };
   const TileSched ts{&S->sched_next, &S->sched_done};
   for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
-    march<T, T, T, MTX, MTY, VX, 1, 0, MG_D>(L.g, s, smem, hsrc, osrc, val, emit, post);
+    march_direct<T, T, MTX, MTY, VX, 1, 0, MG_D>(L.g, s, smem, hsrc, osrc, emit, post);
   }
   sched_finish(ts);
 }
@@ -495,7 +527,7 @@ template <typename T, int VX>
 static void pre_v(const LaunchCfg& L, const MgView<T>& lv, Scalars* S) {
   static bool f = false;
   static int res = 0;
-  const size_t bytes = MgPipe1<T, VX>::bytes();
+  const size_t bytes = MgPipeD0<T, VX>::bytes();
   smem_once(k_mg_pre<T, VX>, bytes, f);
   const int grid = mg_grid(k_mg_pre<T, VX>, bytes, lv.mc.ntiles, res);
   k_mg_pre<T, VX><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, S);
