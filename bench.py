@@ -337,6 +337,8 @@ def run_batch(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     ws = W.film_batch_hysteresis(nfilms=args.films, seed=4, steps=args.steps + args.warmup)
+    if args.solver == "mg":
+        ws = [w.with_(solver="mg", maxit=500) for w in ws]
     t0 = time.perf_counter()
     tuned = {}
     for w in ws:
@@ -388,8 +390,9 @@ def run_batch(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded SplitMix64 initial states and ramp draws)",
             "config": {"workload": "batch of %d FP32 films (32^3, 64x64x32, 96x96x48, 128x128x64 drawn with "
-                                   "seed 4), grounded bottom, ramped top electrode, Jacobi-PCG rtol=1e-06 dt=0.01"
-                                   % len(ws), "cells": cells, "films": len(ws),
+                                   "seed 4), grounded bottom, ramped top electrode, %s rtol=1e-06 dt=0.01"
+                                   % (len(ws), "MG-PCG" if ws[0].solver == "mg" else "Jacobi-PCG"),
+                       "cells": cells, "films": len(ws), "solver": ws[0].solver,
                        "l2": "inputs larger than L2 (%.2f GB of film state)" % (cells * 4 * 11 / 1e9)},
             "poisson_iters_per_step": info["total_iters"] / args.steps / len(ws),
             "gpu_launches": info["kernel_launches"], "status": pf.STATUS_NAMES[st],

@@ -76,7 +76,8 @@ typedef struct {
   int32_t flags;             /* PF_FLAG_* bits (0 = defaults) */
   int32_t integrator;        /* PF_EULER (0) or PF_HEUN (the paper's predictor-corrector) */
   int32_t poisson_every;     /* solve the potential on every k-th step only (0 or 1: every step) */
-  int32_t reserved[4];       /* must be zero */
+  int32_t n_air;             /* top layers that are air (0 <= n_air < nz; needs periodic_z = 0) */
+  int32_t reserved[3];       /* must be zero */
 } pf_params;
 
 /* pf_params.integrator (Section Time Integration), with R(P) = L(-df/dP +
@@ -86,6 +87,12 @@ typedef struct {
  *             P^p = P_n + dt R(P_n), P_{n+1} = P_n + dt (R(P_n) + R(P^p))/2;
  *             two Poisson solves per step (the second warm-started from the
  *             first), computed as P_{n+1} = (P_n + P^p + dt R(P^p))/2.
+ * pf_params.n_air = m > 0 (Section Results, the open-circuit device: air on
+ * top of the film): planes z >= nz - m are air.  Their P is set to zero by
+ * every update (give zero initial values there), their permittivity is the
+ * caller's eps field (has_eps), and the film's top surface is free for the
+ * gradient term (no z+ neighbour in the Laplacian, no wall energy across it).
+ * The Poisson problem spans film and air.  No adjoint step (PF_ERR_NOTIMPL).
  * pf_params.poisson_every = k > 1 (Section Numerical Performance: long-range
  * terms every 5 steps): the potential is solved only on steps whose index
  * (counted from pf_bind) is a multiple of k; the other steps, both Heun

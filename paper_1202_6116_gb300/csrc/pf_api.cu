@@ -109,7 +109,9 @@ bool params_valid(const pf_params* p, std::string* why) {
   if (p->flags & ~(PF_FLAG_NO_GRAPHS | PF_FLAG_ADJOINT)) return fail("unknown bits in flags");
   if (p->integrator != PF_EULER && p->integrator != PF_HEUN) return fail("integrator must be PF_EULER or PF_HEUN");
   if (p->poisson_every < 0) return fail("poisson_every must be >= 0");
-  for (int i = 0; i < 4; ++i)
+  if (p->n_air < 0 || p->n_air >= p->nz) return fail("n_air must be in 0 .. nz - 1");
+  if (p->n_air > 0 && p->periodic_z) return fail("air layers need non-periodic z (periodic_z = 0)");
+  for (int i = 0; i < 3; ++i)
     if (p->reserved[i] != 0) return fail("reserved fields must be zero");
   return true;
 }
@@ -374,6 +376,7 @@ pf::MgView<T> mg_view(pf_ctx* ctx, size_t k) {
   v.g.ny = l.ny;
   v.g.nz = l.nz;
   v.g.periodic_z = ctx->prm.periodic_z;
+  v.g.zair = l.nz;
   v.g.nxy = l.nxy();
   v.g.n = l.n();
   v.ax = (T)l.ax;
@@ -1041,9 +1044,9 @@ pf_status pf_adjoint_step(pf_ctx* ctx, const void* lam_in, void* lam_out, double
   pf_status st = check_ready(ctx);
   if (st != PF_OK) return st;
   if (!ctx->lay.adj) return ctx->fail(PF_ERR_STATE, "the context was created without PF_FLAG_ADJOINT");
-  if (ctx->prm.integrator != PF_EULER || ctx->prm.poisson_every > 1 || ctx->noise_sigma != 0.0)
-    return ctx->fail(PF_ERR_NOTIMPL,
-                     "the adjoint step exists for forward Euler with a solve every step and no thermal noise only");
+  if (ctx->prm.integrator != PF_EULER || ctx->prm.poisson_every > 1 || ctx->noise_sigma != 0.0 || ctx->prm.n_air > 0)
+    return ctx->fail(PF_ERR_NOTIMPL, "the adjoint step exists for forward Euler with a solve every step, no thermal "
+                                     "noise and no air layers only");
   if (!lam_in || !lam_out || !grad_params) return ctx->fail(PF_ERR_ARG, "lam_in, lam_out and grad_params must be non-NULL");
   if (((uintptr_t)lam_in % 16) || ((uintptr_t)lam_out % 16))
     return ctx->fail(PF_ERR_ARG, "lam_in and lam_out must be 16-byte aligned");

@@ -30,6 +30,7 @@ struct MarchCfg {
 struct Geo {
   int nx, ny, nz;
   int periodic_z;
+  int zair;                // first air plane (nz: no air layers); P = 0 from there up
   long long nxy, n;
   double ih, ih2;          // 1/dx, 1/dx^2
   int tz;                  // cells per column in one tile

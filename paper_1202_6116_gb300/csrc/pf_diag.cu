@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_diag(Geo g, Bc<T> bc, const T* __r
   const T* osrc[1] = {nullptr};
   Acc<T> acc[DIAG_NV];
   TileGeo<MTX, MTY, VX> s{};
-  auto emit = [&](int xy, int, const Stencil7<Raw<T, 4>>& st, const T (&)[1], bool) -> T {
+  auto emit = [&](int xy, int z, const Stencil7<Raw<T, 4>>& st, const T (&)[1], bool) -> T {
     const T fc = st.c.v[3];
     T E[3];
     E[0] = -(h * (fc + st.xp.v[3]) - h * (fc + st.xm.v[3])) * ih;
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_diag(Geo g, Bc<T> bc, const T* __r
       const T dxp = st.xp.v[i] - p[i], dyp = st.yp.v[i] - p[i];
       acc[5].add(dxp, dxp);
       acc[5].add(dyp, dyp);
-      if (st.za >= 0) {
+      if (st.za >= 0 && (z + 1 < g.zair || g.zair == g.nz)) {     // no wall energy across the film/air face
         const T dzp = st.zp.v[i] - p[i];
         acc[5].add(dzp, dzp);
       }

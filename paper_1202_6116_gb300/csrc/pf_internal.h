@@ -172,6 +172,7 @@ inline void setup_launch(const pf_params* p, int nsm, cudaStream_t stream, Geo& 
   g.ny = p->ny;
   g.nz = p->nz;
   g.periodic_z = p->periodic_z;
+  g.zair = p->nz - p->n_air;
   g.nxy = (long long)g.nx * g.ny;
   g.n = g.nxy * g.nz;
   g.ih = 1.0 / p->dx;

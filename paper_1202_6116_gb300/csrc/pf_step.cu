@@ -8,6 +8,8 @@
 //           projection of singular problems).
 //   k_tdgl  P' = P + dt L (-df/dP + g Lap P + E), E = -grad phi from face values
 //           (Eq. TDGL with Eqs. F_bulk, dF_grad/dP, F_elec; Section Time Integration).
+//           Planes z >= zair are air: P = 0 there, and the film's top plane has
+//           no z+ neighbour in the Laplacian (free surface).
 //           CORR = true is the corrector of the predictor-corrector scheme: P is
 //           the predicted state P^p, and the output overwrites the state P_n it
 //           started from with (P_n + P^p + dt R(P^p)) / 2 = P_n + dt (R(P_n) +
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __r
       lap += st.ym.v[i] - p[i];
       lap += st.yp.v[i] - p[i];
       if (st.zb >= 0) lap += st.zm.v[i] - p[i];
-      if (st.za >= 0) lap += st.zp.v[i] - p[i];
+      if (st.za >= 0 && (z + 1 < g.zair || g.zair == g.nz)) lap += st.zp.v[i] - p[i];   // free surface under air
       lap *= ih2;
       out[i] = p[i] + k.dtL * (-hi + k.g * lap + E[i]);
     }
@@ -223,6 +225,14 @@ __global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __r
   auto post = [&](int z, const P3<T> (&ov)[VX]) {
     const long long c = (long long)z * g.nxy + s.xy;
     T a[VX], b[VX], d[VX];
+    if (z >= g.zair) {                 // air layers carry no polarization
+#pragma unroll
+      for (int i = 0; i < VX; ++i) a[i] = b[i] = d[i] = T(0);
+      store_n<T, VX>(Pn + c, a);
+      store_n<T, VX>(Pn + g.n + c, b);
+      store_n<T, VX>(Pn + 2 * g.n + c, d);
+      return;
+    }
 #pragma unroll
     for (int i = 0; i < VX; ++i) {
       a[i] = ov[i].x;

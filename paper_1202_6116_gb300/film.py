@@ -22,6 +22,7 @@ def make_params(w: Workload, **overrides) -> pf.pf_params:
     p.poisson_maxit = w.maxit
     p.periodic_z = int(bool(w.periodic_z))
     p.has_eps = int(w.eps is not None)
+    p.n_air = int(w.n_air)
     for k, v in overrides.items():
         setattr(p, k, v)
     return p

@@ -40,8 +40,8 @@ class pf_params(C.Structure):
                 ("precision", C.c_int32), ("solver", C.c_int32),
                 ("poisson_rtol", C.c_double), ("poisson_maxit", C.c_int32),
                 ("periodic_z", C.c_int32), ("has_eps", C.c_int32), ("flags", C.c_int32),
-                ("integrator", C.c_int32), ("poisson_every", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("integrator", C.c_int32), ("poisson_every", C.c_int32), ("n_air", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class pf_step_info(C.Structure):

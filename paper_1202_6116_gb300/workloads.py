@@ -71,6 +71,7 @@ class Workload:
     precision: str = "fp64"              # "fp64" or "fp32"
     solver: str = "pcg"                  # "pcg" (Jacobi-PCG) or "mg" (multigrid-PCG)
     periodic_z: bool = False
+    n_air: int = 0                       # top layers that are air (P = 0; eps from the eps field)
     seed: int = 0
     extra: dict = field(default_factory=dict)
 
@@ -233,3 +234,20 @@ def film_batch_hysteresis(nfilms=64, seed=4, steps=4000, shapes=BATCH_SHAPES, pr
                               dt=0.01, steps=steps, rtol=rtol, maxit=20000, precision=precision,
                               solver="pcg", seed=fseed, extra={"ramp": (amp, period)}))
     return films
+
+
+def film_open_air(nx=64, ny=64, nz=37, n_air=5, steps=200, seed=5, precision="fp32", eps_film=100.0,
+                  eps_air=1.0) -> Workload:
+    """Open-circuit film with air on top (Section Results: a Neumann top surface
+    over 5 layers of air, permittivity 1 in air against 100 in the film):
+    4-variant <111> stripe domains (period 32, 2% noise) in the nz - n_air
+    film layers, P = 0 in the air, grounded bottom electrode, open top.
+    dt 0.005, Jacobi-PCG to 1e-8."""
+    P0 = stripe_film(nx, ny, nz, seed)
+    P0[:, nz - n_air:] = 0.0
+    eps = np.full((nz, ny, nx), eps_film)
+    eps[nz - n_air:] = eps_air
+    tl, vl, th, vh = _faces(nx, ny)
+    tl[:] = DIRICHLET
+    return Workload("open_air_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, P0, tl, vl, th, vh, eps=eps,
+                    dt=0.005, steps=steps, rtol=1e-8, precision=precision, solver="pcg", n_air=n_air, seed=seed)

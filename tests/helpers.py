@@ -7,7 +7,7 @@ from paper_1202_6116_gb300 import workloads as W
 
 def oracle_grid(w: W.Workload) -> O.Grid:
     return O.Grid(w.nx, w.ny, w.nz, w.dx, w.periodic_z, w.type_lo, w.volt_lo, w.type_hi, w.volt_hi,
-                  w.eps)
+                  w.eps, w.n_air)
 
 
 def oracle_params(w: W.Workload, rtol=None) -> O.Params:
