@@ -320,9 +320,10 @@ def run_ours(args):
 # ------------------------------------------------------- batched film sweep
 
 def run_batch(args):
-    """64 independent FP32 films (32^3 .. 128x128x64, Jacobi-PCG to 1e-6,
-    triangular top-electrode ramps) advanced together: one CUDA graph launch
-    per batch step.  Tilings from the autotuner, per film shape."""
+    """64 independent FP32 films (32^3 .. 128x128x64, CG to 1e-6 with the
+    multigrid preconditioner, or Jacobi with --solver pcg; triangular
+    top-electrode ramps) advanced together: one CUDA graph launch per batch
+    step.  Tilings from the autotuner, per film shape."""
     import numpy as np
     import torch
 
@@ -337,7 +338,7 @@ def run_batch(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     ws = W.film_batch_hysteresis(nfilms=args.films, seed=4, steps=args.steps + args.warmup)
-    if args.solver == "mg":
+    if args.solver != "pcg":                       # multigrid-preconditioned CG unless Jacobi is asked for
         ws = [w.with_(solver="mg", maxit=500) for w in ws]
     t0 = time.perf_counter()
     tuned = {}
