@@ -132,6 +132,9 @@ FAMILY_SOURCES = {
     "cg": ("pf_cg.cu",),
     "mg": ("pf_mg.cu",),
     "step": ("pf_step.cu", "pf_rng.cuh"),
+    "flat": ("pf_kernels.cu",),
+    "diag": ("pf_diag.cu",),
+    "adj": ("pf_adjoint.cu",),
 }
 COMMON_SOURCES = ("pf_march.cuh", "pf_common.cuh", "pf_internal.h")
 
@@ -140,8 +143,14 @@ def family_of(kernel):
     name = kernel.split(".")[0]
     if name.startswith("mg_"):
         return "mg"
-    if name in ("cg_p", "cg_r", "cg_finish"):
+    if name in ("cg_p", "cg_r"):
         return "cg"
+    if name in ("cg_finish", "extrap", "sub_mean", "invdiag"):
+        return "flat"
+    if name == "diag":
+        return "diag"
+    if name == "tdgl_adj":
+        return "adj"
     return "step"
 
 

@@ -103,8 +103,19 @@ typedef struct {
  *                      each step as one CUDA graph (profilers cannot see
  *                      kernels inside graphs that contain conditional nodes);
  *   PF_FLAG_ADJOINT    reserve workspace for pf_adjoint_step (one more scalar
- *                      field, the adjoint potential, and one face array). */
-enum { PF_FLAG_NO_GRAPHS = 1, PF_FLAG_ADJOINT = 2 };
+ *                      field, the adjoint potential, and one face array);
+ *   PF_FLAG_WARM_LAST  start every Poisson solve of pf_step from the last
+ *                      potential, as the paper does (Section Numerical
+ *                      Performance).  Without it, forward-Euler runs that
+ *                      solve every step start solve k from the quadratic
+ *                      extrapolation 3 (phi_{k-1} - phi_{k-2}) + phi_{k-3} of
+ *                      the last three potentials (linear, then constant, for
+ *                      the first solves after pf_bind, pf_solve_potential or
+ *                      a pf_set_bc that changes an electrode layout; voltage
+ *                      changes keep the history): the same stopping test, a closer
+ *                      start, fewer iterations.  Costs two more fields of
+ *                      workspace. */
+enum { PF_FLAG_NO_GRAPHS = 1, PF_FLAG_ADJOINT = 2, PF_FLAG_WARM_LAST = 4 };
 
 typedef struct {
   int32_t steps_done;        /* steps completed by this call */
@@ -168,7 +179,8 @@ pf_status pf_bind(pf_ctx* ctx, void* P, void* phi, const void* eps, void* worksp
 pf_status pf_set_bc(pf_ctx* ctx, int32_t face, const int8_t* type_xy, const double* volts_xy);
 
 /* Advance nsteps steps of the chosen integrator.  A forward-Euler step n
- * solves A phi = b(P_n) with the current phi as initial guess, then updates
+ * solves A phi = b(P_n) from the current phi (or its extrapolation, see
+ * PF_FLAG_WARM_LAST) as initial guess, then updates
  *   P <- P - dt L (df/dP - g Lap P - E),  E = -grad phi.
  * On return P = P_nsteps and phi is the last potential solved: with Euler
  * and poisson_every <= 1 the potential of P_{nsteps-1}, with Heun that of the

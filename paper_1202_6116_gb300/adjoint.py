@@ -38,7 +38,8 @@ def _film(spec: TrajectorySpec, P0, coeffs, volt_lo, volt_hi) -> Film:
     w = spec.workload.with_(a1=c[0], a11=c[1], a12=c[2], g=c[3],
                             volt_lo=volt_lo.detach().cpu().double().numpy(),
                             volt_hi=volt_hi.detach().cpu().double().numpy())
-    return Film(w, device=spec.device, P0=P0, flags=pf.PF_FLAG_ADJOINT)
+    # the paper's warm start (last potential): recomputed segments repeat the forward pass exactly
+    return Film(w, device=spec.device, P0=P0, flags=pf.PF_FLAG_ADJOINT | pf.PF_FLAG_WARM_LAST)
 
 
 class _Trajectory(torch.autograd.Function):

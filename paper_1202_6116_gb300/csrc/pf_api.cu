@@ -75,7 +75,7 @@ std::vector<MgLevelHost> mg_levels(const pf_params* p) {
 }
 
 struct Layout {
-  size_t P_alt, r, p0, p1, q, invd, tlo, thi, vlo, vhi, ctr, part, S, diag, z, zt, total;
+  size_t P_alt, r, p0, p1, q, invd, h1, h2, tlo, thi, vlo, vhi, ctr, xctr, part, S, diag, z, zt, total;
   bool adj = false;               // psi and vzero exist (PF_FLAG_ADJOINT)
   size_t psi = 0, vzero = 0;      // adjoint potential; zero face voltages
   std::vector<MgLevelHost> mg;
@@ -106,7 +106,7 @@ bool params_valid(const pf_params* p, std::string* why) {
   }
   for (double v : {p->a1, p->a11, p->a12, p->g, p->L, p->dt})
     if (!std::isfinite(v)) return fail("coefficients must be finite");
-  if (p->flags & ~(PF_FLAG_NO_GRAPHS | PF_FLAG_ADJOINT)) return fail("unknown bits in flags");
+  if (p->flags & ~(PF_FLAG_NO_GRAPHS | PF_FLAG_ADJOINT | PF_FLAG_WARM_LAST)) return fail("unknown bits in flags");
   if (p->integrator != PF_EULER && p->integrator != PF_HEUN) return fail("integrator must be PF_EULER or PF_HEUN");
   if (p->poisson_every < 0) return fail("poisson_every must be >= 0");
   if (p->n_air < 0 || p->n_air >= p->nz) return fail("n_air must be in 0 .. nz - 1");
@@ -114,6 +114,11 @@ bool params_valid(const pf_params* p, std::string* why) {
   for (int i = 0; i < 3; ++i)
     if (p->reserved[i] != 0) return fail("reserved fields must be zero");
   return true;
+}
+
+// Does pf_step start its solves from an extrapolation of the last ones?
+bool extrapolates(const pf_params* p) {
+  return !(p->flags & PF_FLAG_WARM_LAST) && p->integrator == PF_EULER && p->poisson_every <= 1;
 }
 
 Layout layout_of(const pf_params* p) {
@@ -132,11 +137,14 @@ Layout layout_of(const pf_params* p) {
   L.p1 = take(n * w);
   L.q = take(n * w);
   L.invd = take(p->has_eps ? n * w : 0);
+  L.h1 = take(extrapolates(p) ? n * w : 0);      // potentials of the last solves (extrapolated warm start)
+  L.h2 = take(extrapolates(p) ? n * w : 0);
   L.tlo = take(nxy);
   L.thi = take(nxy);
   L.vlo = take(nxy * w);
   L.vhi = take(nxy * w);
   L.ctr = take(sizeof(long long));   // step counter of the thermal noise (zeroed by pf_bind)
+  L.xctr = take(2 * sizeof(long long));   // solves in the extrapolation history, and its block ticket
   // reduction partials: per block (flat kernels) or per tile (plane-march
   // kernels; at most one tile per column group of MTX x MTY and plane)
   const size_t max_tiles = (size_t)((p->nx + pf::MTX - 1) / pf::MTX) * ((p->ny + pf::MTY - 1) / pf::MTY) * p->nz;
@@ -261,11 +269,11 @@ struct pf_ctx {
 namespace {
 
 enum Fam {
-  F_RHS_MEAN, F_RHS, F_CG_P, F_CG_R, F_FINISH, F_SUB_MEAN, F_TDGL, F_INVDIAG, F_TDGL_ADJ, F_DIAG,
+  F_RHS_MEAN, F_RHS, F_CG_P, F_CG_R, F_FINISH, F_SUB_MEAN, F_TDGL, F_INVDIAG, F_TDGL_ADJ, F_DIAG, F_EXTRAP,
   F_MG_PRE, F_MG_RR, F_MG_COARSE, F_MG_POST1, F_MG_POST2, F_COUNT
 };
 const char* const FAM_NAMES[F_COUNT] = {"rhs_mean", "rhs",      "cg_p",     "cg_r",     "cg_finish",
-                                        "sub_mean", "tdgl",     "invdiag",  "tdgl_adj", "diag",
+                                        "sub_mean", "tdgl",     "invdiag",  "tdgl_adj", "diag",     "extrap",
                                         "mg_pre",   "mg_rr",    "mg_bottom", "mg_post1", "mg_post2"};
 
 // Multigrid families are kept per level: family id F_COUNT + level * 5 + kind.
@@ -495,6 +503,21 @@ pf_status read_scalars(pf_ctx* ctx) {
   return PF_OK;
 }
 
+// Extrapolated initial guess of the next step solve, in the bound phi buffer.
+template <typename T>
+void launch_extrap_of(pf_ctx* ctx, const pf::LaunchCfg& L) {
+  long long* xc = (long long*)(ctx->ws + ctx->lay.xctr);
+  pf::launch_extrap<T>(L, ctx->geo.n, (T*)ctx->phi, (T*)(ctx->ws + ctx->lay.h1), (T*)(ctx->ws + ctx->lay.h2), xc,
+                       (unsigned*)(xc + 1));
+}
+
+// Forget the extrapolation history (the next step solve starts from phi).
+pf_status reset_history(pf_ctx* ctx) {
+  if (!extrapolates(&ctx->prm)) return PF_OK;
+  PF_CUDA(cudaMemsetAsync(ctx->ws + ctx->lay.xctr, 0, sizeof(long long), ctx->stream));
+  return PF_OK;
+}
+
 // The adjoint solve's view: the unknown is psi and every electrode is at 0 V.
 template <typename T>
 void adjoint_view(pf_ctx* ctx, pf::Dev<T>& d) {
@@ -507,7 +530,7 @@ void adjoint_view(pf_ctx* ctx, pf::Dev<T>& d) {
 // state): r0, PCG iterations until the device flag says done, final update.
 // adj: solve for the adjoint potential instead (P is then the cotangent).
 template <typename T>
-pf_status solve(pf_ctx* ctx, const T* P, bool adj = false) {
+pf_status solve(pf_ctx* ctx, const T* P, bool adj = false, bool step_solve = false) {
   pf::Dev<T> d = dev_view<T>(ctx);
   if (adj) adjoint_view<T>(ctx, d);
   int& est_iters = adj ? ctx->est_iters_adj : ctx->est_iters;
@@ -518,6 +541,11 @@ pf_status solve(pf_ctx* ctx, const T* P, bool adj = false) {
     pf::launch_invdiag<T>(ctx->L, g, d);
     after_launch(ctx, F_INVDIAG, 2 * N * w);
     ctx->invd_dirty = false;
+  }
+  if (step_solve && extrapolates(&ctx->prm)) {
+    before_launch(ctx);
+    launch_extrap_of<T>(ctx, ctx->L);
+    after_launch(ctx, F_EXTRAP, 6 * N * w);
   }
   if (ctx->singular) {
     before_launch(ctx);
@@ -589,7 +617,7 @@ void step_kernel_counts(const pf_ctx* ctx, int refresh, int64_t* fixed, int64_t*
                          ? 4 * (int64_t)mg_tail_start(ctx->lay, ctx->prm.precision == PF_FP32 ? 4 : 8) + 1
                          : 0;
   const bool heun = ctx->prm.integrator == PF_HEUN;
-  const int64_t per_solve = (ctx->singular ? 2 : 0) + 2 + vc;
+  const int64_t per_solve = (ctx->singular ? 2 : 0) + 2 + vc + (extrapolates(&ctx->prm) ? 1 : 0);
   *fixed = (refresh ? (heun ? 2 : 1) * per_solve : 0) + (heun ? 2 : 1);
   *per_iter = 2 + vc;
 }
@@ -638,6 +666,7 @@ cudaError_t append_step(pf_ctx* ctx, cudaGraph_t graph, std::vector<cudaGraphNod
     cudaGraphConditionalHandle h = 0;
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
     segment([&] {
+      if (extrapolates(&ctx->prm)) launch_extrap_of<T>(ctx, ctx->L);
       if (ctx->singular) pf::launch_rhs_mean<T>(ctx->L, g, d, P);
       pf::launch_rhs<T>(ctx->L, g, d, P, h, 1);
       if (mg) vcycle<T>(ctx, 0);
@@ -771,7 +800,7 @@ pf_status run_steps(pf_ctx* ctx, int nsteps) {
     T* P = Pbuf[ctx->cur];
     T* Q = Pbuf[ctx->cur ^ 1];
     if (refresh) {
-      pf_status st = solve<T>(ctx, P);
+      pf_status st = solve<T>(ctx, P, false, true);
       if (st != PF_OK) return st;
     }
     before_launch(ctx);
@@ -780,7 +809,7 @@ pf_status run_steps(pf_ctx* ctx, int nsteps) {
     PF_CUDA(cudaGetLastError());
     if (heun) {
       if (refresh) {
-        pf_status st = solve<T>(ctx, Q);
+        pf_status st = solve<T>(ctx, Q, false, true);
         if (st != PF_OK) return st;
       }
       before_launch(ctx);
@@ -989,10 +1018,15 @@ pf_status pf_set_bc(pf_ctx* ctx, int32_t face, const int8_t* type_xy, const doub
     PF_CUDA(cudaStreamSynchronize(ctx->stream));
   }
   std::vector<int8_t>& h = face == PF_ZLO ? ctx->tlo_h : ctx->thi_h;
+  const bool types_changed = std::memcmp(h.data(), type_xy, nxy) != 0;
   std::memcpy(h.data(), type_xy, nxy);
   recompute_singular(ctx);
   ctx->invd_dirty = true;
   ctx->gen += 1;
+  if (types_changed) {           // a new electrode layout: the old potentials are no guide
+    st = reset_history(ctx);
+    if (st != PF_OK) return st;
+  }
   return upload_masks(ctx);
 }
 
@@ -1035,6 +1069,8 @@ pf_status pf_solve_potential(pf_ctx* ctx, pf_step_info* info) {
   if (st != PF_OK) return st;
   st = ctx->prm.precision == PF_FP32 ? solve<float>(ctx, (const float*)ctx->P_user)
                                      : solve<double>(ctx, (const double*)ctx->P_user);
+  if (st != PF_OK) return st;
+  st = reset_history(ctx);
   if (st != PF_OK) return st;
   return finish_info(ctx, 0, info);
 }

@@ -100,6 +100,9 @@ void launch_tdgl(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, 
                  int corr, const Noise& nz);
 template <typename T>
 void launch_invdiag(const LaunchCfg& L, const Geo& g, const Dev<T>& d);
+// Extrapolated initial guess of a time step's solve (see k_extrap).
+template <typename T>
+void launch_extrap(const LaunchCfg& L, long long n, T* phi, T* h1, T* h2, long long* nsolve, unsigned* ticket);
 // Adjoint update (pf_adjoint.cu): lam_out from lam, the adjoint potential psi
 // and the state P; adds the parameter sensitivities to grad[4] and, when
 // gv_lo/gv_hi are non-NULL, the face-voltage sensitivities.

@@ -5,6 +5,8 @@
 //   k_cg_finish  last deferred x update / zero solution, mean of x
 //   k_sub_mean   x -= mean(x)                           (singular problems)
 //   k_invdiag    1/diag(A) when a permittivity field is bound
+//   k_extrap     initial guess of a time step's Poisson solve extrapolated
+//                from the last three solutions
 //
 // All reductions use the last-block pattern of pf_common.cuh: deterministic,
 // and no block ever waits on another.  The CG scalars (alpha, beta, the
@@ -132,6 +134,63 @@ __global__ void __launch_bounds__(NTHREADS) k_invdiag(Geo g, Bc<T> bc, const T* 
   }
 }
 
+// Initial guess of solve number k of a time series (k = *nsolve): the
+// quadratic extrapolation 3 (phi_1 - phi_2) + phi_3 of the last three
+// solutions (phi_1 = phi, the last; phi_2 = h1; phi_3 = h2), linear 2 phi_1 -
+// phi_2 for the third solve, the last solution for the second and the given
+// phi for the first.  The history shifts (h2 <- h1, h1 <- phi) and the last
+// block to finish advances the count (every block reads it first).
+// Streams phi, h1, h2 once: read 3 words, write 3 words per cell.
+template <typename T>
+__device__ __forceinline__ T extrap_guess(long long k, T f, T a, T b) {
+  if (k <= 1) return f;
+  if (k == 2) return f + (f - a);
+  return T(3) * (f - a) + b;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FLAT_THREADS) k_extrap(long long n, T* __restrict__ phi, T* __restrict__ h1,
+                                                        T* __restrict__ h2, long long* nsolve, unsigned* ticket) {
+  using V = typename Vec16<T>::type;
+  constexpr int NV = 16 / sizeof(T);
+  __shared__ bool last;
+  const long long k = *nsolve;
+  const long long stride = (long long)gridDim.x * FLAT_THREADS;
+  const long long nvec = n / NV;
+  for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < nvec; i += stride) {
+    V fv = reinterpret_cast<const V*>(phi)[i];
+    const V av = reinterpret_cast<const V*>(h1)[i];
+    const V bv = reinterpret_cast<const V*>(h2)[i];
+    V gv;
+    const T* f = reinterpret_cast<const T*>(&fv);
+    const T* a = reinterpret_cast<const T*>(&av);
+    const T* b = reinterpret_cast<const T*>(&bv);
+    T* gs = reinterpret_cast<T*>(&gv);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) gs[j] = extrap_guess(k, f[j], a[j], b[j]);
+    reinterpret_cast<V*>(h2)[i] = av;
+    reinterpret_cast<V*>(h1)[i] = fv;
+    reinterpret_cast<V*>(phi)[i] = gv;
+  }
+  for (long long i = nvec * NV + blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += stride) {
+    const T f = phi[i], a = h1[i], b = h2[i];
+    h2[i] = a;
+    h1[i] = f;
+    phi[i] = extrap_guess(k, f, a, b);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    *ticket = 0u;
+    *nsolve = k + 1;
+    __threadfence();
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 
 template <typename T>
@@ -149,7 +208,13 @@ void launch_invdiag(const LaunchCfg& L, const Geo& g, const Dev<T>& d) {
   k_invdiag<T><<<L.grid, L.block, 0, L.stream>>>(g, d.bc, d.eps, d.invd);
 }
 
+template <typename T>
+void launch_extrap(const LaunchCfg& L, long long n, T* phi, T* h1, T* h2, long long* nsolve, unsigned* ticket) {
+  k_extrap<T><<<L.flat_grid, FLAT_THREADS, 0, L.stream>>>(n, phi, h1, h2, nsolve, ticket);
+}
+
 #define PF_INSTANTIATE(T)                                                                                   \
+  template void launch_extrap<T>(const LaunchCfg&, long long, T*, T*, T*, long long*, unsigned*);          \
   template void launch_cg_finish<T>(const LaunchCfg&, const Geo&, const Dev<T>&, int);                      \
   template void launch_sub_mean<T>(const LaunchCfg&, const Geo&, const Dev<T>&);                            \
   template void launch_invdiag<T>(const LaunchCfg&, const Geo&, const Dev<T>&);

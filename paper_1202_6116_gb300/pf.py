@@ -21,6 +21,7 @@ PF_NEUMANN, PF_DIRICHLET = 0, 1
 PF_EULER, PF_HEUN = 0, 1
 PF_FLAG_NO_GRAPHS = 1
 PF_FLAG_ADJOINT = 2
+PF_FLAG_WARM_LAST = 4
 
 STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_CUDA", 3: "PF_ERR_NOCONV", 4: "PF_ERR_NONFINITE",
                 5: "PF_ERR_TIMEOUT", 6: "PF_ERR_STATE", 7: "PF_ERR_NOTIMPL"}

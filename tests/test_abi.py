@@ -86,8 +86,10 @@ def test_workspace_bytes_and_validation(L):
     q.periodic_z = 0
     assert pf.pf_workspace_bytes(q) > 0
     q = good_params()
-    q.flags = 4
+    q.flags = 8
     assert pf.pf_workspace_bytes(q) == 0
+    q.flags = pf.PF_FLAG_WARM_LAST
+    assert 0 < pf.pf_workspace_bytes(q) < pf.pf_workspace_bytes(good_params())   # no history fields
     q.flags = pf.PF_FLAG_NO_GRAPHS
     assert pf.pf_workspace_bytes(q) > 0
 

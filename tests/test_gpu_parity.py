@@ -44,9 +44,11 @@ def grounded_32():
 
 
 def test_fp64_grounded_film_200_steps(grounded_32):
-    """32^3 FP64 film between grounded electrodes, 200 steps at CG 1e-12."""
+    """32^3 FP64 film between grounded electrodes, 200 steps at CG 1e-12, each
+    solve warm-started from the last potential as in the paper (and in the
+    oracle): the same results and about the same Jacobi-PCG iteration count."""
     w, (Po, phio, sto, io), (Pt, phit, _, _) = grounded_32
-    P, phi, st, info = gpu_run(w)
+    P, phi, st, info = gpu_run(w, flags=pf.PF_FLAG_WARM_LAST)
     assert st == pf.PF_OK and sto == O.OK
     assert relerr(P, Po) <= FP64_TOL
     assert relerr(phi, phio) <= FP64_TOL
@@ -54,6 +56,41 @@ def test_fp64_grounded_film_200_steps(grounded_32):
     assert relerr(phi, phit) <= FP64_TOL
     assert abs(info["total_iters"] - io["total_iters"]) <= 0.02 * io["total_iters"] + 5
     assert info["graph_steps"] == w.steps          # every step ran as one CUDA graph
+
+
+def test_fp64_extrapolated_warm_start(grounded_32):
+    """The default start of each step solve extrapolates the last three
+    potentials: the same results within the solve tolerance, fewer
+    iterations than the last-potential start."""
+    w, (Po, phio, sto, io), (Pt, phit, _, _) = grounded_32
+    P, phi, st, info = gpu_run(w)
+    assert st == pf.PF_OK
+    assert relerr(P, Pt) <= FP64_TOL
+    assert relerr(phi, phit) <= FP64_TOL
+    assert info["total_iters"] < 0.8 * io["total_iters"]      # 1e-12 Jacobi-PCG: about 0.72
+
+
+def test_extrapolation_history_survives_calls_and_resets():
+    """Steps split over calls equal one call (the history lives on the device);
+    a standalone solve resets it (the next step starts from that potential)."""
+    w = mixed_workload(40, 24, 12, 61, steps=8, rtol=1e-13)
+    a = Film(w)
+    a.step(8)
+    Pa, phia = a.numpy()
+    a.close()
+    b = Film(w)
+    b.step(3)
+    b.step(5)
+    Pb, phib = b.numpy()
+    b.close()
+    assert np.array_equal(Pa, Pb) and np.array_equal(phia, phib)
+    c = Film(w)
+    c.step(3)
+    c.solve_potential()
+    _, ic = c.step(5)
+    Pc, _ = c.numpy()
+    c.close()
+    assert relerr(Pc, Pa) <= FP64_TOL and ic["total_iters"] > 0
 
 
 def test_graph_and_host_driven_steps_agree():
@@ -142,7 +179,8 @@ def test_homogeneous_recurrence_on_gpu():
 
 def test_noconv_is_reported_and_state_valid():
     w = mixed_workload(32, 16, 8, 9, steps=3, rtol=1e-14)
-    P, phi, st, info = gpu_run(w, poisson_maxit=2)
+    # unconverged iterates depend on the initial guess: start from the last potential, as the oracle does
+    P, phi, st, info = gpu_run(w, poisson_maxit=2, flags=pf.PF_FLAG_WARM_LAST)
     assert st == pf.PF_ERR_NOCONV
     assert info["nonconverged"] == 3 and info["last_iters"] == 2 and info["steps_done"] == 3
     assert np.isfinite(P).all() and np.isfinite(phi).all()
