@@ -17,6 +17,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -154,12 +155,20 @@ def family_of(kernel):
     return "step"
 
 
+def _code_only(text):
+    """Source text without comments and blank space (edits of comments leave
+    the compiled kernel, and so the hash, unchanged)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash(kernel):
-    """Hash of the device sources that define a kernel family."""
+    """Hash of the device code that defines a kernel family."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1202_6116_gb300", "csrc")
     for f in sorted(FAMILY_SOURCES[family_of(kernel)] + COMMON_SOURCES):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        h.update(_code_only(open(os.path.join(csrc, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

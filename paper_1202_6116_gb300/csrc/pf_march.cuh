@@ -4,16 +4,20 @@
 // BX = TXT * VX: each thread owns VX consecutive cells of a row (one 16-byte
 // vector: 4 floats or 2 doubles; VX = 1 when nx is not a multiple of that).
 // Tiles are handed out dynamically (an atomic counter), so blocks that finish
-// early take more work.  Along its z range the block streams
-//   - the raw inputs of the stencil field (NH arrays) with a one-cell halo
-//     ring, and the own-cell-only inputs (NO arrays), copied global -> shared
-//     with cp.async D planes ahead into a ring of D + 2 stages (16-byte copies
-//     for the vectors, 4/8-byte copies for the x halo).  Each thread copies,
-//     and later reads back, only its own cells and the halo cells it fills,
-//     so the stages need no block barrier;
-//   - the stencil field itself (the caller's val functor applied to the raw
-//     values, e.g. p = r/diag + beta p_old) through a three-plane shared buffer
-//     (z-1, z, z+1) behind one __syncthreads per plane.
+// early take more work.  Along its z range the block streams the raw inputs
+// of the stencil (NH arrays) with a one-cell halo ring, and the own-cell-only
+// inputs (NO arrays), copied global -> shared with cp.async D planes ahead
+// into a ring of D + 2 stages (16-byte copies for the vectors, 4/8-byte
+// copies for the x halo).  Two walks use them:
+//   - march: the stencil field (the caller's val functor applied to the raw
+//     values, e.g. p = r/diag + beta p_old) is formed once per cell into a
+//     shared buffer of plane z (ring of three planes), read by the in-plane
+//     neighbours after the plane's barrier;
+//   - march_direct: the stencil is the raw input itself, read straight from
+//     the stage of plane z.
+// In both, each thread keeps its own column's values of planes z-1, z, z+1
+// in registers, so only in-plane neighbours cross threads, all within the
+// current plane: one __syncthreads per plane orders every shared access.
 // x neighbours inside a vector come from registers, across vectors of one
 // warp row from shuffles, across the tile edge from the halo.  Periodic x/y
 // wrap is resolved in the halo source addresses; ragged tiles put their
