@@ -56,6 +56,7 @@ def lib():
         L.or_solve_potential.argtypes = [vp, vp, vp, d, i, vp, vp]
         L.or_step.argtypes = [vp, vp, vp, vp, i, vp]
         L.or_rate.argtypes = [vp, vp, vp, vp, vp]
+        L.or_rate_at.argtypes = [vp, vp, vp, vp, vp, i, vp]
         L.or_step_ex.argtypes = [vp, vp, i, i, l, vp, vp, i, d, C.c_ulonglong, vp]
         L.or_philox.argtypes = [C.c_ulonglong, C.c_ulonglong, C.c_ulonglong, vp]
         L.or_gauss4.argtypes = [C.c_ulonglong, C.c_ulonglong, C.c_ulonglong, vp]
@@ -225,6 +226,17 @@ def rate(G: Grid, prm: Params, P, phi):
     out = np.empty_like(P)
     g, p = G._c(), prm._c()
     lib().or_rate(C.byref(g), C.byref(p), _ptr(P), _ptr(phi), _ptr(out))
+    return out
+
+
+def rate_at(G: Grid, prm: Params, P, phi, cells):
+    """TDGL rate at the listed linear cell indices: array (len(cells), 3)."""
+    P = _f64(P).reshape((3,) + G.shape)
+    phi = _f64(phi).reshape(G.shape)
+    idx = np.ascontiguousarray(cells, dtype=np.int64)
+    out = np.empty((len(idx), 3))
+    g, p = G._c(), prm._c()
+    lib().or_rate_at(C.byref(g), C.byref(p), _ptr(P), _ptr(phi), _ptr(idx), len(idx), _ptr(out))
     return out
 
 

@@ -74,14 +74,18 @@ double or_landau_energy(const double* P, long n, double a1, double a11, double a
 }
 
 /* df/dP_i = 2 a1 P_i + 4 a11 P_i^3 + 2 a12 P_i (P_j^2 + P_k^2), from Eq. F_bulk. */
+static void landau_at(const double p[3], double a1, double a11, double a12, double h[3]) {
+  for (int i = 0; i < 3; ++i) {
+    int j = (i + 1) % 3, k = (i + 2) % 3;
+    h[i] = 2.0 * a1 * p[i] + 4.0 * a11 * p[i] * p[i] * p[i] + 2.0 * a12 * p[i] * (p[j] * p[j] + p[k] * p[k]);
+  }
+}
+
 void or_landau_force(const double* P, long n, double a1, double a11, double a12, double* out) {
   for (long c = 0; c < n; ++c) {
-    double p[3] = {P[c], P[n + c], P[2 * n + c]};
-    for (int i = 0; i < 3; ++i) {
-      int j = (i + 1) % 3, k = (i + 2) % 3;
-      out[i * n + c] = 2.0 * a1 * p[i] + 4.0 * a11 * p[i] * p[i] * p[i] +
-                       2.0 * a12 * p[i] * (p[j] * p[j] + p[k] * p[k]);
-    }
+    double p[3] = {P[c], P[n + c], P[2 * n + c]}, h[3];
+    landau_at(p, a1, a11, a12, h);
+    for (int i = 0; i < 3; ++i) out[i * n + c] = h[i];
   }
 }
 
@@ -113,20 +117,21 @@ static void zero_air(const or_grid* G, double* P) {
 /* Eq. dF_grad/dP: Lap f as the sum over the cell's interior faces of
  * (f_nb - f_c)/dx^2.  A non-periodic z face is dropped (zero normal flux),
  * and so is a film/air face; air cells get 0. */
+static double laplacian_at(const or_grid* G, const double* f, int x, int y, int z) {
+  long c = cell_index(G, x, y, z);
+  double acc = 0.0;
+  for (int d = 0; d < 3; ++d)
+    for (int s = -1; s <= 1; s += 2) {
+      long nb;
+      if (wall_face(G, x, y, z, d, s, &nb)) acc += f[nb] - f[c];
+    }
+  return acc / (G->dx * G->dx);
+}
+
 void or_laplacian(const or_grid* G, const double* f, double* out) {
-  double h2 = 1.0 / (G->dx * G->dx);
   for (int z = 0; z < G->nz; ++z)
     for (int y = 0; y < G->ny; ++y)
-      for (int x = 0; x < G->nx; ++x) {
-        long c = cell_index(G, x, y, z);
-        double acc = 0.0;
-        for (int d = 0; d < 3; ++d)
-          for (int s = -1; s <= 1; s += 2) {
-            long nb;
-            if (wall_face(G, x, y, z, d, s, &nb)) acc += f[nb] - f[c];
-          }
-        out[c] = acc * h2;
-      }
+      for (int x = 0; x < G->nx; ++x) out[cell_index(G, x, y, z)] = laplacian_at(G, f, x, y, z);
 }
 
 /* Face permittivity between cells c and nb: the harmonic mean of the two
@@ -216,26 +221,33 @@ void or_diag(const or_grid* G, double* dg) {
 
 /* Eqs. F_elec: E = -grad phi, per component the difference of the two face
  * values of phi divided by dx; face values per reading R3. */
+/* E at cell (x,y,z) from face values (R3). */
+static void field_at(const or_grid* G, const double* phi, int x, int y, int z, double E[3]) {
+  double ih = 1.0 / G->dx;
+  long c = cell_index(G, x, y, z);
+  for (int d = 0; d < 3; ++d) {
+    double f[2];
+    for (int s = -1; s <= 1; s += 2) {
+      long nb;
+      int bt;
+      double bv;
+      if (face_of(G, x, y, z, d, s, &nb, &bt, &bv))
+        f[(s + 1) / 2] = 0.5 * (phi[c] + phi[nb]);
+      else
+        f[(s + 1) / 2] = (bt == 1) ? bv : phi[c];
+    }
+    E[d] = -(f[1] - f[0]) * ih;
+  }
+}
+
 void or_field(const or_grid* G, const double* phi, double* E) {
   long n = ncells(G);
-  double ih = 1.0 / G->dx;
   for (int z = 0; z < G->nz; ++z)
     for (int y = 0; y < G->ny; ++y)
       for (int x = 0; x < G->nx; ++x) {
-        long c = cell_index(G, x, y, z);
-        for (int d = 0; d < 3; ++d) {
-          double f[2];
-          for (int s = -1; s <= 1; s += 2) {
-            long nb;
-            int bt;
-            double bv;
-            if (face_of(G, x, y, z, d, s, &nb, &bt, &bv))
-              f[(s + 1) / 2] = 0.5 * (phi[c] + phi[nb]);
-            else
-              f[(s + 1) / 2] = (bt == 1) ? bv : phi[c];
-          }
-          E[(long)d * n + c] = -(f[1] - f[0]) * ih;
-        }
+        double e[3];
+        field_at(G, phi, x, y, z, e);
+        for (int d = 0; d < 3; ++d) E[(long)d * n + cell_index(G, x, y, z)] = e[d];
       }
 }
 
@@ -447,6 +459,27 @@ static void add_noise(const or_grid* G, double* P, double amp, unsigned long lon
     double g[4];
     or_gauss4(seed, step, (unsigned long long)c, g);
     for (int i = 0; i < 3; ++i) P[(long)i * n + c] += amp * g[i];
+  }
+}
+
+/* The TDGL rate at m listed cells (linear indices), out[3 * k + i] for
+ * component i of cell k: the same per-cell terms as or_rate, evaluated only
+ * there, so that a state of any size can be checked at samples. */
+void or_rate_at(const or_grid* G, const or_params* prm, const double* P, const double* phi, const long* cells,
+                int m, double* out) {
+  long n = ncells(G), nxy = (long)G->nx * G->ny;
+  for (int k = 0; k < m; ++k) {
+    long c = cells[k];
+    int z = (int)(c / nxy), y = (int)((c % nxy) / G->nx), x = (int)(c % G->nx);
+    if (!is_film(G, z)) {
+      out[3 * k] = out[3 * k + 1] = out[3 * k + 2] = 0.0;
+      continue;
+    }
+    double p[3] = {P[c], P[n + c], P[2 * n + c]}, h[3], E[3];
+    landau_at(p, prm->a1, prm->a11, prm->a12, h);
+    field_at(G, phi, x, y, z, E);
+    for (int i = 0; i < 3; ++i)
+      out[3 * k + i] = prm->L * (-h[i] + prm->g * laplacian_at(G, P + (long)i * n, x, y, z) + E[i]);
   }
 }
 

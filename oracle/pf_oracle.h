@@ -119,6 +119,11 @@ enum { OR_EULER = 0, OR_HEUN = 1 };
 /* TDGL rate L(-df/dP + g Lap P + E(phi)) at the state P (3N) and potential phi. */
 void or_rate(const or_grid* G, const or_params* prm, const double* P, const double* phi, double* R);
 
+/* The rate of or_rate at m listed cells (linear indices): out[3k + i] is
+ * component i at cells[k].  For checks of large states at sampled cells. */
+void or_rate_at(const or_grid* G, const or_params* prm, const double* P, const double* phi, const long* cells,
+                int m, double* out);
+
 /* nsteps steps of forward Euler (OR_EULER) or of the paper's predictor-corrector
  * (OR_HEUN: P^p = P^c + dt R(P^c); P^c <- P^c + dt (R(P^c) + R(P^p))/2, each
  * rate with the potential of its own state).  The potential is solved only on

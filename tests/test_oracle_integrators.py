@@ -165,3 +165,25 @@ def test_heun_energy_decreases():
         P, phi, st, _ = O.step_ex(G, prm, P, phi, 1, "heun")
         F.append(O.energy(G, prm, P))
     assert all(b < a for a, b in zip(F, F[1:]))
+
+
+@pytest.mark.parametrize("kind", ["mixed", "air", "periodic"])
+def test_rate_at_samples_equals_the_whole_grid_rate(kind):
+    """or_rate_at (used to check large GPU states at sampled cells) evaluates
+    the same per-cell terms as or_rate."""
+    rng = np.random.default_rng(8)
+    if kind == "air":
+        eps = rng.uniform(1.0, 3.0, (7, 6, 9))
+        G = O.Grid(9, 6, 7, 1.0, False, np.ones((6, 9), np.int8), None, np.zeros((6, 9), np.int8), None, eps, 2)
+    elif kind == "periodic":
+        G = O.Grid(9, 6, 7, 1.0, True)
+    else:
+        G = strip_grid(9, 6, 7)
+    prm = O.Params(g=0.3, L=1.3)
+    P = rng.uniform(-0.5, 0.5, (3,) + G.shape)
+    if kind == "air":
+        P[:, G.nz - G.n_air:] = 0.0
+    phi = rng.uniform(-1, 1, G.shape)
+    R = O.rate(G, prm, P, phi).reshape(3, -1)
+    cells = np.arange(G.n)
+    assert np.array_equal(O.rate_at(G, prm, P, phi, cells), R.T)
