@@ -20,7 +20,10 @@ using CgPipe = Pipe<T, typename FieldOf<T, EPS>::type, MTX, MTY, VX, EPS ? 4 : 2
 
 // MG = false: z = r/diag (Jacobi), r is the staged input.  MG = true: z comes
 // from the V-cycle and is the staged input.
-template <typename T, bool EPS, bool MG, int VX>
+// DIRECT (multigrid, eps = 1): the stencil of p = z + beta p_old is formed
+// from the staged planes of z and p_old at each of the seven cells (no field
+// buffer); otherwise p goes through the march's shared field buffer.
+template <typename T, bool EPS, bool MG, int VX, bool DIRECT = false>
 __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g, Bc<T> bc, const T* __restrict__ eps,
                                                   const T* __restrict__ invd, const T* __restrict__ r, T* p0,
                                                   T* p1, T* __restrict__ q, T* __restrict__ x, double* part,
@@ -88,11 +91,36 @@ __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g
     store_n<T, VX>(pnew + c, ps);
     store_n<T, VX>(q + c, qs);
   };
+  // direct form: p at a cell from the raw (z, p_old) pair
+  auto pval = [&](const Raw<T, NH>& rw) -> T { return first ? rw.v[0] : rw.v[0] + beta * rw.v[1]; };
+  auto emit_d = [&](int xy, int, const Stencil7<Raw<T, NH>>& sr, const T (&o)[1], const bool bt) -> Out {
+    Stencil7<T> st;
+    st.c = pval(sr.c);
+    st.xm = pval(sr.xm);
+    st.xp = pval(sr.xp);
+    st.ym = pval(sr.ym);
+    st.yp = pval(sr.yp);
+    st.zm = pval(sr.zm);
+    st.zp = pval(sr.zp);
+    st.zb = sr.zb;
+    st.za = sr.za;
+    const bool B = bt;
+    const int dlo = (B && st.zb < 0) ? (int)bc.tlo[xy] : 0;
+    const int dhi = (B && st.za < 0) ? (int)bc.thi[xy] : 0;
+    const T qv = apply_bt(st, dlo, dhi, ih2, bt);
+    apq.add(st.c, qv);
+    return Out{first ? o[0] : o[0] + alpha * sr.c.v[1], st.c, qv};
+  };
   const TileSched ts{&S->sched_next, &S->sched_done};
   for (long long t = sched_take(ts, &tile_slot); t < mc.ntiles; t = sched_take(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(g, t, mc);
     apq = Acc<T>();
-    march<T, F, Out, MTX, MTY, VX, NH, 1, CG_D>(g, s, smem, hsrc, osrc, val, emit, post);
+    if constexpr (DIRECT) {
+      static_assert(MG && !EPS, "the direct form is the multigrid search direction with eps = 1");
+      march_direct<T, Out, MTX, MTY, VX, NH, 1, CG_D>(g, s, smem, hsrc, osrc, emit_d, post);
+    } else {
+      march<T, F, Out, MTX, MTY, VX, NH, 1, CG_D>(g, s, smem, hsrc, osrc, val, emit, post);
+    }
     double v[1] = {apq.value()};
     tile_partials<1, MTX * MTY>(v, part, t);
   }
@@ -198,13 +226,15 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_cg_r(Geo g, Bc<T> bc, const T*
 
 template <typename T, bool EPS, bool MG, int VX>
 static void launch_cg_p_t(const LaunchCfg& L, const Geo& g, const Dev<T>& d) {
-  const size_t bytes = CgPipe<T, EPS, VX>::bytes();
+  constexpr bool DIRECT = MG && !EPS;
+  using PD = Pipe<T, void, MTX, MTY, VX, 2, 1, CG_D>;
+  const size_t bytes = DIRECT ? PD::bytes() : CgPipe<T, EPS, VX>::bytes();
   static bool once = false;
   if (!once) {
-    allow_smem(k_cg_p<T, EPS, MG, VX>, bytes);
+    allow_smem(k_cg_p<T, EPS, MG, VX, DIRECT>, bytes);
     once = true;
   }
-  k_cg_p<T, EPS, MG, VX><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(
+  k_cg_p<T, EPS, MG, VX, DIRECT><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(
       g, d.bc, d.eps, d.invd, MG ? d.z : d.r, d.p0, d.p1, d.q, d.phi, d.part, d.S, L.march);
 }
 
