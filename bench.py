@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 METRIC = "TDGL cell-steps/s incl. Poisson solve"
 UNIT = "cell-steps/s"
 L2_BYTES = 129 * 2 ** 20
-WORKLOADS = ("tip", "strips", "grounded", "batch")
+WORKLOADS = ("tip", "strips", "grounded", "batch", "adjoint", "air")
 
 
 def make_workload(name, seed_offset=0, solver=None, size=None):
@@ -42,6 +42,8 @@ def make_workload(name, seed_offset=0, solver=None, size=None):
         w = W.film_tip_fp32(seed=2 + seed_offset, **dims)
     elif name == "grounded":
         w = W.film_fp64_grounded(seed=0 + seed_offset, **dims)
+    elif name == "air":
+        w = W.film_open_air(seed=5 + seed_offset, **dims)
     else:
         raise ValueError(name)
     if solver == "mg":
@@ -58,15 +60,26 @@ def sample_workload(name):
         return W.film_strip_fp32(64, 64, 16, seed=1), "64x64x16 film of the strip-electrode recipe"
     if name == "tip":
         return W.film_tip_fp32(128, 128, 16, seed=2), "128x128x16 film of the tip-electrode recipe"
+    if name == "air":
+        return W.film_open_air(32, 32, 21, seed=5), "32x32x21 film of the open-air recipe"
     return W.film_fp64_grounded(32, 32, 32, seed=0), "the full 32x32x32 grounded film"
 
 
-def workload_config(w, name, flush):
-    return {"workload": "%s %dx%dx%d %s %s rtol=%g dt=%g" % (name, w.nx, w.ny, w.nz, w.precision,
-                                                             "MG-PCG" if w.solver == "mg" else "Jacobi-PCG",
-                                                             w.rtol, w.dt),
-            "cells": w.n, "precision": w.precision, "solver": w.solver, "poisson_rtol": w.rtol,
-            "dt": w.dt, "l2": flush}
+def workload_config(w, name, flush, args=None):
+    c = {"workload": "%s %dx%dx%d %s %s rtol=%g dt=%g" % (name, w.nx, w.ny, w.nz, w.precision,
+                                                          "MG-PCG" if w.solver == "mg" else "Jacobi-PCG",
+                                                          w.rtol, w.dt),
+         "cells": w.n, "precision": w.precision, "solver": w.solver, "poisson_rtol": w.rtol,
+         "dt": w.dt, "l2": flush}
+    if args is not None:
+        c["integrator"] = args.integrator
+        c["poisson_every"] = max(1, args.poisson_every)
+        c["warm_start"] = "last potential" if args.warm_last else "extrapolated (last three potentials)"
+        if args.noise > 0:
+            c["noise_sigma"] = args.noise
+        if w.n_air:
+            c["n_air"] = w.n_air
+    return c
 
 
 # --------------------------------------------------------------------- clocks
@@ -224,7 +237,14 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     w = make_workload(args.workload, seed_offset=rank, solver=args.solver, size=args.size)
-    film = Film(w, device=dev, **({"flags": 1} if args.no_graphs else {}))
+    if args.dt:
+        w = w.with_(dt=args.dt)
+    over = {"flags": (pf.PF_FLAG_NO_GRAPHS if args.no_graphs else 0) | (pf.PF_FLAG_WARM_LAST if args.warm_last else 0),
+            "integrator": pf.PF_HEUN if args.integrator == "heun" else pf.PF_EULER,
+            "poisson_every": args.poisson_every}
+    film = Film(w, device=dev, **over)
+    if args.noise > 0:
+        film.set_noise(args.noise, 12345)
     stream = film.stream
     flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     flush = "flushed (a %d MiB buffer is written between timed steps)" % (2 * L2_BYTES // 2 ** 20)
@@ -325,7 +345,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w.precision == "fp32" else "f64",
                 "data": "synthetic (seeded SplitMix64 initial state, electrode masks of the workload)",
-                "config": workload_config(w, args.workload, flush),
+                "config": workload_config(w, args.workload, flush, args),
                 "poisson_iters_per_step": iters / args.steps,
                 "graph_steps": graph_steps,
                 "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
@@ -427,6 +447,65 @@ def run_batch(args):
             "loop_example": {"film": 0, "volts": [round(x, 4) for x in loops[:, 0, 0][-5:].tolist()],
                              "mean_pz": [round(x, 5) for x in loops[:, 0, 3][-5:].tolist()]},
             "clocks": clk, "impl": "ours"}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------- differentiation workload
+
+def run_adjoint(args):
+    """Gradient of the differentiation workload (128x128x32 FP64, strip
+    electrodes, 500 steps, MG-PCG to 1e-12) through the discrete adjoint: forward pass with a
+    checkpoint every 50 steps, backward pass recomputing each segment.  The
+    metric counts forward cell-steps of the trajectory per second of the whole
+    forward + backward computation."""
+    import torch
+
+    from paper_1202_6116_gb300 import adjoint as A
+    from paper_1202_6116_gb300 import build as B
+    from paper_1202_6116_gb300 import workloads as W
+
+    B.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = W.film_adjoint_fp64().with_(solver="mg", maxit=500)
+    steps = args.steps
+    spec = A.TrajectorySpec(w, steps=steps, checkpoint_every=50, device="cuda")
+    P0 = torch.as_tensor(w.P0, device=dev)
+    target = torch.zeros_like(P0)
+    target[2] = 1.0
+
+    def one():
+        coeffs = torch.tensor([w.a1, w.a11, w.a12, w.g], dtype=torch.float64, device=dev, requires_grad=True)
+        vlo = torch.as_tensor(w.volt_lo, device=dev).clone().requires_grad_(True)
+        vhi = torch.as_tensor(w.volt_hi, device=dev).clone().requires_grad_(True)
+        P = A.trajectory(P0, coeffs, vlo, vhi, spec)
+        loss = ((P[2] - target[2]) ** 2).mean()
+        loss.backward()
+        return coeffs.grad.detach().cpu().numpy()
+
+    for _ in range(max(1, args.warmup // 3)):
+        one()
+    clocks = ClockSampler(0)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    grad = one()
+    e1.record(stream)
+    e1.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    line = {"metric": "TDGL cell-steps/s of forward + discrete adjoint (gradient of a trajectory)",
+            "value": w.n * steps / (wall), "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * wall / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded SplitMix64 initial state, strip electrodes)",
+            "config": {"workload": "adjoint 128x128x32 fp64 MG-PCG rtol=1e-12 dt=0.01, checkpoint every 50",
+                       "cells": w.n, "loss": "mean (P_z - 1)^2 of the final state"},
+            "device_ms": ms, "grad_a1_a11_a12_g": [float(v) for v in grad], "clocks": clk, "impl": "ours"}
     print(json.dumps(line))
 
 
@@ -532,6 +611,13 @@ def main():
                     help="steps of the FP32-against-FP64 comparison on the strip film (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--films", type=int, default=64, help="films of the batch workload")
+    ap.add_argument("--integrator", choices=("euler", "heun"), default="euler",
+                    help="forward Euler or the paper's predictor-corrector")
+    ap.add_argument("--poisson-every", type=int, default=1, help="solve the potential on every k-th step only")
+    ap.add_argument("--dt", type=float, default=None, help="override the workload's time step")
+    ap.add_argument("--noise", type=float, default=0.0, help="thermal random force sigma (0: off)")
+    ap.add_argument("--warm-last", action="store_true",
+                    help="start each solve from the last potential (the paper's scheme) instead of extrapolating")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel from the host (profilers cannot see kernels inside CUDA graphs "
                          "with conditional nodes)")
@@ -544,6 +630,10 @@ def main():
         args.steps = 300 if args.steps is None else args.steps
         args.warmup = 5 if args.warmup is None else max(3, args.warmup)
         run_batch(args)
+    elif args.workload == "adjoint":
+        args.steps = 500 if args.steps is None else args.steps
+        args.warmup = 3 if args.warmup is None else max(3, args.warmup)
+        run_adjoint(args)
     else:
         args.steps = 30 if args.steps is None else args.steps
         args.warmup = 5 if args.warmup is None else max(3, args.warmup)
