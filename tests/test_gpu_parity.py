@@ -313,3 +313,34 @@ def test_mg_rejects_grids_it_cannot_coarsen():
     assert pf.pf_workspace_bytes(p) == 0
     with pytest.raises(pf.PfError):
         pf.pf_create(p, None)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 5, 3), (7, 1, 1), (2, 2, 1), (3, 1, 4), (16, 2, 2)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_degenerate_shapes(shape, precision):
+    """Grids one cell thin in any direction (a cell its own x/y neighbour, a
+    single plane touching both z faces) against the oracle."""
+    nx, ny, nz = shape
+    w = mixed_workload(nx, ny, nz, 71, precision=precision, steps=4, rtol=1e-13 if precision == "fp64" else 1e-7,
+                       amp=0.5)
+    P, phi, st, info = gpu_run(w)
+    Po, phio, sto, _ = oracle_run(w, rtol=1e-14)
+    assert st == pf.PF_OK and sto == O.OK
+    tol = FP64_TOL if precision == "fp64" else FP32_TOL
+    assert relerr(P, Po) <= tol
+    assert relerr(phi, phio) <= (tol if precision == "fp64" else 1e-3)
+
+
+def test_zero_steps_and_repeated_calls():
+    w = mixed_workload(24, 16, 8, 73, steps=3, rtol=1e-13)
+    f = Film(w)
+    st, info = f.step(0)
+    assert st == pf.PF_OK and info["steps_done"] == 0 and info["total_iters"] == 0
+    P0, _ = f.numpy()
+    assert np.array_equal(P0, w.P0)
+    for _ in range(3):
+        f.step(1)
+    P, phi = f.numpy()
+    f.close()
+    Po, phio, _, _ = oracle_run(w, rtol=1e-14)
+    assert relerr(P, Po) <= FP64_TOL and relerr(phi, phio) <= FP64_TOL
