@@ -106,8 +106,9 @@ typedef struct {
  *                      field, the adjoint potential, and one face array);
  *   PF_FLAG_WARM_LAST  start every Poisson solve of pf_step from the last
  *                      potential, as the paper does (Section Numerical
- *                      Performance).  Without it, forward-Euler runs that
- *                      solve every step start solve k from the quadratic
+ *                      Performance).  Without it, forward-Euler runs (which
+ *                      solve every step, or every poisson_every-th: equally
+ *                      spaced in time either way) start solve k from the quadratic
  *                      extrapolation 3 (phi_{k-1} - phi_{k-2}) + phi_{k-3} of
  *                      the last three potentials (linear, then constant, for
  *                      the first solves after pf_bind, pf_solve_potential or

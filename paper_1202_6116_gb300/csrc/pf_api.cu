@@ -116,9 +116,10 @@ bool params_valid(const pf_params* p, std::string* why) {
   return true;
 }
 
-// Does pf_step start its solves from an extrapolation of the last ones?
+// Does pf_step start its solves from an extrapolation of the last ones?  (Forward
+// Euler: its solves are equally spaced in time, every step or every k-th.)
 bool extrapolates(const pf_params* p) {
-  return !(p->flags & PF_FLAG_WARM_LAST) && p->integrator == PF_EULER && p->poisson_every <= 1;
+  return !(p->flags & PF_FLAG_WARM_LAST) && p->integrator == PF_EULER;
 }
 
 Layout layout_of(const pf_params* p) {

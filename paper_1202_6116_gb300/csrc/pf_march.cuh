@@ -110,7 +110,11 @@ __device__ __forceinline__ void cp_wait() {
 // VX consecutive values through one 16-byte access when they fill it.
 template <typename V, int VX>
 __device__ __forceinline__ void load_n(const V* p, V (&o)[VX]) {
-  if constexpr (VX == 4 && sizeof(V) == 4) {
+  if constexpr (VX == 2 && sizeof(V) == 4) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    reinterpret_cast<float*>(o)[0] = t.x;
+    reinterpret_cast<float*>(o)[1] = t.y;
+  } else if constexpr (VX == 4 && sizeof(V) == 4) {
     const float4 t = *reinterpret_cast<const float4*>(p);
     const float* f = reinterpret_cast<const float*>(&t);
 #pragma unroll
@@ -487,17 +491,21 @@ __device__ __forceinline__ void march(const Geo& g, const TileGeo<TXT, TYT, VX>&
 
 // Walk one tile whose stencil is the raw input itself: the neighbours are read
 // straight from the staged planes (after the plane's barrier), with no field
-// buffer.  emit(xy, z, const Stencil7<Raw<T,NH>>&, const T (&o)[NO], bt) -> Out;
-// post and bt as in march.
-template <typename T, typename Out, int TXT, int TYT, int VX, int NH, int NO, int D, class Emit, class Post>
+// buffer.  emit(xy, z, const Stencil7<Raw<T,NH+NP>>&, const T (&o)[NO], bt) -> Out;
+// post and bt as in march.  With NP = 1 the staged coarse-grid parents come as
+// field NH of the stencil (the parent of each of the seven cells); a vector's
+// parents are stored compactly (VX / fx values), read with one access and
+// expanded in registers.
+template <typename T, typename Out, int TXT, int TYT, int VX, int NH, int NO, int D, int NP = 0, class Emit,
+          class Post>
 __device__ __forceinline__ void march_direct(const Geo& g, const TileGeo<TXT, TYT, VX>& s, unsigned char* smem,
                                              const T* const (&hsrc)[NH], const T* const (&osrc)[NO > 0 ? NO : 1],
-                                             Emit emit, Post post) {
-  using SG = Stager<T, TXT, TYT, VX, NH, NO, D>;
-  using R = Raw<T, NH>;
-  constexpr int NS = SG::NS;
+                                             Emit emit, Post post, ParentSrc<T> par = ParentSrc<T>{}) {
+  using SG = Stager<T, TXT, TYT, VX, NH, NO, D, NP>;
+  using R = Raw<T, NH + NP>;
+  constexpr int NS = SG::NS, OFF = SG::OFF;
   static_assert(TXT == 16 || TXT == 32, "a warp holds one or two tile rows");
-  const SG sg(g, s, reinterpret_cast<T*>(smem), hsrc, osrc);
+  const SG sg(g, s, reinterpret_cast<T*>(smem), hsrc, osrc, par);
   const int nt = sg.nt, row = sg.row, col = sg.col;
   const bool left_in_warp = s.tx > 0;
   const bool right_in_warp = s.tx < TXT - 1 && (s.tx + 1) * VX < s.w;
@@ -509,11 +517,29 @@ __device__ __forceinline__ void march_direct(const Geo& g, const TileGeo<TXT, TY
   // that a thread still in iteration v - 1 reads, and one barrier per plane
   // orders every shared access.
   static_assert(D >= 2 && NS >= D + 2, "stage ring too short for one barrier per plane");
-  T zmr[NH][VX], cr[NH][VX], zpr[NH][VX];
+  constexpr int NF = NH + NP;
+  T zmr[NF][VX], cr[NF][VX], zpr[NF][VX];
 #pragma unroll
-  for (int k = 0; k < NH; ++k)
+  for (int k = 0; k < NF; ++k)
 #pragma unroll
     for (int i = 0; i < VX; ++i) zmr[k][i] = cr[k][i] = zpr[k][i] = T(0);
+  // field k of the vector row rw in stage st (parents: compact, expanded)
+  auto load_vec = [&](int st, int k, int rw, T (&o)[VX]) {
+    if (k < NH) {
+      load_n<T, VX>(sg.H(st, k, rw, col), o);
+    } else if constexpr (VX >= 2) {
+      if (par.fx == 2) {
+        T h[VX / 2];
+        load_n<T, VX / 2>(sg.PA(st, rw, col), h);
+#pragma unroll
+        for (int i = 0; i < VX; ++i) o[i] = h[i >> 1];
+      } else {
+        load_n<T, VX>(sg.PA(st, rw, col), o);
+      }
+    } else {
+      o[0] = *sg.PA(st, rw, col);
+    }
+  };
   for (int v = 0; v <= D; ++v) sg.issue(v);
   for (int v = 1; v <= nt; ++v) {
     sg.issue(v + D);
@@ -523,24 +549,29 @@ __device__ __forceinline__ void march_direct(const Geo& g, const TileGeo<TXT, TY
     const int zb = sg.plane(v - 1), za = sg.plane(v + 1);
     if (v == 1 && s.act) {
 #pragma unroll
-      for (int k = 0; k < NH; ++k) {
-        if (zb >= 0) load_n<T, VX>(sg.H(0, k, row, col), zmr[k]);
-        load_n<T, VX>(sg.H(st, k, row, col), cr[k]);
+      for (int k = 0; k < NF; ++k) {
+        if (zb >= 0) load_vec(0, k, row, zmr[k]);
+        load_vec(st, k, row, cr[k]);
       }
     }
-    T ym[NH][VX], yp[NH][VX], lft[NH], rgt[NH];
+    T ym[NF][VX], yp[NF][VX], lft[NF], rgt[NF];
 #pragma unroll
-    for (int k = 0; k < NH; ++k) {
+    for (int k = 0; k < NF; ++k) {
       if (s.act) {
-        load_n<T, VX>(sg.H(st, k, row - 1, col), ym[k]);
-        load_n<T, VX>(sg.H(st, k, row + 1, col), yp[k]);
-        if (za >= 0) load_n<T, VX>(sg.H(sa, k, row, col), zpr[k]);
+        load_vec(st, k, row - 1, ym[k]);
+        load_vec(st, k, row + 1, yp[k]);
+        if (za >= 0) load_vec(sa, k, row, zpr[k]);
       }
       lft[k] = shfl_up1(s.act ? cr[k][VX - 1] : T(0));
       rgt[k] = shfl_down1(s.act ? cr[k][0] : T(0));
       if (s.act) {
-        if (!left_in_warp) lft[k] = *sg.H(st, k, row, col - 1);
-        if (!right_in_warp) rgt[k] = *sg.H(st, k, row, col + VX);
+        if (k < NH) {
+          if (!left_in_warp) lft[k] = *sg.H(st, k, row, col - 1);
+          if (!right_in_warp) rgt[k] = *sg.H(st, k, row, col + VX);
+        } else {
+          if (!left_in_warp) lft[k] = *sg.PA(st, row, OFF - 1);
+          if (!right_in_warp) rgt[k] = *sg.PA(st, row, OFF + s.w);
+        }
       }
     }
     if (s.act) {
@@ -554,7 +585,7 @@ __device__ __forceinline__ void march_direct(const Geo& g, const TileGeo<TXT, TY
         for (int i = 0; i < VX; ++i) {
           Stencil7<R> sc;
 #pragma unroll
-          for (int k = 0; k < NH; ++k) {
+          for (int k = 0; k < NF; ++k) {
             sc.c.v[k] = cr[k][i];
             sc.xm.v[k] = i == 0 ? lft[k] : cr[k][i - 1];
             sc.xp.v[k] = i == VX - 1 ? rgt[k] : cr[k][i + 1];
@@ -576,7 +607,7 @@ __device__ __forceinline__ void march_direct(const Geo& g, const TileGeo<TXT, TY
       else emit_all(false);
     }
 #pragma unroll
-    for (int k = 0; k < NH; ++k)
+    for (int k = 0; k < NF; ++k)
 #pragma unroll
       for (int i = 0; i < VX; ++i) {
         zmr[k][i] = cr[k][i];

@@ -84,7 +84,7 @@ __device__ __forceinline__ T mg_inv_bt(const MgView<T>& L, int xy, int z, T inv_
 template <typename T, int VX>
 using MgPipeD0 = Pipe<T, void, MTX, MTY, VX, 1, 0, MG_D>;
 template <typename T, int VX>
-using MgPipeP = Pipe<T, T, MTX, MTY, VX, 1, 1, MG_D, 1>;
+using MgPipeP = Pipe<T, void, MTX, MTY, VX, 1, 1, MG_D, 1>;
 // stencil read straight from the staged planes (no field buffer)
 template <typename T, int VX>
 using MgPipeD = Pipe<T, void, MTX, MTY, VX, 1, 1, MG_D>;
@@ -217,7 +217,8 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Sc
 }
 
 // Prolongation + correction fused into the first post-smoothing sweep: the
-// stencil field is e + e_c(parent), the parents staged with the fine planes.
+// stencil field is e + e_c(parent), the parents staged with the fine planes
+// and combined with e at each of the seven cells.
 template <typename T, int VX>
 __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_mg_post1(MgView<T> L, MgView<T> C, Scalars* S) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -228,8 +229,17 @@ __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_mg_post1(M
   const T* osrc[1] = {L.f};
   const ParentSrc<T> par{C.e, L.fx, L.fy, L.fz, C.g.nx, C.g.nxy};
   TileGeo<MTX, MTY, VX> s;
-  auto val = [&](const T (&h)[1], int, int, int, int, T parent, bool) -> T { return h[0] + parent; };
-  auto emit = [&](int xy, int z, const Stencil7<T>& st, const T (&)[1], const T (&o)[1], const bool bt) -> T {
+  auto emit = [&](int xy, int z, const Stencil7<Raw<T, 2>>& sr, const T (&o)[1], const bool bt) -> T {
+    Stencil7<T> st;
+    st.c = sr.c.v[0] + sr.c.v[1];
+    st.xm = sr.xm.v[0] + sr.xm.v[1];
+    st.xp = sr.xp.v[0] + sr.xp.v[1];
+    st.ym = sr.ym.v[0] + sr.ym.v[1];
+    st.yp = sr.yp.v[0] + sr.yp.v[1];
+    st.zm = sr.zm.v[0] + sr.zm.v[1];
+    st.zp = sr.zp.v[0] + sr.zp.v[1];
+    st.zb = sr.zb;
+    st.za = sr.za;
     const bool B = bt;
     const int dlo = (B && st.zb < 0) ? (int)L.tlo[xy] : 0;
     const int dhi = (B && st.za < 0) ? (int)L.thi[xy] : 0;
@@ -240,7 +250,7 @@ __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_mg_post1(M
   const TileSched ts{&S->sched_next, &S->sched_done};
   for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
-    march<T, T, T, MTX, MTY, VX, 1, 1, MG_D, 1>(L.g, s, smem, hsrc, osrc, val, emit, post, par);
+    march_direct<T, T, MTX, MTY, VX, 1, 1, MG_D, 1>(L.g, s, smem, hsrc, osrc, emit, post, par);
   }
   sched_finish(ts);
 }
