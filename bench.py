@@ -74,7 +74,7 @@ def workload_config(w, name, flush, args=None):
     if args is not None:
         c["integrator"] = args.integrator
         c["poisson_every"] = max(1, args.poisson_every)
-        c["warm_start"] = "last potential" if args.warm_last else "extrapolated (last three potentials)"
+        c["warm_start"] = "last potential" if args.warm_last else "extrapolated (last four potentials, compensated in FP32)"
         if args.noise > 0:
             c["noise_sigma"] = args.noise
         if w.n_air:

@@ -108,14 +108,21 @@ typedef struct {
  *                      potential, as the paper does (Section Numerical
  *                      Performance).  Without it, forward-Euler runs (which
  *                      solve every step, or every poisson_every-th: equally
- *                      spaced in time either way) start solve k from the quadratic
- *                      extrapolation 3 (phi_{k-1} - phi_{k-2}) + phi_{k-3} of
- *                      the last three potentials (linear, then constant, for
- *                      the first solves after pf_bind, pf_solve_potential or
- *                      a pf_set_bc that changes an electrode layout; voltage
- *                      changes keep the history): the same stopping test, a closer
- *                      start, fewer iterations.  Costs two more fields of
- *                      workspace. */
+ *                      spaced in time either way) start solve k from the cubic
+ *                      extrapolation 4 phi_{k-1} - 6 phi_{k-2} + 4 phi_{k-3}
+ *                      - phi_{k-4} of the last four potentials (quadratic,
+ *                      linear, then constant, for the first solves after
+ *                      pf_bind, pf_solve_potential or a pf_set_bc that changes
+ *                      an electrode layout; voltage changes keep the
+ *                      history): the same stopping test, a closer start,
+ *                      fewer iterations.  Costs three more fields of
+ *                      workspace.  In FP32 (unless the problem is singular)
+ *                      the library also keeps, in two more fields, the part
+ *                      of each solution that the FP32 phi cannot hold, and
+ *                      extrapolates from that compensated potential: without
+ *                      it the rounding of phi alone would leave a start
+ *                      residual above a 1e-7 tolerance on large films.  phi
+ *                      is still the solution rounded to FP32. */
 enum { PF_FLAG_NO_GRAPHS = 1, PF_FLAG_ADJOINT = 2, PF_FLAG_WARM_LAST = 4 };
 
 typedef struct {

@@ -75,7 +75,7 @@ std::vector<MgLevelHost> mg_levels(const pf_params* p) {
 }
 
 struct Layout {
-  size_t P_alt, r, p0, p1, q, invd, h1, h2, tlo, thi, vlo, vhi, ctr, xctr, part, S, diag, z, zt, total;
+  size_t P_alt, r, p0, p1, q, invd, hist[3], clo, cx, tlo, thi, vlo, vhi, ctr, xctr, part, S, diag, z, zt, total;
   bool adj = false;               // psi and vzero exist (PF_FLAG_ADJOINT)
   size_t psi = 0, vzero = 0;      // adjoint potential; zero face voltages
   std::vector<MgLevelHost> mg;
@@ -122,6 +122,10 @@ bool extrapolates(const pf_params* p) {
   return !(p->flags & PF_FLAG_WARM_LAST) && p->integrator == PF_EULER;
 }
 
+// FP32 time series keep the potential compensated (k_extrap_comp) unless the
+// problem is singular (all-periodic: its mean removal acts on phi alone).
+bool comp_buffers(const pf_params* p) { return extrapolates(p) && p->precision == PF_FP32; }
+
 Layout layout_of(const pf_params* p) {
   const size_t w = p->precision == PF_FP32 ? 4 : 8;
   const size_t n = (size_t)p->nx * p->ny * p->nz, nxy = (size_t)p->nx * p->ny;
@@ -138,8 +142,10 @@ Layout layout_of(const pf_params* p) {
   L.p1 = take(n * w);
   L.q = take(n * w);
   L.invd = take(p->has_eps ? n * w : 0);
-  L.h1 = take(extrapolates(p) ? n * w : 0);      // potentials of the last solves (extrapolated warm start)
-  L.h2 = take(extrapolates(p) ? n * w : 0);
+  for (size_t& h : L.hist) h = take(extrapolates(p) ? n * w : 0);   // ring of past potentials (or differences)
+  L.clo = take(comp_buffers(p) ? n * w : 0);    // remainder of the compensated potential
+  L.cx = take(comp_buffers(p) ? n * w : 0);     // the solve's correction to it
+
   L.tlo = take(nxy);
   L.thi = take(nxy);
   L.vlo = take(nxy * w);
@@ -504,12 +510,37 @@ pf_status read_scalars(pf_ctx* ctx) {
   return PF_OK;
 }
 
-// Extrapolated initial guess of the next step solve, in the bound phi buffer.
+// Is this context's next step solve compensated (see comp_buffers)?
+bool compensated(const pf_ctx* ctx) { return comp_buffers(&ctx->prm) && !ctx->singular; }
+
+// The step solve's view of a compensated potential: the Krylov iterate is the
+// correction, the start is the pair phi + lo.
+template <typename T>
+void comp_view(pf_ctx* ctx, pf::Dev<T>& d) {
+  char* ws = ctx->ws;
+  d.cp.hi = (T*)ctx->phi;
+  d.cp.lo = (T*)(ws + ctx->lay.clo);
+  for (int i = 0; i < 3; ++i) d.cp.ring[i] = (T*)(ws + ctx->lay.hist[i]);
+  d.cp.nsolve = (const long long*)(ws + ctx->lay.xctr);
+  d.phi = (T*)(ws + ctx->lay.cx);
+}
+
+// Extrapolated initial guess of the next step solve: in the bound phi buffer,
+// or (compensated) in the pair phi + lo with the correction zeroed.
 template <typename T>
 void launch_extrap_of(pf_ctx* ctx, const pf::LaunchCfg& L) {
   long long* xc = (long long*)(ctx->ws + ctx->lay.xctr);
-  pf::launch_extrap<T>(L, ctx->geo.n, (T*)ctx->phi, (T*)(ctx->ws + ctx->lay.h1), (T*)(ctx->ws + ctx->lay.h2), xc,
-                       (unsigned*)(xc + 1));
+  if constexpr (std::is_same<T, float>::value) {
+    if (compensated(ctx)) {
+      pf::Dev<float> d{};
+      comp_view<float>(ctx, d);
+      pf::launch_extrap_comp(L, ctx->geo.n, d.cp, d.phi, xc, (unsigned*)(xc + 1));
+      return;
+    }
+  }
+  T* const ring[3] = {(T*)(ctx->ws + ctx->lay.hist[0]), (T*)(ctx->ws + ctx->lay.hist[1]),
+                      (T*)(ctx->ws + ctx->lay.hist[2])};
+  pf::launch_extrap<T>(L, ctx->geo.n, (T*)ctx->phi, ring, xc, (unsigned*)(xc + 1));
 }
 
 // Forget the extrapolation history (the next step solve starts from phi).
@@ -534,6 +565,8 @@ template <typename T>
 pf_status solve(pf_ctx* ctx, const T* P, bool adj = false, bool step_solve = false) {
   pf::Dev<T> d = dev_view<T>(ctx);
   if (adj) adjoint_view<T>(ctx, d);
+  const bool comp = step_solve && !adj && compensated(ctx);
+  if (comp) comp_view<T>(ctx, d);
   int& est_iters = adj ? ctx->est_iters_adj : ctx->est_iters;
   const Geo& g = ctx->geo;
   const double N = (double)g.n, w = sizeof(T), e = ctx->prm.has_eps ? 1.0 : 0.0;
@@ -546,7 +579,7 @@ pf_status solve(pf_ctx* ctx, const T* P, bool adj = false, bool step_solve = fal
   if (step_solve && extrapolates(&ctx->prm)) {
     before_launch(ctx);
     launch_extrap_of<T>(ctx, ctx->L);
-    after_launch(ctx, F_EXTRAP, 6 * N * w);
+    after_launch(ctx, F_EXTRAP, (comp ? 9 : 6) * N * w);   // steady state
   }
   if (ctx->singular) {
     before_launch(ctx);
@@ -555,7 +588,7 @@ pf_status solve(pf_ctx* ctx, const T* P, bool adj = false, bool step_solve = fal
   }
   before_launch(ctx);
   pf::launch_rhs<T>(ctx->L, g, d, P, 0, 0);
-  after_launch(ctx, F_RHS, (5 + 2 * e) * N * w);
+  after_launch(ctx, F_RHS, (5 + 2 * e + (comp ? 1 : 0)) * N * w);
   const int mg = ctx->prm.solver == PF_PCG_MG;
   if (mg) vcycle<T>(ctx, 0);
   PF_CUDA(cudaGetLastError());
@@ -588,7 +621,7 @@ pf_status solve(pf_ctx* ctx, const T* P, bool adj = false, bool step_solve = fal
   if (!s.zero_x) est_iters = std::max(1, s.iter);
   before_launch(ctx);
   pf::launch_cg_finish<T>(ctx->L, g, d, ctx->singular);
-  after_launch(ctx, F_FINISH, (s.zero_x ? 1.0 : (s.pending ? 3.0 : 1.0)) * N * w);
+  after_launch(ctx, F_FINISH, (comp ? (s.pending ? 8.0 : 7.0) : s.zero_x ? 1.0 : (s.pending ? 3.0 : 1.0)) * N * w);
   if (ctx->singular) {
     pf::launch_sub_mean<T>(ctx->L, g, d);
     after_launch(ctx, F_SUB_MEAN, 2 * N * w);
@@ -663,7 +696,10 @@ cudaError_t append_step(pf_ctx* ctx, cudaGraph_t graph, std::vector<cudaGraphNod
     if (e == cudaSuccess) e = e2;
   };
   // One Poisson solve for the state P with its own loop condition.
+  pf::Dev<T> ds = d;
+  if (compensated(ctx)) comp_view<T>(ctx, ds);
   auto solve_nodes = [&](const T* P) {
+    const pf::Dev<T>& d = ds;
     cudaGraphConditionalHandle h = 0;
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
     segment([&] {

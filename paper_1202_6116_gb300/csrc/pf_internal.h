@@ -27,10 +27,22 @@ struct LaunchCfg {
   cudaStream_t stream;
 };
 
+// Compensated potential of an FP32 time series: the solution is the pair
+// hi + lo of FP32 words (hi is the bound phi, lo its rounding remainder), and
+// ring holds the differences of the last three solutions, D_m in slot m mod 3
+// (see k_extrap_comp).  lo == nullptr: off.
+template <typename T>
+struct Comp {
+  T* hi;
+  T* lo;
+  T* ring[3];
+  const long long* nsolve;   // solves in the history (after this solve's guess)
+};
+
 // Device views of one context's buffers, typed by the storage precision.
 template <typename T>
 struct Dev {
-  T* phi;
+  T* phi;            // the Krylov iterate: the potential, or its correction when cp.lo is set
   const T* eps;      // nullptr when eps = 1
   T* invd;           // 1/diag(A), only when eps is bound
   T* r;
@@ -41,6 +53,7 @@ struct Dev {
   Bc<T> bc;
   double* part;
   Scalars* S;
+  Comp<T> cp;
 };
 
 // One multigrid level as the kernels see it.
@@ -100,9 +113,12 @@ void launch_tdgl(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, 
                  int corr, const Noise& nz);
 template <typename T>
 void launch_invdiag(const LaunchCfg& L, const Geo& g, const Dev<T>& d);
-// Extrapolated initial guess of a time step's solve (see k_extrap).
+// Extrapolated initial guess of a time step's solve (see k_extrap), and its
+// compensated FP32 form (see k_extrap_comp; x is the correction, zeroed).
 template <typename T>
-void launch_extrap(const LaunchCfg& L, long long n, T* phi, T* h1, T* h2, long long* nsolve, unsigned* ticket);
+void launch_extrap(const LaunchCfg& L, long long n, T* phi, T* const ring[3], long long* nsolve, unsigned* ticket);
+void launch_extrap_comp(const LaunchCfg& L, long long n, const Comp<float>& cp, float* x, long long* nsolve,
+                        unsigned* ticket);
 // Adjoint update (pf_adjoint.cu): lam_out from lam, the adjoint potential psi
 // and the state P; adds the parameter sensitivities to grad[4] and, when
 // gv_lo/gv_hi are non-NULL, the face-voltage sensitivities.

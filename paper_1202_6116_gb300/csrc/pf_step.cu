@@ -4,7 +4,9 @@
 //   k_rhs   b = -div P + (Dirichlet terms) (Eqs. rho, Poisson; face values of P:
 //           mean inside, P_cell at an electrode, 0 at an open face), the warm
 //           start residual r0 = b - A phi (Section Numerical Performance), and
-//           ||b||^2, ||r||^2, r.z.  With MEAN = true it only sums b (the zero-mean
+//           ||b||^2, ||r||^2, r.z.  An FP32 time series starts from the
+//           compensated pair phi + lo (r0 = b - A phi - A lo, see
+//           k_extrap_comp).  With MEAN = true it only sums b (the zero-mean
 //           projection of singular problems).
 //   k_tdgl  P' = P + dt L (-df/dP + g Lap P + E), E = -grad phi from face values
 //           (Eq. TDGL with Eqs. F_bulk, dF_grad/dP, F_elec; Section Time Integration).
@@ -17,7 +19,8 @@
 //
 // Both read P (3 components) and phi with their 6 neighbours; the neighbours
 // come straight from the staged planes (march_direct).  Algorithmic traffic
-// per cell: k_rhs reads 4 words and writes 1; k_tdgl reads 4 and writes 3.
+// per cell: k_rhs reads 4 words (5 with a compensated start) and writes 1;
+// k_tdgl reads 4 and writes 3.
 #include "pf_internal.h"
 #include "pf_march.cuh"
 #include "pf_rng.cuh"
@@ -26,8 +29,9 @@ namespace pf {
 
 constexpr int STEP_D = 2;
 
-template <typename T, bool EPS, int VX>
-using StepPipe = Pipe<T, void, MTX, MTY, VX, EPS ? 5 : 4, EPS ? 1 : 0, STEP_D>;
+// X: extra staged fields (the remainder of a compensated potential)
+template <typename T, bool EPS, int VX, int X = 0>
+using StepPipe = Pipe<T, void, MTX, MTY, VX, (EPS ? 5 : 4) + X, EPS ? 1 : 0, STEP_D>;
 
 // Face values of P along the face normal (reading of the boundary kinds).
 template <typename T, int NH>
@@ -46,14 +50,18 @@ __device__ __forceinline__ T divergence(const Stencil7<Raw<T, NH>>& s, int dlo, 
   return div;
 }
 
-template <typename T, bool EPS, bool MEAN, int VX>
+// COMP: the start is the compensated pair phi + lo (r0 = b - A phi - A lo).
+template <typename T, bool EPS, bool MEAN, int VX, bool COMP = false>
 __global__ void __launch_bounds__(MTX* MTY) k_rhs(Geo g, Bc<T> bc, const T* __restrict__ P, const T* __restrict__ phi,
-                                                 const T* __restrict__ eps, const T* __restrict__ invd,
-                                                 T* __restrict__ r, double* part, Scalars* S, MarchCfg mc,
-                                                 cudaGraphConditionalHandle cond, int use_cond) {
+                                                 const T* __restrict__ lo, const T* __restrict__ eps,
+                                                 const T* __restrict__ invd, T* __restrict__ r, double* part,
+                                                 Scalars* S, MarchCfg mc, cudaGraphConditionalHandle cond,
+                                                 int use_cond) {
+  static_assert(!(COMP && MEAN), "the mean of b needs no start");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
-  constexpr int NH = EPS ? 5 : 4;     // Px, Py, Pz, phi (, eps)
+  constexpr int NH = (EPS ? 5 : 4) + (COMP ? 1 : 0);   // Px, Py, Pz, phi (, lo) (, eps)
+  constexpr int IE = NH - 1;                           // eps, when staged
   constexpr int NO = EPS ? 1 : 0;     // (1/diag)
   constexpr int NV = MEAN ? 1 : 3;
   const T mb = MEAN ? T(0) : T(S->mean_b);
@@ -64,7 +72,8 @@ __global__ void __launch_bounds__(MTX* MTY) k_rhs(Geo g, Bc<T> bc, const T* __re
   hsrc[1] = P + g.n;
   hsrc[2] = P + 2 * g.n;
   hsrc[3] = phi;
-  if constexpr (EPS) hsrc[4] = eps;
+  if constexpr (COMP) hsrc[4] = lo;
+  if constexpr (EPS) hsrc[IE] = eps;
   const T* osrc[1] = {invd};
   Acc<T> abb, arr, arz;
   TileGeo<MTX, MTY, VX> s;
@@ -72,7 +81,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_rhs(Geo g, Bc<T> bc, const T* __re
     const bool B = bt;
     const int dlo = (B && st.zb < 0) ? (int)bc.tlo[xy] : 0;
     const int dhi = (B && st.za < 0) ? (int)bc.thi[xy] : 0;
-    const T ec = EPS ? st.c.v[NH - 1] : T(1);
+    const T ec = EPS ? st.c.v[IE] : T(1);
     T dir = T(0);
     if (dlo) dir += T(2) * ec * bc.vlo[xy];
     if (dhi) dir += T(2) * ec * bc.vhi[xy];
@@ -81,24 +90,26 @@ __global__ void __launch_bounds__(MTX* MTY) k_rhs(Geo g, Bc<T> bc, const T* __re
       abb.add(b, T(1));
       return T(0);
     }
-    T Aphi;
-    if constexpr (EPS) {
-      Stencil7<EpsVal<T>> se;
-      auto ev = [&](const Raw<T, NH>& rw) { return EpsVal<T>{rw.v[3], rw.v[4]}; };
-      se.c = ev(st.c);
-      se.xm = ev(st.xm);
-      se.xp = ev(st.xp);
-      se.ym = ev(st.ym);
-      se.yp = ev(st.yp);
-      se.zm = ev(st.zm);
-      se.zp = ev(st.zp);
-      se.zb = st.zb;
-      se.za = st.za;
-      Aphi = apply_bt(se, dlo, dhi, ih2, bt);
-    } else {
-      Aphi = apply_bt(pick(st, 3), dlo, dhi, ih2, bt);
-    }
-    const T rv = b - Aphi;
+    auto Aof = [&](int i) -> T {
+      if constexpr (EPS) {
+        Stencil7<EpsVal<T>> se;
+        auto ev = [&](const Raw<T, NH>& rw) { return EpsVal<T>{rw.v[i], rw.v[IE]}; };
+        se.c = ev(st.c);
+        se.xm = ev(st.xm);
+        se.xp = ev(st.xp);
+        se.ym = ev(st.ym);
+        se.yp = ev(st.yp);
+        se.zm = ev(st.zm);
+        se.zp = ev(st.zp);
+        se.zb = st.zb;
+        se.za = st.za;
+        return apply_bt(se, dlo, dhi, ih2, bt);
+      } else {
+        return apply_bt(pick(st, i), dlo, dhi, ih2, bt);
+      }
+    };
+    T rv = b - Aof(3);
+    if constexpr (COMP) rv -= Aof(4);
     T inv;
     if constexpr (EPS) inv = o[0];
     else inv = B ? inv_diag_unit(g, bc, xy, z, inv6) : inv6;
@@ -295,28 +306,41 @@ static void smem_attr(K kernel, size_t bytes, bool& done) {
   }
 }
 
-template <typename T, bool EPS, bool MEAN, int VX>
+template <typename T, bool EPS, bool MEAN, int VX, bool COMP>
 static void rhs_t(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, cudaGraphConditionalHandle cond,
                   int use_cond) {
   static bool f = false;
-  const size_t bytes = StepPipe<T, EPS, VX>::bytes();
-  smem_attr(k_rhs<T, EPS, MEAN, VX>, bytes, f);
-  k_rhs<T, EPS, MEAN, VX><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(
-      g, d.bc, P, d.phi, d.eps, d.invd, d.r, d.part, d.S, L.march, cond, use_cond);
+  const size_t bytes = StepPipe<T, EPS, VX, COMP ? 1 : 0>::bytes();
+  smem_attr(k_rhs<T, EPS, MEAN, VX, COMP>, bytes, f);
+  k_rhs<T, EPS, MEAN, VX, COMP><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(
+      g, d.bc, P, COMP ? d.cp.hi : d.phi, d.cp.lo, d.eps, d.invd, d.r, d.part, d.S, L.march, cond, use_cond);
+}
+
+template <typename T, bool MEAN, bool COMP>
+static void rhs_c(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, cudaGraphConditionalHandle cond,
+                  int use_cond) {
+  constexpr int V = 16 / sizeof(T);
+  const bool vec = L.march.vx == V;
+  if (d.eps) {
+    if (vec) rhs_t<T, true, MEAN, V, COMP>(L, g, d, P, cond, use_cond);
+    else rhs_t<T, true, MEAN, 1, COMP>(L, g, d, P, cond, use_cond);
+  } else {
+    if (vec) rhs_t<T, false, MEAN, V, COMP>(L, g, d, P, cond, use_cond);
+    else rhs_t<T, false, MEAN, 1, COMP>(L, g, d, P, cond, use_cond);
+  }
 }
 
 template <typename T, bool MEAN>
 static void rhs_v(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, cudaGraphConditionalHandle cond,
                   int use_cond) {
-  constexpr int V = 16 / sizeof(T);
-  const bool vec = L.march.vx == V;
-  if (d.eps) {
-    if (vec) rhs_t<T, true, MEAN, V>(L, g, d, P, cond, use_cond);
-    else rhs_t<T, true, MEAN, 1>(L, g, d, P, cond, use_cond);
-  } else {
-    if (vec) rhs_t<T, false, MEAN, V>(L, g, d, P, cond, use_cond);
-    else rhs_t<T, false, MEAN, 1>(L, g, d, P, cond, use_cond);
+  // compensated starts are FP32 only (FP64 potentials need no remainder)
+  if constexpr (!MEAN && std::is_same<T, float>::value) {
+    if (d.cp.lo) {
+      rhs_c<T, false, true>(L, g, d, P, cond, use_cond);
+      return;
+    }
   }
+  rhs_c<T, MEAN, false>(L, g, d, P, cond, use_cond);
 }
 
 template <typename T>

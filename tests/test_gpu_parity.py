@@ -93,6 +93,35 @@ def test_extrapolation_history_survives_calls_and_resets():
     assert relerr(Pc, Pa) <= FP64_TOL and ic["total_iters"] > 0
 
 
+@pytest.mark.parametrize("precision,rtol,bound", [("fp64", 1e-10, 1e-7), ("fp32", 1e-7, 1e-5)])
+def test_extrapolation_is_exact_for_cubic_potentials(precision, rtol, bound):
+    """With the mobility at 0 (P frozen) and the top electrode voltages a cubic
+    in the step index, the potentials are that cubic too, so the extrapolation
+    of the last four starts each solve from the fifth on within a few
+    multiples of the tolerance: at most 2 MG-PCG iterations (a quadratic
+    extrapolation would start about 1e-2 off; in FP32 so would a start whose
+    potential is rounded to FP32, at about 1e-5).  The potential still equals
+    the oracle's for the last voltages."""
+    w = mixed_workload(32, 24, 12, 71, steps=1, rtol=rtol, precision=precision).with_(L=0.0, solver="mg", maxit=500)
+    volts = [w.volt_hi * (1 + 0.3 * k - 0.05 * k ** 2 + 0.01 * k ** 3) for k in range(10)]
+    P0 = w.P0.astype(np.float32).astype(np.float64) if precision == "fp32" else w.P0
+    its = {}
+    for flags in (0, pf.PF_FLAG_WARM_LAST):
+        f = Film(w, flags=flags)
+        its[flags] = []
+        for v in volts:
+            f.set_bc(pf.PF_ZHI, w.type_hi, v)
+            _, info = f.step(1)
+            its[flags].append(info["last_iters"])
+        P, phi = f.numpy()
+        f.close()
+        assert np.array_equal(P, P0)
+    assert max(its[0][4:]) <= 2, its
+    assert sum(its[pf.PF_FLAG_WARM_LAST][4:]) >= 2 * max(sum(its[0][4:]), 1), its
+    phio, st, _, _ = O.solve_potential(oracle_grid(w.with_(volt_hi=volts[-1])), P0, rtol=1e-14)
+    assert st == O.OK and relerr(phi, phio) <= bound
+
+
 def test_graph_and_host_driven_steps_agree():
     """The same steps launched as CUDA graphs (device-driven Krylov loop) and
     host-driven (profiling on) give bit-identical states."""
