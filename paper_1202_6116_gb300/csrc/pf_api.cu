@@ -229,6 +229,7 @@ struct pf_ctx {
   bool graphs_broken = false;     // capture not possible: host-driven loop
   int64_t graph_steps = 0;        // steps of the current call run as graphs
   int64_t graph_fixed = 0;        // kernels of those steps outside the Krylov loops
+  int64_t graph_solves = 0;       // Poisson solves of those steps
   int64_t nstep = 0;              // steps since pf_bind (schedules poisson_every)
   uint64_t gen = 0;               // bumped by every change that invalidates captured graphs
   double noise_sigma = 0.0;       // thermal random force (pf_set_noise)
@@ -494,6 +495,7 @@ pf_status reset_scalars(pf_ctx* ctx) {
   ctx->launches = 0;
   ctx->graph_steps = 0;
   ctx->graph_fixed = 0;
+  ctx->graph_solves = 0;
   Scalars& s = *ctx->S_tmpl;
   std::memset(&s, 0, sizeof(Scalars));
   s.rtol = ctx->prm.poisson_rtol;
@@ -601,7 +603,7 @@ pf_status solve(pf_ctx* ctx, const T* P, bool adj = false, bool step_solve = fal
     for (int i = 0; i < batch; ++i) {
       const int it = issued + i + 1;
       before_launch(ctx);
-      pf::launch_cg_p<T>(ctx->L, g, d, mg);
+      pf::launch_cg_p<T>(ctx->L, g, d, mg, it == 1);
       after_launch(ctx, F_CG_P, (6 + 2 * e) * N * w, 1, it, (3 + 2 * e) * N * w);
       pf::launch_cg_r<T>(ctx->L, g, d, mg, 0, 0);
       after_launch(ctx, F_CG_R, (3 + e) * N * w, 1, it);
@@ -652,8 +654,10 @@ void step_kernel_counts(const pf_ctx* ctx, int refresh, int64_t* fixed, int64_t*
                          : 0;
   const bool heun = ctx->prm.integrator == PF_HEUN;
   const int64_t per_solve = (ctx->singular ? 2 : 0) + 2 + vc + (extrapolates(&ctx->prm) ? 1 : 0);
-  *fixed = (refresh ? (heun ? 2 : 1) * per_solve : 0) + (heun ? 2 : 1);
   *per_iter = 2 + vc;
+  // graph-captured multigrid solves run their first iteration outside the loop
+  const int64_t peeled = vc ? *per_iter : 0;
+  *fixed = (refresh ? (heun ? 2 : 1) * (per_solve + peeled) : 0) + (heun ? 2 : 1);
 }
 
 // Append one whole time step of film ctx, reading P from buffer cur, to
@@ -706,7 +710,12 @@ cudaError_t append_step(pf_ctx* ctx, cudaGraph_t graph, std::vector<cudaGraphNod
       if (extrapolates(&ctx->prm)) launch_extrap_of<T>(ctx, ctx->L);
       if (ctx->singular) pf::launch_rhs_mean<T>(ctx->L, g, d, P);
       pf::launch_rhs<T>(ctx->L, g, d, P, h, 1);
-      if (mg) vcycle<T>(ctx, 0);
+      if (mg) {                  // the first iteration (p = z) runs outside the loop
+        vcycle<T>(ctx, 0);
+        pf::launch_cg_p<T>(ctx->L, g, d, mg, 1);
+        pf::launch_cg_r<T>(ctx->L, g, d, mg, h, 1);
+        vcycle<T>(ctx, 1);
+      }
     });
     if (e != cudaSuccess) return;
     cudaGraphNode_t cnode = nullptr;
@@ -812,6 +821,7 @@ bool run_steps_graph(pf_ctx* ctx, int nsteps, pf_status* st) {
     int64_t fixed = 0, per_iter = 0;
     step_kernel_counts(ctx, refresh, &fixed, &per_iter);
     ctx->graph_fixed += fixed;
+    ctx->graph_solves += refresh ? (heun ? 2 : 1) : 0;
     ctx->graph_steps += 1;
     if (!heun) ctx->cur ^= 1;
     ctx->nstep += 1;
@@ -919,7 +929,10 @@ pf_status finish_info(pf_ctx* ctx, int nsteps, pf_step_info* info) {
     int64_t fixed = 0, per_iter = 0;
     step_kernel_counts(ctx, 1, &fixed, &per_iter);
     // graph-launched steps: kernels = fixed part + one loop body per iteration
-    info->kernel_launches = ctx->launches + (ctx->graph_steps ? ctx->graph_fixed + s.total_iters * per_iter : 0);
+    // (multigrid: per iteration after the first, which is in the fixed part)
+    const int64_t mg = ctx->prm.solver == PF_PCG_MG;
+    const int64_t bodies = mg ? s.total_iters + s.zero_solves - ctx->graph_solves : s.total_iters;
+    info->kernel_launches = ctx->launches + (ctx->graph_steps ? ctx->graph_fixed + bodies * per_iter : 0);
     info->graph_steps = ctx->graph_steps;
   }
   return result;
@@ -1536,6 +1549,7 @@ pf_status pf_batch_step(pf_batch* b, int32_t nsteps, pf_step_info* info) {
       int64_t fixed = 0, per_iter = 0;
       step_kernel_counts(c, refresh, &fixed, &per_iter);
       c->graph_fixed += fixed;
+      c->graph_solves += refresh ? (heun ? 2 : 1) : 0;
       c->graph_steps += 1;
       if (!heun) c->cur ^= 1;
       c->nstep += 1;

@@ -23,7 +23,9 @@ using CgPipe = Pipe<T, typename FieldOf<T, EPS>::type, MTX, MTY, VX, EPS ? 4 : 2
 // DIRECT (multigrid, eps = 1): the stencil of p = z + beta p_old is formed
 // from the staged planes of z and p_old at each of the seven cells (no field
 // buffer); otherwise p goes through the march's shared field buffer.
-template <typename T, bool EPS, bool MG, int VX, bool DIRECT = false>
+// FIRST (direct form, launched for a solve's first iteration only): p = z,
+// and neither p_old nor x is read (1 word read, 2 written per cell).
+template <typename T, bool EPS, bool MG, int VX, bool DIRECT = false, bool FIRST = false>
 __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g, Bc<T> bc, const T* __restrict__ eps,
                                                   const T* __restrict__ invd, const T* __restrict__ r, T* p0,
                                                   T* p1, T* __restrict__ q, T* __restrict__ x, double* part,
@@ -32,8 +34,9 @@ __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g
   __shared__ long long tile_slot;
   using F = typename FieldOf<T, EPS>::type;
   constexpr int NH = EPS ? 4 : 2;          // r or z, p_old (, eps, 1/diag) with halo
+  static_assert(!FIRST || DIRECT, "the first-iteration form is the direct one");
   if (S->done) return;
-  const int first = S->first;
+  const int first = FIRST ? 1 : S->first;
   const T beta = first ? T(0) : T(S->beta);
   const T alpha = T(S->alpha);
   const int pb = S->pbuf;
@@ -115,7 +118,20 @@ __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g
   for (long long t = sched_take(ts, &tile_slot); t < mc.ntiles; t = sched_take(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(g, t, mc);
     apq = Acc<T>();
-    if constexpr (DIRECT) {
+    if constexpr (DIRECT && FIRST) {
+      const T* const hs1[1] = {r};
+      const T* const os1[1] = {nullptr};
+      auto emit_f = [&](int xy, int, const Stencil7<Raw<T, 1>>& sr, const T (&)[1], const bool bt) -> Out {
+        Stencil7<T> st = pick(sr, 0);
+        const bool B = bt;
+        const int dlo = (B && st.zb < 0) ? (int)bc.tlo[xy] : 0;
+        const int dhi = (B && st.za < 0) ? (int)bc.thi[xy] : 0;
+        const T qv = apply_bt(st, dlo, dhi, ih2, bt);
+        apq.add(st.c, qv);
+        return Out{T(0), st.c, qv};
+      };
+      march_direct<T, Out, MTX, MTY, VX, 1, 0, CG_D>(g, s, smem, hs1, os1, emit_f, post);
+    } else if constexpr (DIRECT) {
       static_assert(MG && !EPS, "the direct form is the multigrid search direction with eps = 1");
       march_direct<T, Out, MTX, MTY, VX, NH, 1, CG_D>(g, s, smem, hsrc, osrc, emit_d, post);
     } else {
@@ -224,30 +240,31 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_cg_r(Geo g, Bc<T> bc, const T*
   }
 }
 
-template <typename T, bool EPS, bool MG, int VX>
+template <typename T, bool EPS, bool MG, int VX, bool FIRST>
 static void launch_cg_p_t(const LaunchCfg& L, const Geo& g, const Dev<T>& d) {
   constexpr bool DIRECT = MG && !EPS;
-  using PD = Pipe<T, void, MTX, MTY, VX, 2, 1, CG_D>;
+  using PD = Pipe<T, void, MTX, MTY, VX, FIRST ? 1 : 2, FIRST ? 0 : 1, CG_D>;
   const size_t bytes = DIRECT ? PD::bytes() : CgPipe<T, EPS, VX>::bytes();
   static bool once = false;
   if (!once) {
-    allow_smem(k_cg_p<T, EPS, MG, VX, DIRECT>, bytes);
+    allow_smem(k_cg_p<T, EPS, MG, VX, DIRECT, FIRST>, bytes);
     once = true;
   }
-  k_cg_p<T, EPS, MG, VX, DIRECT><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(
+  k_cg_p<T, EPS, MG, VX, DIRECT, FIRST><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(
       g, d.bc, d.eps, d.invd, MG ? d.z : d.r, d.p0, d.p1, d.q, d.phi, d.part, d.S, L.march);
 }
 
-template <typename T, bool EPS, bool MG>
+template <typename T, bool EPS, bool MG, bool FIRST = false>
 static void launch_cg_p_v(const LaunchCfg& L, const Geo& g, const Dev<T>& d) {
   constexpr int V = 16 / sizeof(T);
-  if (L.march.vx == V) launch_cg_p_t<T, EPS, MG, V>(L, g, d);
-  else launch_cg_p_t<T, EPS, MG, 1>(L, g, d);
+  if (L.march.vx == V) launch_cg_p_t<T, EPS, MG, V, FIRST>(L, g, d);
+  else launch_cg_p_t<T, EPS, MG, 1, FIRST>(L, g, d);
 }
 
 template <typename T>
-void launch_cg_p(const LaunchCfg& L, const Geo& g, const Dev<T>& d, int mg) {
-  if (mg) launch_cg_p_v<T, false, true>(L, g, d);
+void launch_cg_p(const LaunchCfg& L, const Geo& g, const Dev<T>& d, int mg, int first) {
+  if (mg && first) launch_cg_p_v<T, false, true, true>(L, g, d);
+  else if (mg) launch_cg_p_v<T, false, true>(L, g, d);
   else if (d.eps) launch_cg_p_v<T, true, false>(L, g, d);
   else launch_cg_p_v<T, false, false>(L, g, d);
 }
@@ -284,8 +301,8 @@ int march_blocks_per_sm(int fp32, int eps) {
   return eps ? occ_cg_p<double, true, 2>() : occ_cg_p<double, false, 2>();
 }
 
-template void launch_cg_p<float>(const LaunchCfg&, const Geo&, const Dev<float>&, int);
-template void launch_cg_p<double>(const LaunchCfg&, const Geo&, const Dev<double>&, int);
+template void launch_cg_p<float>(const LaunchCfg&, const Geo&, const Dev<float>&, int, int);
+template void launch_cg_p<double>(const LaunchCfg&, const Geo&, const Dev<double>&, int, int);
 template void launch_cg_r<float>(const LaunchCfg&, const Geo&, const Dev<float>&, int, cudaGraphConditionalHandle,
                                  int);
 template void launch_cg_r<double>(const LaunchCfg&, const Geo&, const Dev<double>&, int,

@@ -105,7 +105,7 @@ struct Scalars {
   int nonfinite;
   unsigned long long sched_next;   // dynamic tile scheduler: next tile
   unsigned sched_done;             // blocks that ran out of tiles
-  int pad;
+  int zero_solves;                 // solves that ended with no iteration (per pf_step call)
 };
 
 // ---------------------------------------------------------------- reductions

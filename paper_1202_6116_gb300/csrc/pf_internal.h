@@ -88,7 +88,7 @@ void launch_rhs(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, c
 // mg = 1: the search direction is built from z (multigrid-preconditioned
 // CG) instead of r/diag, and k_cg_r leaves r.z and beta to the V-cycle.
 template <typename T>
-void launch_cg_p(const LaunchCfg& L, const Geo& g, const Dev<T>& d, int mg);
+void launch_cg_p(const LaunchCfg& L, const Geo& g, const Dev<T>& d, int mg, int first = 0);
 template <typename T>
 void launch_cg_r(const LaunchCfg& L, const Geo& g, const Dev<T>& d, int mg, cudaGraphConditionalHandle cond,
                  int use_cond);

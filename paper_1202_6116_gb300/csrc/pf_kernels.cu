@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cg_finish(Geo g, T* __restrict__ x
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       S->mean_x = singular ? out[0] / (double)g.n : 0.0;
       S->pending = 0;
+      if (S->iter == 0) S->zero_solves += 1;
       S->total_iters += S->iter;
       S->last_iters = S->iter;
       if (S->status != 0) S->nonconv += 1;
