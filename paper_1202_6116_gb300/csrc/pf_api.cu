@@ -122,7 +122,7 @@ bool extrapolates(const pf_params* p) {
   return !(p->flags & PF_FLAG_WARM_LAST) && p->integrator == PF_EULER;
 }
 
-// FP32 time series keep the potential compensated (k_extrap_comp) unless the
+// FP32 time series keep the potential compensated (see k_cg_finish_comp) unless the
 // problem is singular (all-periodic: its mean removal acts on phi alone).
 bool comp_buffers(const pf_params* p) { return extrapolates(p) && p->precision == PF_FP32; }
 
@@ -523,32 +523,34 @@ void comp_view(pf_ctx* ctx, pf::Dev<T>& d) {
   d.cp.hi = (T*)ctx->phi;
   d.cp.lo = (T*)(ws + ctx->lay.clo);
   for (int i = 0; i < 3; ++i) d.cp.ring[i] = (T*)(ws + ctx->lay.hist[i]);
-  d.cp.nsolve = (const long long*)(ws + ctx->lay.xctr);
+  d.cp.nsolve = (long long*)(ws + ctx->lay.xctr);
   d.phi = (T*)(ws + ctx->lay.cx);
 }
 
-// Extrapolated initial guess of the next step solve: in the bound phi buffer,
-// or (compensated) in the pair phi + lo with the correction zeroed.
+// Does a step solve start with k_extrap?  (Compensated series form their
+// start at the end of the solve before.)
+bool plain_extrap(const pf_ctx* ctx) { return extrapolates(&ctx->prm) && !compensated(ctx); }
+
+// Extrapolated initial guess of the next step solve, in the bound phi buffer.
 template <typename T>
 void launch_extrap_of(pf_ctx* ctx, const pf::LaunchCfg& L) {
   long long* xc = (long long*)(ctx->ws + ctx->lay.xctr);
-  if constexpr (std::is_same<T, float>::value) {
-    if (compensated(ctx)) {
-      pf::Dev<float> d{};
-      comp_view<float>(ctx, d);
-      pf::launch_extrap_comp(L, ctx->geo.n, d.cp, d.phi, xc, (unsigned*)(xc + 1));
-      return;
-    }
-  }
   T* const ring[3] = {(T*)(ctx->ws + ctx->lay.hist[0]), (T*)(ctx->ws + ctx->lay.hist[1]),
                       (T*)(ctx->ws + ctx->lay.hist[2])};
   pf::launch_extrap<T>(L, ctx->geo.n, (T*)ctx->phi, ring, xc, (unsigned*)(xc + 1));
 }
 
-// Forget the extrapolation history (the next step solve starts from phi).
+// Forget the extrapolation history (the next step solve starts from phi; a
+// compensated one from phi + 0 with increment 0 and correction 0).
 pf_status reset_history(pf_ctx* ctx) {
   if (!extrapolates(&ctx->prm)) return PF_OK;
   PF_CUDA(cudaMemsetAsync(ctx->ws + ctx->lay.xctr, 0, sizeof(long long), ctx->stream));
+  if (comp_buffers(&ctx->prm)) {
+    const size_t bytes = (size_t)ctx->geo.n * sizeof(float);
+    PF_CUDA(cudaMemsetAsync(ctx->ws + ctx->lay.clo, 0, bytes, ctx->stream));
+    PF_CUDA(cudaMemsetAsync(ctx->ws + ctx->lay.cx, 0, bytes, ctx->stream));
+    PF_CUDA(cudaMemsetAsync(ctx->ws + ctx->lay.hist[0], 0, bytes, ctx->stream));
+  }
   return PF_OK;
 }
 
@@ -578,10 +580,10 @@ pf_status solve(pf_ctx* ctx, const T* P, bool adj = false, bool step_solve = fal
     after_launch(ctx, F_INVDIAG, 2 * N * w);
     ctx->invd_dirty = false;
   }
-  if (step_solve && extrapolates(&ctx->prm)) {
+  if (step_solve && plain_extrap(ctx)) {
     before_launch(ctx);
     launch_extrap_of<T>(ctx, ctx->L);
-    after_launch(ctx, F_EXTRAP, (comp ? 9 : 6) * N * w);   // steady state
+    after_launch(ctx, F_EXTRAP, 6 * N * w);   // steady state: 4 reads, 2 writes
   }
   if (ctx->singular) {
     before_launch(ctx);
@@ -623,7 +625,7 @@ pf_status solve(pf_ctx* ctx, const T* P, bool adj = false, bool step_solve = fal
   if (!s.zero_x) est_iters = std::max(1, s.iter);
   before_launch(ctx);
   pf::launch_cg_finish<T>(ctx->L, g, d, ctx->singular);
-  after_launch(ctx, F_FINISH, (comp ? (s.pending ? 8.0 : 7.0) : s.zero_x ? 1.0 : (s.pending ? 3.0 : 1.0)) * N * w);
+  after_launch(ctx, F_FINISH, (comp ? (s.pending ? 12.0 : 11.0) : s.zero_x ? 1.0 : (s.pending ? 3.0 : 1.0)) * N * w);
   if (ctx->singular) {
     pf::launch_sub_mean<T>(ctx->L, g, d);
     after_launch(ctx, F_SUB_MEAN, 2 * N * w);
@@ -653,7 +655,7 @@ void step_kernel_counts(const pf_ctx* ctx, int refresh, int64_t* fixed, int64_t*
                          ? 4 * (int64_t)mg_tail_start(ctx->lay, ctx->prm.precision == PF_FP32 ? 4 : 8) + 1
                          : 0;
   const bool heun = ctx->prm.integrator == PF_HEUN;
-  const int64_t per_solve = (ctx->singular ? 2 : 0) + 2 + vc + (extrapolates(&ctx->prm) ? 1 : 0);
+  const int64_t per_solve = (ctx->singular ? 2 : 0) + 2 + vc + (plain_extrap(ctx) ? 1 : 0);
   *per_iter = 2 + vc;
   // graph-captured multigrid solves run their first iteration outside the loop
   const int64_t peeled = vc ? *per_iter : 0;
@@ -707,7 +709,7 @@ cudaError_t append_step(pf_ctx* ctx, cudaGraph_t graph, std::vector<cudaGraphNod
     cudaGraphConditionalHandle h = 0;
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
     segment([&] {
-      if (extrapolates(&ctx->prm)) launch_extrap_of<T>(ctx, ctx->L);
+      if (plain_extrap(ctx)) launch_extrap_of<T>(ctx, ctx->L);
       if (ctx->singular) pf::launch_rhs_mean<T>(ctx->L, g, d, P);
       pf::launch_rhs<T>(ctx->L, g, d, P, h, 1);
       if (mg) {                  // the first iteration (p = z) runs outside the loop

@@ -27,16 +27,16 @@ struct LaunchCfg {
   cudaStream_t stream;
 };
 
-// Compensated potential of an FP32 time series: the solution is the pair
-// hi + lo of FP32 words (hi is the bound phi, lo its rounding remainder), and
-// ring holds the differences of the last three solutions, D_m in slot m mod 3
-// (see k_extrap_comp).  lo == nullptr: off.
+// Compensated potential of an FP32 time series (see k_cg_finish_comp): hi is the
+// bound phi, lo the rest of the start (the part of the last solution hi cannot
+// hold plus the extrapolation increment), ring the differences of the last
+// solutions.  lo == nullptr: off.
 template <typename T>
 struct Comp {
   T* hi;
   T* lo;
   T* ring[3];
-  const long long* nsolve;   // solves in the history (after this solve's guess)
+  long long* nsolve;   // solves in the history
 };
 
 // Device views of one context's buffers, typed by the storage precision.
@@ -113,12 +113,10 @@ void launch_tdgl(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, 
                  int corr, const Noise& nz);
 template <typename T>
 void launch_invdiag(const LaunchCfg& L, const Geo& g, const Dev<T>& d);
-// Extrapolated initial guess of a time step's solve (see k_extrap), and its
-// compensated FP32 form (see k_extrap_comp; x is the correction, zeroed).
+// Extrapolated initial guess of a time step's solve (see k_extrap; FP32 time
+// series form theirs in k_cg_finish).
 template <typename T>
 void launch_extrap(const LaunchCfg& L, long long n, T* phi, T* const ring[3], long long* nsolve, unsigned* ticket);
-void launch_extrap_comp(const LaunchCfg& L, long long n, const Comp<float>& cp, float* x, long long* nsolve,
-                        unsigned* ticket);
 // Adjoint update (pf_adjoint.cu): lam_out from lam, the adjoint potential psi
 // and the state P; adds the parameter sensitivities to grad[4] and, when
 // gv_lo/gv_hi are non-NULL, the face-voltage sensitivities.

@@ -2,14 +2,13 @@
 //
 //   (the right-hand side and TDGL kernels live in pf_step.cu, the CG
 //   iteration kernels in pf_cg.cu, the multigrid V-cycle in pf_mg.cu)
-//   k_cg_finish  last deferred x update / zero solution, mean of x (or the
-//                correction folded into a compensated potential)
+//   k_cg_finish  last deferred x update / zero solution, mean of x
+//   k_cg_finish_comp  the same for an FP32 time series: the compensated
+//                potential and the next solve's extrapolated start
 //   k_sub_mean   x -= mean(x)                           (singular problems)
 //   k_invdiag    1/diag(A) when a permittivity field is bound
 //   k_extrap     initial guess of a time step's Poisson solve extrapolated
 //                from the last four solutions
-//   k_extrap_comp  the same for FP32 time series, on a compensated potential
-//                (FP32 pair hi + lo) and the differences of past solutions
 //
 // All reductions use the last-block pattern of pf_common.cuh: deterministic,
 // and no block ever waits on another.  The CG scalars (alpha, beta, the
@@ -75,41 +74,32 @@ __device__ __forceinline__ float2 two_sum(float a, float b) {
   return make_float2(s, e);
 }
 
-// COMP (FP32 time series): x is the correction to the compensated start
-// hi + lo.  The solution becomes hi + lo + x (TwoSum, so lo keeps what hi
-// cannot hold), and the ring slot of this solve (holding the extrapolation
-// increment c) gains x, giving the difference D_k = phi_k - phi_{k-1}.
-// Per cell: read x, p, hi, lo, the slot; write hi, lo, the slot.
-template <typename T, bool COMP>
+// Increment of the extrapolated start of solve k over phi_{k-1}, from the
+// differences d_j = phi_{k-j} - phi_{k-j-1} of the last solutions: constant
+// (k <= 1), linear, quadratic, then cubic,
+//   c = d1,  2 d1 - d2,  3 (d1 - d2) + d3,
+// the increments of 2 phi_1 - phi_2, 3 phi_1 - 3 phi_2 + phi_3 and
+// 4 phi_1 - 6 phi_2 + 4 phi_3 - phi_4 (phi_j = phi_{k-j}).
+__device__ __forceinline__ float extrap_inc(long long k, float d1, float d2, float d3) {
+  if (k <= 1) return 0.0f;
+  if (k == 2) return d1;
+  if (k == 3) return 2.0f * d1 - d2;
+  return 3.0f * (d1 - d2) + d3;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(NTHREADS) k_cg_finish(Geo g, T* __restrict__ x, const T* __restrict__ p0,
                                                         const T* __restrict__ p1, double* part, Scalars* S,
-                                                        int singular, Comp<T> cp) {
+                                                        int singular) {
   const int zero = S->zero_x, pend = S->pending;
   const T alpha = T(S->alpha);
   const T* __restrict__ p = S->pbuf ? p1 : p0;
-  T* __restrict__ slot = nullptr;
-  if constexpr (COMP) slot = cp.ring[(*cp.nsolve + 2) % 3];   // solve k = nsolve - 1
   Acc<T> ax;
   for (long long t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
     TileCoord tc = tile_coord(g, t);
     if (!tc.active) continue;
     for (int z = tc.z0; z < tc.z1; ++z) {
       const long long c = (long long)z * g.nxy + (long long)tc.y * g.nx + tc.x;
-      if constexpr (COMP) {
-        const T hi = cp.hi[c], lo = cp.lo[c], inc = slot[c];
-        if (zero) {                     // phi_k = 0
-          cp.hi[c] = T(0);
-          cp.lo[c] = T(0);
-          slot[c] = (inc - lo) - hi;
-        } else {
-          const T dx = pend ? x[c] + alpha * p[c] : x[c];
-          const float2 sl = two_sum(hi, lo + dx);
-          cp.hi[c] = sl.x;
-          cp.lo[c] = sl.y;
-          slot[c] = inc + dx;
-        }
-        continue;
-      }
       if (zero) {
         x[c] = T(0);
       } else if (pend) {
@@ -135,6 +125,112 @@ __global__ void __launch_bounds__(NTHREADS) k_cg_finish(Geo g, T* __restrict__ x
       if (S->status != 0) S->nonconv += 1;
       S->ticket = 0;
     }
+  }
+}
+
+// COMP: the compensated potential of an FP32 time series (non-singular
+// problems, extrapolated starts).  Rounding the potential to FP32 leaves a
+// residual of order u |A| |phi|, above a 1e-7 tolerance on large films, and an
+// extrapolation of rounded potentials would carry its weights' worth of it
+// into every start.  So solve k starts from the pair hi + s, where hi is the
+// bound phi (phi_{k-1} rounded to FP32) and s = lo + c_k holds the part of
+// phi_{k-1} that hi cannot (lo) plus the extrapolation increment c_k; x is
+// the correction the Krylov loop finds.  The ring holds the differences
+// D_m = phi_m - phi_{m-1}, small beside phi and so nearly exact in FP32, in
+// slot m mod 3; slot k holds c_k during solve k.  This kernel ends solve k:
+//   phi_k = hi + s + x       -> (hi, lo) by TwoSum; phi = hi
+//   D_k = c_k + x            -> slot k
+//   c_{k+1} from D_k, D_{k-1}, D_{k-2} -> slot k + 1 (D_{k-2} read first)
+//   s = lo + c_{k+1}, x = 0 (the next solve's start), and the count k + 1.
+// A reset history starts with s = 0, slot 0 = 0, x = 0 and k = 0.
+// Per cell: read x, p, hi, s and three slots; write hi, s, two slots and x
+// (flat, 16-byte vectors).
+__device__ __forceinline__ void finish_comp_cell(bool zero, long long k, float dx, float& hi, float& sv, float& ck,
+                                                 float d1, float& dm2) {
+  float nlo, dk;
+  if (zero) {                     // phi_k = 0 = phi_{k-1} + D_k, phi_{k-1} = hi + s - c_k
+    dk = (ck - sv) - hi;
+    hi = 0.0f;
+    nlo = 0.0f;
+  } else {
+    const float2 sl = two_sum(hi, sv + dx);
+    hi = sl.x;
+    nlo = sl.y;
+    dk = ck + dx;
+  }
+  const float cn = extrap_inc(k + 1, dk, d1, dm2);
+  sv = nlo + cn;
+  ck = dk;
+  dm2 = cn;
+}
+
+__global__ void __launch_bounds__(FLAT_THREADS) k_cg_finish_comp(long long n, float* __restrict__ x,
+                                                                const float* __restrict__ p0,
+                                                                const float* __restrict__ p1, Scalars* S,
+                                                                Comp<float> cp) {
+  __shared__ bool last;
+  const bool zero = S->zero_x;
+  const int pend = S->pending;
+  const float alpha = float(S->alpha);
+  const float* __restrict__ p = S->pbuf ? p1 : p0;
+  const long long k = *cp.nsolve;
+  float* const rk = cp.ring[k % 3];         // c_k, then D_k
+  float* const r1 = cp.ring[(k + 2) % 3];   // D_{k-1}
+  float* const r2 = cp.ring[(k + 1) % 3];   // D_{k-2}, then c_{k+1}
+  const long long stride = (long long)gridDim.x * FLAT_THREADS;
+  const long long nvec = n / 4;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < nvec; i += stride) {
+    float4 xv = reinterpret_cast<const float4*>(x)[i];
+    if (pend) {
+      const float4 pv = reinterpret_cast<const float4*>(p)[i];
+      xv.x += alpha * pv.x;
+      xv.y += alpha * pv.y;
+      xv.z += alpha * pv.z;
+      xv.w += alpha * pv.w;
+    }
+    float4 h = reinterpret_cast<const float4*>(cp.hi)[i];
+    float4 sv = reinterpret_cast<const float4*>(cp.lo)[i];
+    float4 c = reinterpret_cast<const float4*>(rk)[i];
+    const float4 a = k >= 1 ? reinterpret_cast<const float4*>(r1)[i] : z4;
+    float4 b = k >= 2 ? reinterpret_cast<const float4*>(r2)[i] : z4;
+    finish_comp_cell(zero, k, xv.x, h.x, sv.x, c.x, a.x, b.x);
+    finish_comp_cell(zero, k, xv.y, h.y, sv.y, c.y, a.y, b.y);
+    finish_comp_cell(zero, k, xv.z, h.z, sv.z, c.z, a.z, b.z);
+    finish_comp_cell(zero, k, xv.w, h.w, sv.w, c.w, a.w, b.w);
+    reinterpret_cast<float4*>(cp.hi)[i] = h;
+    reinterpret_cast<float4*>(cp.lo)[i] = sv;
+    reinterpret_cast<float4*>(rk)[i] = c;
+    reinterpret_cast<float4*>(r2)[i] = b;
+    reinterpret_cast<float4*>(x)[i] = z4;
+  }
+  for (long long i = nvec * 4 + blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += stride) {
+    const float dx = pend ? x[i] + alpha * p[i] : x[i];
+    float h = cp.hi[i], sv = cp.lo[i], c = rk[i], b = k >= 2 ? r2[i] : 0.0f;
+    finish_comp_cell(zero, k, dx, h, sv, c, k >= 1 ? r1[i] : 0.0f, b);
+    cp.hi[i] = h;
+    cp.lo[i] = sv;
+    rk[i] = c;
+    r2[i] = b;
+    x[i] = 0.0f;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&S->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    S->mean_x = 0.0;
+    S->pending = 0;
+    if (S->iter == 0) S->zero_solves += 1;
+    S->total_iters += S->iter;
+    S->last_iters = S->iter;
+    if (S->status != 0) S->nonconv += 1;
+    S->ticket = 0;
+    *cp.nsolve = k + 1;
+    __threadfence();
   }
 }
 
@@ -241,96 +337,17 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_extrap(long long n, T* __restr
   }
 }
 
-// Compensated form for FP32 time series (non-singular problems).  Rounding
-// the potential to FP32 leaves a residual of order u |A| |phi|, well above a
-// 1e-7 tolerance on large films, and the extrapolation above would add its
-// weights' worth of it to every start.  Here the last solution is the pair
-// hi + lo (lo: the part hi cannot hold), and the ring holds the differences
-// D_m = phi_m - phi_{m-1} of consecutive solutions (slot m mod 3), small
-// beside phi and so nearly exact in FP32.  The start of solve k is
-// phi_{k-1} + c with the increment
-//   c = 0 (k <= 1), D1 (k = 2), 2 D1 - D2 (k = 3), 3 (D1 - D2) + D3 (k >= 4)
-// (D_j = D_{k-j}; the same linear, quadratic and cubic extrapolations as
-// above), added to the pair by TwoSum.  c goes into the slot of D_{k-3} once
-// that has been read; k_cg_finish adds the solve's correction x to it, which
-// makes it D_k.  Solve 0 keeps hi and drops a stale lo.  x starts at 0.
-// Per cell at k >= 4: read hi, lo and 3 differences; write hi, lo, c and x.
-__device__ __forceinline__ float extrap_inc(long long k, float d1, float d2, float d3) {
-  if (k <= 1) return 0.0f;
-  if (k == 2) return d1;
-  if (k == 3) return 2.0f * d1 - d2;
-  return 3.0f * (d1 - d2) + d3;
-}
-
-__global__ void __launch_bounds__(FLAT_THREADS) k_extrap_comp(long long n, Comp<float> cp, float* __restrict__ x,
-                                                             long long* nsolve, unsigned* ticket) {
-  __shared__ bool last;
-  const long long k = *nsolve;
-  const float* const r1 = cp.ring[(k + 2) % 3];   // D_{k-1}
-  const float* const r2 = cp.ring[(k + 1) % 3];   // D_{k-2}
-  float* const r3 = cp.ring[k % 3];               // D_{k-3}, then c
-  const long long stride = (long long)gridDim.x * FLAT_THREADS;
-  const long long nvec = n / 4;
-  auto one = [&](float& hi, float& lo, float d1, float d2, float d3) -> float {
-    if (k == 0) {
-      lo = 0.0f;
-      return 0.0f;
-    }
-    const float c = extrap_inc(k, d1, d2, d3);
-    const float2 sl = two_sum(hi, lo + c);
-    hi = sl.x;
-    lo = sl.y;
-    return c;
-  };
-  for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < nvec; i += stride) {
-    float4 h = reinterpret_cast<const float4*>(cp.hi)[i];
-    float4 l = make_float4(0.f, 0.f, 0.f, 0.f), a = l, b = l, e = l;
-    if (k >= 1) l = reinterpret_cast<const float4*>(cp.lo)[i];
-    if (k >= 2) a = reinterpret_cast<const float4*>(r1)[i];
-    if (k >= 3) b = reinterpret_cast<const float4*>(r2)[i];
-    if (k >= 4) e = reinterpret_cast<const float4*>(r3)[i];
-    float4 c;
-    c.x = one(h.x, l.x, a.x, b.x, e.x);
-    c.y = one(h.y, l.y, a.y, b.y, e.y);
-    c.z = one(h.z, l.z, a.z, b.z, e.z);
-    c.w = one(h.w, l.w, a.w, b.w, e.w);
-    if (k >= 1) reinterpret_cast<float4*>(cp.hi)[i] = h;
-    reinterpret_cast<float4*>(cp.lo)[i] = l;
-    reinterpret_cast<float4*>(r3)[i] = c;
-    reinterpret_cast<float4*>(x)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  for (long long i = nvec * 4 + blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += stride) {
-    float h = cp.hi[i], l = k >= 1 ? cp.lo[i] : 0.0f;
-    const float c = one(h, l, k >= 2 ? r1[i] : 0.0f, k >= 3 ? r2[i] : 0.0f, k >= 4 ? r3[i] : 0.0f);
-    if (k >= 1) cp.hi[i] = h;
-    cp.lo[i] = l;
-    r3[i] = c;
-    x[i] = 0.0f;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    *ticket = 0u;
-    *nsolve = k + 1;
-    __threadfence();
-  }
-}
-
 // ---------------------------------------------------------------- launchers
 
 template <typename T>
 void launch_cg_finish(const LaunchCfg& L, const Geo& g, const Dev<T>& d, int singular) {
   if constexpr (std::is_same<T, float>::value) {
     if (d.cp.lo) {
-      k_cg_finish<T, true><<<L.grid, L.block, 0, L.stream>>>(g, d.phi, d.p0, d.p1, d.part, d.S, 0, d.cp);
+      k_cg_finish_comp<<<L.flat_grid, FLAT_THREADS, 0, L.stream>>>(g.n, d.phi, d.p0, d.p1, d.S, d.cp);
       return;
     }
   }
-  k_cg_finish<T, false><<<L.grid, L.block, 0, L.stream>>>(g, d.phi, d.p0, d.p1, d.part, d.S, singular, d.cp);
+  k_cg_finish<T><<<L.grid, L.block, 0, L.stream>>>(g, d.phi, d.p0, d.p1, d.part, d.S, singular);
 }
 
 template <typename T>
@@ -346,11 +363,6 @@ void launch_invdiag(const LaunchCfg& L, const Geo& g, const Dev<T>& d) {
 template <typename T>
 void launch_extrap(const LaunchCfg& L, long long n, T* phi, T* const ring[3], long long* nsolve, unsigned* ticket) {
   k_extrap<T><<<L.flat_grid, FLAT_THREADS, 0, L.stream>>>(n, phi, ring[0], ring[1], ring[2], nsolve, ticket);
-}
-
-void launch_extrap_comp(const LaunchCfg& L, long long n, const Comp<float>& cp, float* x, long long* nsolve,
-                        unsigned* ticket) {
-  k_extrap_comp<<<L.flat_grid, FLAT_THREADS, 0, L.stream>>>(n, cp, x, nsolve, ticket);
 }
 
 #define PF_INSTANTIATE(T)                                                                                   \
