@@ -74,7 +74,9 @@ def workload_config(w, name, flush, args=None):
     if args is not None:
         c["integrator"] = args.integrator
         c["poisson_every"] = max(1, args.poisson_every)
-        c["warm_start"] = "last potential" if args.warm_last else "extrapolated (last four potentials, compensated in FP32)"
+        order = args.extrap_order or (1 if args.noise > 0 else 2 if w.rtol > 5e-7 else 3)
+        c["warm_start"] = ("last potential" if args.warm_last else
+                           "extrapolated (order %d from the last potentials, compensated in FP32)" % order)
         if args.noise > 0:
             c["noise_sigma"] = args.noise
         if w.n_air:
@@ -241,7 +243,7 @@ def run_ours(args):
         w = w.with_(dt=args.dt)
     over = {"flags": (pf.PF_FLAG_NO_GRAPHS if args.no_graphs else 0) | (pf.PF_FLAG_WARM_LAST if args.warm_last else 0),
             "integrator": pf.PF_HEUN if args.integrator == "heun" else pf.PF_EULER,
-            "poisson_every": args.poisson_every}
+            "poisson_every": args.poisson_every, "extrap_order": args.extrap_order}
     film = Film(w, device=dev, **over)
     if args.noise > 0:
         film.set_noise(args.noise, 12345)
@@ -385,7 +387,7 @@ def run_batch(args):
         if k not in tuned:
             tuned[k] = AT.tune(w, steps=3, warmup=1, device=dev)
     tune_s = time.perf_counter() - t0
-    films = [Film(w, device=dev) for w in ws]
+    films = [Film(w, device=dev, extrap_order=args.extrap_order) for w in ws]
     for f in films:
         AT.apply(f, tuned[AT.key_of(f.w)])
     record_every = 10
@@ -432,6 +434,7 @@ def run_batch(args):
                                    "seed 4), grounded bottom, ramped top electrode, %s rtol=1e-06 dt=0.01"
                                    % (len(ws), "MG-PCG" if ws[0].solver == "mg" else "Jacobi-PCG"),
                        "cells": cells, "films": len(ws), "solver": ws[0].solver,
+                       "extrap_order": args.extrap_order or (2 if ws[0].rtol > 5e-7 else 3),
                        "l2": "inputs larger than L2 (%.2f GB of film state)" % (cells * 4 * 11 / 1e9)},
             "poisson_iters_per_step": info["total_iters"] / args.steps / len(ws),
             "gpu_launches": info["kernel_launches"], "status": pf.STATUS_NAMES[st],
@@ -616,6 +619,8 @@ def main():
     ap.add_argument("--poisson-every", type=int, default=1, help="solve the potential on every k-th step only")
     ap.add_argument("--dt", type=float, default=None, help="override the workload's time step")
     ap.add_argument("--noise", type=float, default=0.0, help="thermal random force sigma (0: off)")
+    ap.add_argument("--extrap-order", type=int, choices=(0, 1, 2, 3), default=0,
+                    help="highest order of the extrapolated start (0: automatic)")
     ap.add_argument("--warm-last", action="store_true",
                     help="start each solve from the last potential (the paper's scheme) instead of extrapolating")
     ap.add_argument("--no-graphs", action="store_true",

@@ -77,7 +77,13 @@ typedef struct {
   int32_t integrator;        /* PF_EULER (0) or PF_HEUN (the paper's predictor-corrector) */
   int32_t poisson_every;     /* solve the potential on every k-th step only (0 or 1: every step) */
   int32_t n_air;             /* top layers that are air (0 <= n_air < nz; needs periodic_z = 0) */
-  int32_t reserved[3];       /* must be zero */
+  int32_t extrap_order;      /* highest order of the extrapolated start (see PF_FLAG_WARM_LAST):
+                                1 linear, 2 quadratic, 3 cubic; 0: automatic: cubic when
+                                poisson_rtol <= 5e-7, quadratic above, linear while the thermal
+                                noise is on (a start inherits the previous solves' residuals
+                                times the weights' magnitudes, 3, 7 and 15, and the noise
+                                roughens the potential series) */
+  int32_t reserved[2];       /* must be zero */
 } pf_params;
 
 /* pf_params.integrator (Section Time Integration), with R(P) = L(-df/dP +
@@ -108,10 +114,11 @@ typedef struct {
  *                      potential, as the paper does (Section Numerical
  *                      Performance).  Without it, forward-Euler runs (which
  *                      solve every step, or every poisson_every-th: equally
- *                      spaced in time either way) start solve k from the cubic
- *                      extrapolation 4 phi_{k-1} - 6 phi_{k-2} + 4 phi_{k-3}
- *                      - phi_{k-4} of the last four potentials (quadratic,
- *                      linear, then constant, for the first solves after
+ *                      spaced in time either way) start solve k from a
+ *                      polynomial extrapolation of the last potentials, up to
+ *                      the order extrap_order of pf_params (cubic:
+ *                      4 phi_{k-1} - 6 phi_{k-2} + 4 phi_{k-3} - phi_{k-4};
+ *                      lower orders, then constant, for the first solves after
  *                      pf_bind, pf_solve_potential or a pf_set_bc that changes
  *                      an electrode layout; voltage changes keep the
  *                      history): the same stopping test, a closer start,

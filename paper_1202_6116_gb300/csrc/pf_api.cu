@@ -111,7 +111,8 @@ bool params_valid(const pf_params* p, std::string* why) {
   if (p->poisson_every < 0) return fail("poisson_every must be >= 0");
   if (p->n_air < 0 || p->n_air >= p->nz) return fail("n_air must be in 0 .. nz - 1");
   if (p->n_air > 0 && p->periodic_z) return fail("air layers need non-periodic z (periodic_z = 0)");
-  for (int i = 0; i < 3; ++i)
+  if (p->extrap_order < 0 || p->extrap_order > 3) return fail("extrap_order must be in 0 .. 3");
+  for (int i = 0; i < 2; ++i)
     if (p->reserved[i] != 0) return fail("reserved fields must be zero");
   return true;
 }
@@ -512,6 +513,19 @@ pf_status read_scalars(pf_ctx* ctx) {
   return PF_OK;
 }
 
+// 1 + the highest order of the extrapolated start.  extrap_order, or
+// automatically: a start inherits the previous solves' residuals (each up to
+// the tolerance) times the sum of the weights' magnitudes (3, 7, 15 for orders
+// 1, 2, 3) and the truncation error of the order.  So the cubic pays at tight
+// tolerances, the quadratic at looser ones (above 5e-7), and the linear while
+// the thermal noise roughens the potential series.
+int extrap_kcap(const pf_ctx* ctx) {
+  const int o = ctx->prm.extrap_order;
+  if (o > 0) return 1 + o;
+  if (ctx->noise_sigma > 0.0) return 2;
+  return ctx->prm.poisson_rtol > 5e-7 ? 3 : 4;
+}
+
 // Is this context's next step solve compensated (see comp_buffers)?
 bool compensated(const pf_ctx* ctx) { return comp_buffers(&ctx->prm) && !ctx->singular; }
 
@@ -524,6 +538,7 @@ void comp_view(pf_ctx* ctx, pf::Dev<T>& d) {
   d.cp.lo = (T*)(ws + ctx->lay.clo);
   for (int i = 0; i < 3; ++i) d.cp.ring[i] = (T*)(ws + ctx->lay.hist[i]);
   d.cp.nsolve = (long long*)(ws + ctx->lay.xctr);
+  d.cp.kcap = extrap_kcap(ctx);
   d.phi = (T*)(ws + ctx->lay.cx);
 }
 
@@ -537,7 +552,7 @@ void launch_extrap_of(pf_ctx* ctx, const pf::LaunchCfg& L) {
   long long* xc = (long long*)(ctx->ws + ctx->lay.xctr);
   T* const ring[3] = {(T*)(ctx->ws + ctx->lay.hist[0]), (T*)(ctx->ws + ctx->lay.hist[1]),
                       (T*)(ctx->ws + ctx->lay.hist[2])};
-  pf::launch_extrap<T>(L, ctx->geo.n, (T*)ctx->phi, ring, xc, (unsigned*)(xc + 1));
+  pf::launch_extrap<T>(L, ctx->geo.n, (T*)ctx->phi, ring, xc, (unsigned*)(xc + 1), extrap_kcap(ctx));
 }
 
 // Forget the extrapolation history (the next step solve starts from phi; a

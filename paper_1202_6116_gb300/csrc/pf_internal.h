@@ -37,6 +37,7 @@ struct Comp {
   T* lo;
   T* ring[3];
   long long* nsolve;   // solves in the history
+  int kcap;            // 1 + the highest extrapolation order
 };
 
 // Device views of one context's buffers, typed by the storage precision.
@@ -116,7 +117,8 @@ void launch_invdiag(const LaunchCfg& L, const Geo& g, const Dev<T>& d);
 // Extrapolated initial guess of a time step's solve (see k_extrap; FP32 time
 // series form theirs in k_cg_finish).
 template <typename T>
-void launch_extrap(const LaunchCfg& L, long long n, T* phi, T* const ring[3], long long* nsolve, unsigned* ticket);
+void launch_extrap(const LaunchCfg& L, long long n, T* phi, T* const ring[3], long long* nsolve, unsigned* ticket,
+                   int kcap);
 // Adjoint update (pf_adjoint.cu): lam_out from lam, the adjoint potential psi
 // and the state P; adds the parameter sensitivities to grad[4] and, when
 // gv_lo/gv_hi are non-NULL, the face-voltage sensitivities.

@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(NTHREADS) k_cg_finish(Geo g, T* __restrict__ x
 // A reset history starts with s = 0, slot 0 = 0, x = 0 and k = 0.
 // Per cell: read x, p, hi, s and three slots; write hi, s, two slots and x
 // (flat, 16-byte vectors).
-__device__ __forceinline__ void finish_comp_cell(bool zero, long long k, float dx, float& hi, float& sv, float& ck,
-                                                 float d1, float& dm2) {
+__device__ __forceinline__ void finish_comp_cell(bool zero, long long k, int kcap, float dx, float& hi, float& sv,
+                                                 float& ck, float d1, float& dm2) {
   float nlo, dk;
   if (zero) {                     // phi_k = 0 = phi_{k-1} + D_k, phi_{k-1} = hi + s - c_k
     dk = (ck - sv) - hi;
@@ -158,7 +158,7 @@ __device__ __forceinline__ void finish_comp_cell(bool zero, long long k, float d
     nlo = sl.y;
     dk = ck + dx;
   }
-  const float cn = extrap_inc(k + 1, dk, d1, dm2);
+  const float cn = extrap_inc(k + 1 < kcap ? k + 1 : kcap, dk, d1, dm2);
   sv = nlo + cn;
   ck = dk;
   dm2 = cn;
@@ -194,10 +194,10 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_cg_finish_comp(long long n, fl
     float4 c = reinterpret_cast<const float4*>(rk)[i];
     const float4 a = k >= 1 ? reinterpret_cast<const float4*>(r1)[i] : z4;
     float4 b = k >= 2 ? reinterpret_cast<const float4*>(r2)[i] : z4;
-    finish_comp_cell(zero, k, xv.x, h.x, sv.x, c.x, a.x, b.x);
-    finish_comp_cell(zero, k, xv.y, h.y, sv.y, c.y, a.y, b.y);
-    finish_comp_cell(zero, k, xv.z, h.z, sv.z, c.z, a.z, b.z);
-    finish_comp_cell(zero, k, xv.w, h.w, sv.w, c.w, a.w, b.w);
+    finish_comp_cell(zero, k, cp.kcap, xv.x, h.x, sv.x, c.x, a.x, b.x);
+    finish_comp_cell(zero, k, cp.kcap, xv.y, h.y, sv.y, c.y, a.y, b.y);
+    finish_comp_cell(zero, k, cp.kcap, xv.z, h.z, sv.z, c.z, a.z, b.z);
+    finish_comp_cell(zero, k, cp.kcap, xv.w, h.w, sv.w, c.w, a.w, b.w);
     reinterpret_cast<float4*>(cp.hi)[i] = h;
     reinterpret_cast<float4*>(cp.lo)[i] = sv;
     reinterpret_cast<float4*>(rk)[i] = c;
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_cg_finish_comp(long long n, fl
   for (long long i = nvec * 4 + blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += stride) {
     const float dx = pend ? x[i] + alpha * p[i] : x[i];
     float h = cp.hi[i], sv = cp.lo[i], c = rk[i], b = k >= 2 ? r2[i] : 0.0f;
-    finish_comp_cell(zero, k, dx, h, sv, c, k >= 1 ? r1[i] : 0.0f, b);
+    finish_comp_cell(zero, k, cp.kcap, dx, h, sv, c, k >= 1 ? r1[i] : 0.0f, b);
     cp.hi[i] = h;
     cp.lo[i] = sv;
     rk[i] = c;
@@ -290,11 +290,12 @@ __device__ __forceinline__ T extrap_guess(long long k, T f1, T f2, T f3, T f4) {
 template <typename T>
 __global__ void __launch_bounds__(FLAT_THREADS) k_extrap(long long n, T* __restrict__ phi, T* __restrict__ s0,
                                                         T* __restrict__ s1, T* __restrict__ s2,
-                                                        long long* nsolve, unsigned* ticket) {
+                                                        long long* nsolve, unsigned* ticket, int kcap) {
   using V = typename Vec16<T>::type;
   constexpr int NV = 16 / sizeof(T);
   __shared__ bool last;
   const long long k = *nsolve;
+  const long long ke = k < kcap ? k : kcap;   // the order: ke - 1 (at most the requested one)
   T* const ring[3] = {s0, s1, s2};
   // phi_2, phi_3 and phi_4 (= the slot phi_1 goes to) of solve k; only the
   // ones solve k reads are ever dereferenced
@@ -305,9 +306,9 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_extrap(long long n, T* __restr
   const long long nvec = n / NV;
   for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < nvec; i += stride) {
     V v1 = reinterpret_cast<const V*>(phi)[i], v2{}, v3{}, v4{};
-    if (k >= 2) v2 = reinterpret_cast<const V*>(h2)[i];
-    if (k >= 3) v3 = reinterpret_cast<const V*>(h3)[i];
-    if (k >= 4) v4 = reinterpret_cast<const V*>(h4)[i];
+    if (ke >= 2) v2 = reinterpret_cast<const V*>(h2)[i];
+    if (ke >= 3) v3 = reinterpret_cast<const V*>(h3)[i];
+    if (ke >= 4) v4 = reinterpret_cast<const V*>(h4)[i];
     V gv;
     const T* f1 = reinterpret_cast<const T*>(&v1);
     const T* f2 = reinterpret_cast<const T*>(&v2);
@@ -315,14 +316,14 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_extrap(long long n, T* __restr
     const T* f4 = reinterpret_cast<const T*>(&v4);
     T* gs = reinterpret_cast<T*>(&gv);
 #pragma unroll
-    for (int j = 0; j < NV; ++j) gs[j] = extrap_guess(k, f1[j], f2[j], f3[j], f4[j]);
+    for (int j = 0; j < NV; ++j) gs[j] = extrap_guess(ke, f1[j], f2[j], f3[j], f4[j]);
     if (k >= 1) reinterpret_cast<V*>(h4)[i] = v1;
     reinterpret_cast<V*>(phi)[i] = gv;
   }
   for (long long i = nvec * NV + blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += stride) {
-    const T f1 = phi[i], f2 = k >= 2 ? h2[i] : T(0), f3 = k >= 3 ? h3[i] : T(0), f4 = k >= 4 ? h4[i] : T(0);
+    const T f1 = phi[i], f2 = ke >= 2 ? h2[i] : T(0), f3 = ke >= 3 ? h3[i] : T(0), f4 = ke >= 4 ? h4[i] : T(0);
     if (k >= 1) h4[i] = f1;
-    phi[i] = extrap_guess(k, f1, f2, f3, f4);
+    phi[i] = extrap_guess(ke, f1, f2, f3, f4);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -361,12 +362,13 @@ void launch_invdiag(const LaunchCfg& L, const Geo& g, const Dev<T>& d) {
 }
 
 template <typename T>
-void launch_extrap(const LaunchCfg& L, long long n, T* phi, T* const ring[3], long long* nsolve, unsigned* ticket) {
-  k_extrap<T><<<L.flat_grid, FLAT_THREADS, 0, L.stream>>>(n, phi, ring[0], ring[1], ring[2], nsolve, ticket);
+void launch_extrap(const LaunchCfg& L, long long n, T* phi, T* const ring[3], long long* nsolve, unsigned* ticket,
+                   int kcap) {
+  k_extrap<T><<<L.flat_grid, FLAT_THREADS, 0, L.stream>>>(n, phi, ring[0], ring[1], ring[2], nsolve, ticket, kcap);
 }
 
 #define PF_INSTANTIATE(T)                                                                                   \
-  template void launch_extrap<T>(const LaunchCfg&, long long, T*, T* const[3], long long*, unsigned*);     \
+  template void launch_extrap<T>(const LaunchCfg&, long long, T*, T* const[3], long long*, unsigned*, int); \
   template void launch_cg_finish<T>(const LaunchCfg&, const Geo&, const Dev<T>&, int);                      \
   template void launch_sub_mean<T>(const LaunchCfg&, const Geo&, const Dev<T>&);                            \
   template void launch_invdiag<T>(const LaunchCfg&, const Geo&, const Dev<T>&);

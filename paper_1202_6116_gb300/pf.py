@@ -42,7 +42,7 @@ class pf_params(C.Structure):
                 ("poisson_rtol", C.c_double), ("poisson_maxit", C.c_int32),
                 ("periodic_z", C.c_int32), ("has_eps", C.c_int32), ("flags", C.c_int32),
                 ("integrator", C.c_int32), ("poisson_every", C.c_int32), ("n_air", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("extrap_order", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class pf_step_info(C.Structure):

@@ -69,7 +69,8 @@ def test_workspace_bytes_and_validation(L):
     assert 0 < b32 < b64
     for field, bad in (("nx", 0), ("nz", -3), ("dx", 0.0), ("precision", 7), ("solver", 9),
                        ("poisson_rtol", 0.0), ("poisson_maxit", 0), ("periodic_z", 2), ("dt", float("nan")),
-                       ("integrator", 2), ("poisson_every", -1), ("n_air", 4), ("n_air", -1)):
+                       ("integrator", 2), ("poisson_every", -1), ("n_air", 4), ("n_air", -1),
+                       ("extrap_order", 4), ("extrap_order", -1)):
         q = good_params()
         setattr(q, field, bad)
         assert pf.pf_workspace_bytes(q) == 0, field
@@ -78,7 +79,7 @@ def test_workspace_bytes_and_validation(L):
         assert ctx.value is None
         assert pf.pf_last_error(None) != ""
     q = good_params()
-    q.reserved[2] = 1
+    q.reserved[1] = 1
     assert pf.pf_workspace_bytes(q) == 0
     q = good_params()
     q.n_air, q.periodic_z = 1, 1                   # air layers need non-periodic z
