@@ -265,15 +265,16 @@ __global__ void __launch_bounds__(NTHREADS) k_invdiag(Geo g, Bc<T> bc, const T* 
   }
 }
 
-// Initial guess of solve number k of a time series (k = *nsolve): the cubic
-// extrapolation 4 phi_1 - 6 phi_2 + 4 phi_3 - phi_4 of the last four
-// solutions (phi_1 = phi, the last one; the three before it sit in a ring of
-// history fields, phi_j of solve number m in slot m mod 3).  Solves 1 to 3
-// take the orders their history allows: the given phi, the last solution,
-// then the linear and quadratic extrapolations.  phi_1 goes into the slot of
-// phi_4 once that has been read, so the ring never moves.  The last block to
-// finish advances the count (every block reads it first).
-// Streams phi and the ring once: read 4 words, write 2 words per cell.
+// Initial guess of solve number k of a time series (k = *nsolve), FP64 and
+// singular FP32 problems: the cubic extrapolation 4 phi_1 - 6 phi_2 + 4 phi_3
+// - phi_4 of the last four solutions (phi_1 = phi, the last one; the three
+// before it sit in a ring of history fields, phi_j of solve number m in slot
+// m mod 3).  Solves 1 to 3 take the orders their history allows: the given
+// phi, the last solution, then the linear and quadratic extrapolations; kcap
+// (1 + the highest order asked for) caps the order.  phi_1 goes into the slot
+// of phi_4 once that has been read, so the ring never moves.  The last block
+// to finish advances the count (every block reads it first).
+// Streams phi and the ring once: read at most 4 words, write 2 words per cell.
 // The guess is formed from the differences of consecutive solutions (exact
 // in floating point when they are close) plus one final rounding.
 template <typename T>

@@ -5,9 +5,9 @@
 //           mean inside, P_cell at an electrode, 0 at an open face), the warm
 //           start residual r0 = b - A phi (Section Numerical Performance), and
 //           ||b||^2, ||r||^2, r.z.  An FP32 time series starts from the
-//           compensated pair phi + lo (r0 = b - A phi - A lo, see
-//           k_extrap_comp).  With MEAN = true it only sums b (the zero-mean
-//           projection of singular problems).
+//           compensated pair phi + s (r0 = b - A phi - A s, see
+//           k_cg_finish_comp).  With MEAN = true it only sums b (the
+//           zero-mean projection of singular problems).
 //   k_tdgl  P' = P + dt L (-df/dP + g Lap P + E), E = -grad phi from face values
 //           (Eq. TDGL with Eqs. F_bulk, dF_grad/dP, F_elec; Section Time Integration).
 //           Planes z >= zair are air: P = 0 there, and the film's top plane has
@@ -50,7 +50,7 @@ __device__ __forceinline__ T divergence(const Stencil7<Raw<T, NH>>& s, int dlo, 
   return div;
 }
 
-// COMP: the start is the compensated pair phi + lo (r0 = b - A phi - A lo).
+// COMP: the start is the compensated pair phi + s (r0 = b - A phi - A s).
 template <typename T, bool EPS, bool MEAN, int VX, bool COMP = false>
 __global__ void __launch_bounds__(MTX* MTY) k_rhs(Geo g, Bc<T> bc, const T* __restrict__ P, const T* __restrict__ phi,
                                                  const T* __restrict__ lo, const T* __restrict__ eps,

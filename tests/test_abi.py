@@ -101,3 +101,27 @@ def test_null_context_calls_are_rejected(L):
     assert L.pf_solve_potential(None, None) == pf.PF_ERR_ARG
     assert L.pf_bind(None, None, None, None, None, 0) == pf.PF_ERR_ARG
     assert L.pf_destroy(None) == pf.PF_OK
+
+
+def test_workspace_of_the_extrapolated_start():
+    """The extrapolated start costs three history fields (FP64); an FP32
+    series adds the compensated remainder and the Krylov correction (five
+    fields); the paper's last-potential start and the predictor-corrector
+    need none."""
+    p = good_params()
+    p.nx, p.ny, p.nz = 32, 32, 32                 # fields of 128 or 256 KiB: no alignment padding
+    n = 32 * 32 * 32
+    for prec, word, fields in ((pf.PF_FP64, 8, 3), (pf.PF_FP32, 4, 5)):
+        p.precision = prec
+        p.flags, p.integrator = 0, pf.PF_EULER
+        extrap = pf.pf_workspace_bytes(p)
+        p.flags = pf.PF_FLAG_WARM_LAST
+        last = pf.pf_workspace_bytes(p)
+        p.flags, p.integrator = 0, pf.PF_HEUN
+        heun = pf.pf_workspace_bytes(p)
+        assert extrap - last == fields * n * word
+        assert heun == last
+    p.integrator = pf.PF_EULER
+    for order in (1, 2, 3):                       # the order changes no layout
+        p.extrap_order = order
+        assert pf.pf_workspace_bytes(p) == extrap

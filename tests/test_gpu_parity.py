@@ -59,7 +59,7 @@ def test_fp64_grounded_film_200_steps(grounded_32):
 
 
 def test_fp64_extrapolated_warm_start(grounded_32):
-    """The default start of each step solve extrapolates the last three
+    """The default start of each step solve extrapolates the last
     potentials: the same results within the solve tolerance, fewer
     iterations than the last-potential start."""
     w, (Po, phio, sto, io), (Pt, phit, _, _) = grounded_32
