@@ -2,13 +2,16 @@
 and Gaussian variance), drawn per cell, component and step from a
 counter-based generator (Philox4x32-10 with the Box-Muller transform).
 
-The pins are statistical and analytic, independent of the generator's code:
-the draws are standard normal and uncorrelated; one step of the free process
+The pins are independent of the generator's code: the generator's published
+known-answer values (tests/golden/philox4x32_10_kat.json); the draws are
+standard normal and uncorrelated; one step of the free process
 has variance sigma^2 dt; a linear restoring force gives the Ornstein-Uhlenbeck
 process, whose discrete stationary variance has a closed form; the
 predictor-corrector adds the same increment in both stages.
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -16,6 +19,18 @@ import pytest
 import oracle as O
 
 scipy_stats = pytest.importorskip("scipy.stats")
+
+
+def test_philox_known_answers():
+    """Philox4x32-10 as published (Salmon et al., SC11): the known-answer
+    outputs for zero, all-ones and pi-digit counters and keys.  A wrong
+    multiplier, Weyl constant, round count or word order fails them."""
+    kat = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.json")))
+    for v in kat["vectors"]:
+        c = [int(w, 16) for w in v["counter"]]
+        k = [int(w, 16) for w in v["key"]]
+        cell, step, seed = c[0] | c[1] << 32, c[2] | c[3] << 32, k[0] | k[1] << 32
+        assert O.philox(seed, step, cell) == [int(w, 16) for w in v["out"]]
 
 
 def test_draws_are_standard_normal_and_uncorrelated():
