@@ -213,7 +213,9 @@ pf_status pf_step(pf_ctx* ctx, int32_t nsteps, pf_step_info* info);
 pf_status pf_step_host(pf_ctx* ctx, void* P_host, void* phi_host, int32_t nsteps,
                        pf_step_info* info);
 
-/* Solve the Poisson problem for the current P only (no P update). */
+/* Solve the Poisson problem for the current P only (no P update; Eqs. rho
+ * and Poisson), starting from the bound phi.  Restarts the extrapolation
+ * history of pf_step: its next solve starts from this potential. */
 pf_status pf_solve_potential(pf_ctx* ctx, pf_step_info* info);
 
 /* Reverse-mode (discrete adjoint) step of one forward-Euler TDGL + Poisson
