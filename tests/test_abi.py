@@ -40,15 +40,16 @@ def test_exports_every_declared_symbol(L):
 def test_struct_layout_matches_header(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pf.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(pf_params), sizeof(pf_step_info),'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pf_params), sizeof(pf_step_info),'
                     ' offsetof(pf_params, poisson_rtol), offsetof(pf_step_info, last_relres),'
-                    ' sizeof(pf_kernel_stat), offsetof(pf_kernel_stat, bytes));return 0;}\n')
+                    ' sizeof(pf_kernel_stat), offsetof(pf_kernel_stat, bytes), offsetof(pf_params, extrap_order));'
+                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert got == [C.sizeof(pf.pf_params), C.sizeof(pf.pf_step_info),
                    pf.pf_params.poisson_rtol.offset, pf.pf_step_info.last_relres.offset,
-                   C.sizeof(pf.pf_kernel_stat), pf.pf_kernel_stat.bytes.offset]
+                   C.sizeof(pf.pf_kernel_stat), pf.pf_kernel_stat.bytes.offset, pf.pf_params.extrap_order.offset]
 
 
 def good_params():
