@@ -39,10 +39,17 @@ class _Info(C.Structure):
                 ("last_relres", C.c_double), ("nonconverged", C.c_int)]
 
 
+_libs = {}
+_openmp = False
+
+
 def lib():
+    """The loaded oracle library: the serial build, or the OpenMP build of the
+    same source inside ``openmp()`` (timing baselines only)."""
     global _lib
-    if _lib is None:
-        path = _build.build()
+    key = "omp" if _openmp else "serial"
+    if key not in _libs:
+        path = _build.build(openmp=_openmp)
         L = C.CDLL(path)
         vp, d, i, l = C.c_void_p, C.c_double, C.c_int, C.c_long
         L.or_landau_energy.restype = d
@@ -64,8 +71,33 @@ def lib():
         L.or_energy.argtypes = [vp, vp, vp, d]
         L.or_adjoint_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.or_diagnostics.argtypes = [vp, vp, vp, vp, d, vp]
-        _lib = L
+        L.or_threads.restype = i
+        L.or_threads.argtypes = []
+        _libs[key] = L
+    _lib = _libs[key]
     return _lib
+
+
+class openmp:
+    """Context in which the oracle functions run the OpenMP build (all host
+    cores, OMP_NUM_THREADS permitting).  For timing baselines only: the
+    tests use the serial build."""
+
+    def __enter__(self):
+        global _openmp
+        self._prev = _openmp
+        _openmp = True
+        return self
+
+    def __exit__(self, *exc):
+        global _openmp
+        _openmp = self._prev
+        return False
+
+
+def threads() -> int:
+    """Threads the current build's loops run on (1 for the serial build)."""
+    return int(lib().or_threads())
 
 
 def _f64(a):

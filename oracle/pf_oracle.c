@@ -15,6 +15,14 @@
  *                         predictor-corrector ("velocity Verlet") scheme
  *   Section Numerical Performance: the Krylov solve is warm-started from the
  *                         previous step's potential
+ *
+ * Built twice from this one source: serially (liboracle.so, the reference
+ * the tests use) and with OpenMP (liboracle_omp.so, a timing baseline on all
+ * host cores).  The "omp parallel for" lines only split the z loops of the
+ * operators and the vector updates over threads; they change no arithmetic.
+ * The one difference is the dot product of the OpenMP build, which sums
+ * fixed chunks of cells and then the chunk sums in chunk order: the same
+ * result for any thread count, and the serial sum up to rounding order.
  */
 #include "pf_oracle.h"
 
@@ -82,6 +90,7 @@ static void landau_at(const double p[3], double a1, double a11, double a12, doub
 }
 
 void or_landau_force(const double* P, long n, double a1, double a11, double a12, double* out) {
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < n; ++c) {
     double p[3] = {P[c], P[n + c], P[2 * n + c]}, h[3];
     landau_at(p, a1, a11, a12, h);
@@ -129,6 +138,7 @@ static double laplacian_at(const or_grid* G, const double* f, int x, int y, int 
 }
 
 void or_laplacian(const or_grid* G, const double* f, double* out) {
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < G->nz; ++z)
     for (int y = 0; y < G->ny; ++y)
       for (int x = 0; x < G->nx; ++x) out[cell_index(G, x, y, z)] = laplacian_at(G, f, x, y, z);
@@ -148,6 +158,7 @@ static double eps_face(const or_grid* G, long c, long nb) {
 void or_rhs(const or_grid* G, const double* P, double* b) {
   long n = ncells(G);
   double ih = 1.0 / G->dx, ih2 = ih * ih;
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < G->nz; ++z)
     for (int y = 0; y < G->ny; ++y)
       for (int x = 0; x < G->nx; ++x) {
@@ -179,6 +190,7 @@ void or_rhs(const or_grid* G, const double* P, double* b) {
  * contributing nothing (Section Electrostatics Calculation, R4). */
 void or_apply(const or_grid* G, const double* phi, double* out) {
   double ih2 = 1.0 / (G->dx * G->dx);
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < G->nz; ++z)
     for (int y = 0; y < G->ny; ++y)
       for (int x = 0; x < G->nx; ++x) {
@@ -200,6 +212,7 @@ void or_apply(const or_grid* G, const double* phi, double* out) {
 
 void or_diag(const or_grid* G, double* dg) {
   double ih2 = 1.0 / (G->dx * G->dx);
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < G->nz; ++z)
     for (int y = 0; y < G->ny; ++y)
       for (int x = 0; x < G->nx; ++x) {
@@ -242,6 +255,7 @@ static void field_at(const or_grid* G, const double* phi, int x, int y, int z, d
 
 void or_field(const or_grid* G, const double* phi, double* E) {
   long n = ncells(G);
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < G->nz; ++z)
     for (int y = 0; y < G->ny; ++y)
       for (int x = 0; x < G->nx; ++x) {
@@ -259,11 +273,33 @@ int or_has_dirichlet(const or_grid* G) {
   return 0;
 }
 
+#ifdef _OPENMP
+#include <omp.h>
+#define OR_CHUNK 4096L
+static double dot(const double* a, const double* b, long n) {
+  long nc = (n + OR_CHUNK - 1) / OR_CHUNK;
+  double* part = (double*)malloc(sizeof(double) * (size_t)nc);
+#pragma omp parallel for schedule(static)
+  for (long k = 0; k < nc; ++k) {
+    long e = (k + 1) * OR_CHUNK < n ? (k + 1) * OR_CHUNK : n;
+    double s = 0.0;
+    for (long i = k * OR_CHUNK; i < e; ++i) s += a[i] * b[i];
+    part[k] = s;
+  }
+  double s = 0.0;
+  for (long k = 0; k < nc; ++k) s += part[k];
+  free(part);
+  return s;
+}
+int or_threads(void) { return omp_get_max_threads(); }
+#else
 static double dot(const double* a, const double* b, long n) {
   double s = 0.0;
   for (long i = 0; i < n; ++i) s += a[i] * b[i];
   return s;
 }
+int or_threads(void) { return 1; }
+#endif
 
 static double mean(const double* a, long n) {
   double s = 0.0;
@@ -298,10 +334,13 @@ int or_solve(const or_grid* G, const double* b_in, double* phi, double rtol, int
     goto done;
   }
   or_apply(G, phi, q);
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < n; ++i) r[i] = b[i] - q[i];
   rel = sqrt(dot(r, r, n)) / bnorm;
   if (rel < rtol) goto finish;
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < n; ++i) z[i] = r[i] / dg[i];
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < n; ++i) p[i] = z[i];
   double rz = dot(r, z, n);
   status = OR_NOCONV;
@@ -310,17 +349,21 @@ int or_solve(const or_grid* G, const double* b_in, double* phi, double rtol, int
     double pq = dot(p, q, n);
     if (!(pq > 0.0)) break;                 /* breakdown: keep the current iterate */
     double alpha = rz / pq;
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < n; ++i) phi[i] += alpha * p[i];
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < n; ++i) r[i] -= alpha * q[i];
     rel = sqrt(dot(r, r, n)) / bnorm;
     if (rel < rtol) {
       status = OR_OK;
       break;
     }
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < n; ++i) z[i] = r[i] / dg[i];
     double rz_new = dot(r, z, n);
     double beta = rz_new / rz;
     rz = rz_new;
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
   }
   if (k > maxit) k = maxit;
@@ -375,6 +418,7 @@ int or_step(const or_grid* G, const or_params* prm, double* P, double* phi, int 
     or_field(G, phi, E);
     or_landau_force(P, n, prm->a1, prm->a11, prm->a12, h);
     for (int c = 0; c < 3; ++c) or_laplacian(G, P + (long)c * n, lap + (long)c * n);
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < 3 * n; ++i)
       P[i] = P[i] + prm->dt * prm->L * (-h[i] + prm->g * lap[i] + E[i]);
     zero_air(G, P);

@@ -162,6 +162,10 @@ int or_adjoint_step(const or_grid* G, const or_params* prm, const double* P, con
 void or_diagnostics(const or_grid* G, const or_params* prm, const double* P, const double* phi,
                     double threshold, double* out);
 
+/* Threads the oracle's loops run on: 1 for the serial build, the OpenMP
+ * thread count for the OpenMP build. */
+int or_threads(void);
+
 #ifdef __cplusplus
 }
 #endif
