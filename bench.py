@@ -14,6 +14,7 @@ cell-steps / max over ranks of the timed device time ("scaling": "weak").
 from __future__ import annotations
 
 import argparse
+import contextlib
 import hashlib
 import json
 import os
@@ -249,7 +250,9 @@ def run_ours(args):
         film.set_noise(args.noise, 12345)
     stream = film.stream
     flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    flush = "flushed (a %d MiB buffer is written between timed steps)" % (2 * L2_BYTES // 2 ** 20)
+    state_gb = (4 * w.n * (4 if w.precision == "fp32" else 8) + film.ws_bytes) / 1e9
+    flush = ("inputs larger than L2: every step streams the film's fields (%.2f GB of state and workspace, "
+             "L2 %d MiB)" % (state_gb, L2_BYTES // 2 ** 20))
 
     def barrier():
         if world > 1:
@@ -259,25 +262,22 @@ def run_ours(args):
     for _ in range(args.warmup):
         film.step(1)
     clocks = ClockSampler(local)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    launches = 0
-    iters = 0
-    graph_steps = 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     clocks.start()
     time.sleep(0.3)
-    for k in range(args.steps):
-        flush_buf.zero_()
-        starts[k].record(stream)
-        st, info = film.step(1)
-        ends[k].record(stream)
-        launches += info["kernel_launches"]
-        iters += info["total_iters"]
-        graph_steps += info["graph_steps"]
+    # the K steps go out as one asynchronous call: one CUDA graph per step,
+    # no host round trip between steps, the statistics read once at the end
+    e0.record(stream)
+    film.step_async(args.steps)
+    e1.record(stream)
+    st, info = film.wait()
     barrier()
     clk = clocks.stop()
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    launches = info["kernel_launches"]
+    iters = info["total_iters"]
+    graph_steps = info["graph_steps"]
+    ms = e0.elapsed_time(e1)
     ms_max, value = replica_throughput(ms, w.n * args.steps, world, dev)
 
     # per-kernel device times: a second pass of the same steps with the
@@ -338,8 +338,11 @@ def run_ours(args):
     cpu = None
     film.close()
     prec = None
+    full = None
     if rank == 0 and world == 1 and args.precision_steps > 3:
         prec = precision_check(dev, args.precision_steps)
+    if rank == 0 and world == 1 and args.full_steps > 2 and args.workload == "tip" and args.size is None:
+        full = full_run(dev, w, args.full_steps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, args.cpu_seconds)
     if rank == 0:
@@ -349,9 +352,10 @@ def run_ours(args):
                 "data": "synthetic (seeded SplitMix64 initial state, electrode masks of the workload)",
                 "config": workload_config(w, args.workload, flush, args),
                 "poisson_iters_per_step": iters / args.steps,
+                "max_poisson_iters": info["max_iters"],
                 "graph_steps": graph_steps,
                 "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
-                "clocks": clk, "fp32_vs_fp64": prec, "impl": "ours"}
+                "clocks": clk, "fp32_vs_fp64": prec, "full_run": full, "impl": "ours"}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -514,36 +518,125 @@ def run_adjoint(args):
 
 # -------------------------------------------------------- FP32 against FP64
 
-def precision_check(dev, steps):
-    """The strip-electrode film (256x256x64, MG-PCG to 1e-8) advanced in FP32
-    (FP64 reductions) and in plain FP64 on this GPU: time per step of each,
-    the FP32 error on P (max |P32 - P64| / max |P64| per component) and the
-    switched-domain fraction (P_x > 0.3) of both."""
+def precision_check(dev, steps, chunk=1000):
+    """The strip-electrode film (256x256x64, MG-PCG to 1e-8) advanced for
+    the whole run in FP32 (the compensated state, the default), in plain
+    FP32 and in FP64 on this GPU, side by side in chunks: time per step of
+    each, the FP32 errors on P against FP64 after every chunk (max |P32 -
+    P64| / max |P64| per component, the maximum over components; the
+    relative 2-norm error; the cells off by more than 1e-4), the
+    switched-domain fraction (P_x > 0.3) of each, and the true FP64 residual
+    of each run's last potential."""
     import torch
+    from paper_1202_6116_gb300 import pf
     from paper_1202_6116_gb300 import workloads as W
     from paper_1202_6116_gb300.film import Film
-    out = {"workload": "strips 256x256x64 MG-PCG rtol=1e-08 dt=0.01, %d steps from the seeded state" % steps}
-    finals = {}
-    for prec in ("fp32", "fp64"):
+    out = {"workload": "strips 256x256x64 MG-PCG rtol=1e-08 dt=0.01, %d steps from the seeded state" % steps,
+           "error_metric": "max |P32 - P64| / max |P64| per component (the maximum over components)"}
+    forms = (("fp32", "fp32", 0), ("fp32_plain", "fp32", pf.PF_FLAG_PLAIN_FP32), ("fp64", "fp64", 0))
+    films, ms, its, solves, worst = {}, {}, {}, {}, {}
+    for key, prec, flags in forms:
         w = W.film_strip_fp32().with_(precision=prec, solver="mg", maxit=500)
-        f = Film(w, device=dev)
-        f.step(3)                                  # graph capture and warm-up, excluded
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(f.stream)
-        _, info = f.step(steps - 3)
-        e1.record(f.stream)
-        e1.synchronize()
+        films[key] = Film(w, device=dev, flags=flags)
+        films[key].step(3)                         # graph captures and warm-up, excluded from the timing
+        ms[key], its[key], solves[key], worst[key] = 0.0, 0, 0, 0
+    done = 3
+    timeline = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    while done < steps - 1:
+        n = min(chunk - done % chunk, steps - 1 - done)
+        for key, f in films.items():
+            torch.cuda.synchronize(dev)
+            e0.record(f.stream)
+            f.step_async(n)
+            e1.record(f.stream)
+            _, info = f.wait()
+            ms[key] += e0.elapsed_time(e1)
+            its[key] += info["total_iters"]
+            solves[key] += info["solves"]
+            worst[key] = max(worst[key], info["max_iters"])
+        done += n
+        if done % chunk == 0 or done == steps - 1:
+            b = films["fp64"].P
+            row = {"step": done}
+            for key in ("fp32", "fp32_plain"):
+                a = films[key].P.double()
+                row[key] = max(float((a[c] - b[c]).abs().max() / b[c].abs().max()) for c in range(3))
+            timeline.append(row)
+    finals = {}
+    for key, f in films.items():
+        Pprev = f.P.clone()
+        f.step(1)                                  # the last step: its potential belongs to Pprev
+        res, bn, resc = f.true_residual(Pprev)
         d = f.diagnostics(0.3)
-        finals[prec] = f.P.double()
-        out[prec + "_ms_per_step"] = round(e0.elapsed_time(e1) / (steps - 3), 4)
-        out[prec + "_poisson_iters_per_step"] = round(info["total_iters"] / (steps - 3), 2)
-        out[prec + "_switched_fraction"] = d["switched_fraction"]
+        finals[key] = f.P.double()
+        out[key + "_ms_per_step"] = round(ms[key] / (steps - 4), 4)
+        out[key + "_poisson_iters_per_step"] = round(its[key] / max(1, solves[key]), 3)
+        out[key + "_max_poisson_iters"] = worst[key]
+        out[key + "_switched_fraction"] = d["switched_fraction"]
+        out[key + "_true_relres_last_solve"] = res / bn if bn > 0 else 0.0
+        out[key + "_true_relres_last_solve_compensated"] = resc / bn if bn > 0 else 0.0
         f.close()
-    a, b = finals["fp32"], finals["fp64"]
-    out["max_rel_err_P"] = max(float((a[c] - b[c]).abs().max() / b[c].abs().max()) for c in range(3))
-    out["switched_diff_pp"] = 100.0 * abs(out["fp32_switched_fraction"] - out["fp64_switched_fraction"])
+        del Pprev
+    b = finals["fp64"]
+    for key in ("fp32", "fp32_plain"):
+        a = finals[key]
+        out[key + "_max_rel_err_P"] = max(float((a[c] - b[c]).abs().max() / b[c].abs().max()) for c in range(3))
+        out[key + "_rel_l2_err_P"] = float((a - b).norm() / b.norm())
+        out[key + "_cells_off_by_1e-4"] = int(((a - b).abs() > 1e-4).sum())
+        out[key + "_switched_diff_pp"] = 100.0 * abs(out[key + "_switched_fraction"] - out["fp64_switched_fraction"])
+        out[key + "_peak_max_rel_err_P"] = max([r[key] for r in timeline] + [out[key + "_max_rel_err_P"]])
+    out["timeline"] = timeline
+    out["max_rel_err_P"] = out["fp32_max_rel_err_P"]
+    out["switched_diff_pp"] = out["fp32_switched_diff_pp"]
     out["fp32_speedup"] = round(out["fp64_ms_per_step"] / out["fp32_ms_per_step"], 3)
+    out["meets_stated_error"] = bool(out["fp32_peak_max_rel_err_P"] <= 1e-4 and out["switched_diff_pp"] <= 0.1)
+    return out
+
+
+def full_run(dev, w, steps):
+    """One whole run of the bench film from its seeded state (untimed in the
+    headline): Poisson iterations per step over all of it, device time per
+    step, and the true FP64 relative residual ||b - A phi|| / ||b|| of the
+    last solve (phi as stored, P the state it was solved for)."""
+    import torch
+    from paper_1202_6116_gb300.film import Film
+    f = Film(w, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f.step(2)                                      # graph captures
+    pairs = (steps - 4) // 2
+    total, solves, worst, nonconv = 0, 0, 0, 0
+    torch.cuda.synchronize(dev)
+    ms = 0.0
+    for _ in range(pairs):                         # two steps per call: the state ends in the bound buffer
+        e0.record(f.stream)
+        f.step_async(2)
+        e1.record(f.stream)
+        _, info = f.wait()
+        ms += e0.elapsed_time(e1)
+        total += info["total_iters"]
+        solves += info["solves"]
+        worst = max(worst, info["max_iters"])
+        nonconv += info["nonconverged"]
+    done = 2 + 2 * pairs
+    while done < steps - 1:
+        _, info = f.step(1)
+        total, solves, worst, done = total + info["total_iters"], solves + info["solves"], \
+            max(worst, info["max_iters"]), done + 1
+    Pprev = f.P.clone()
+    _, info = f.step(1)
+    total, solves, worst = total + info["total_iters"], solves + info["solves"], max(worst, info["max_iters"])
+    res, bn, resc = f.true_residual(Pprev)
+    d = f.diagnostics(0.3)
+    out = {"workload": "%s, %d steps from the seeded state" % (w.name, steps),
+           "steps": steps, "poisson_iters_per_step_mean": round(total / max(1, solves), 3),
+           "poisson_iters_per_step_max": worst, "nonconverged": nonconv,
+           "ms_per_step_steps_3_to_%d" % (2 + 2 * pairs): round(ms / (2 * pairs), 4),
+           "last_solve_recursive_relres": info["last_relres"],
+           "last_solve_true_relres_fp64": {"stored_fp32_phi": res / bn if bn > 0 else 0.0,
+                                           "compensated_phi": resc / bn if bn > 0 else 0.0},
+           "mean_P": [d["mean_px"], d["mean_py"], d["mean_pz"]], "switched_fraction": d["switched_fraction"]}
+    f.close()
     return out
 
 
@@ -559,41 +652,126 @@ def oracle_timed(w, warm, steps):
     return time.perf_counter() - t0, info
 
 
-def cpu_baseline(name, budget_s):
-    """The FP64 oracle as it stands, serial, on a bounded sample of the workload."""
+def host_cpu():
+    """Core count and CPU model of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "model": model or "unknown", "arch": platform.machine()}
+
+
+def sample_desc(w, desc):
+    return "%s (%dx%dx%d, FP64, Jacobi-PCG rtol=%g, dt=%g)" % (desc, w.nx, w.ny, w.nz, w.rtol, w.dt)
+
+
+def oracle_rate(name, budget_s, openmp):
+    """cell-steps/s of the FP64 oracle on the bounded sample: steps sized to
+    about budget_s seconds of CPU work after 2 warm-up steps."""
+    import oracle as O
     import oracle.build
-    oracle.build.build()
     w, desc = sample_workload(name)
-    dt1, _ = oracle_timed(w, 2, 1)
-    steps = max(1, min(50, int(budget_s / max(dt1, 1e-3))))
-    secs, info = oracle_timed(w, 2, steps)
-    return {"value": w.n * steps / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%s, FP64, %d timed steps after 3 warm-up steps (%.1f s, %d CG iterations)" %
-                      (desc, steps, secs, info["total_iters"])}
+    ctx = O.openmp() if openmp else contextlib.nullcontext()
+    with ctx:
+        oracle.build.build(openmp=openmp)
+        dt1, _ = oracle_timed(w, 2, 1)
+        steps = max(1, min(200, int(budget_s / max(dt1, 1e-3))))
+        secs, info = oracle_timed(w, 2, steps)
+        cores = O.threads()
+    return {"value": w.n * steps / secs, "unit": UNIT, "cores": cores,
+            "kind": "oracle" + (" (OpenMP build)" if openmp else ""),
+            "cflags": " ".join(oracle.build.flags(openmp)),
+            "sample": "%s, %d timed steps after 2 warm-up steps (%.1f s, %d CG iterations)" %
+                      (sample_desc(w, desc), steps, secs, info["total_iters"])}
+
+
+def cpu_baseline(name, budget_s):
+    """The FP64 oracle as it stands on a bounded sample of the workload: the
+    serial build on one core, and the same source built with OpenMP on all
+    of this host's cores."""
+    base = oracle_rate(name, budget_s, openmp=False)
+    base["host"] = host_cpu()
+    base["all_cores"] = oracle_rate(name, budget_s, openmp=True)
+    return base
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the OpenMP build of the same
+    source, on all host cores) on a bounded sample of the workload."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
+    import oracle as O
     import oracle.build
-    oracle.build.build()
     w, desc = sample_workload(args.workload)
-    secs, info = oracle_timed(w, args.warmup, args.steps)
+    with O.openmp():
+        oracle.build.build(openmp=True)
+        secs, info = oracle_timed(w, args.warmup, args.steps)
+        cores = O.threads()
     value = w.n * args.steps / secs
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 initial state, electrode masks of the workload)",
-            "config": workload_config(make_workload(args.workload, solver=args.solver, size=args.size), args.workload,
-                                      "n/a (CPU)"),
+            "config": {"workload": "%s %dx%dx%d fp64 Jacobi-PCG rtol=%g dt=%g (CPU oracle sample of the %s film)"
+                                   % (args.workload, w.nx, w.ny, w.nz, w.rtol, w.dt, args.workload),
+                       "cells": w.n, "precision": "fp64", "solver": "pcg", "poisson_rtol": w.rtol, "dt": w.dt,
+                       "l2": "n/a (CPU)", "cores": cores},
             "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%s, FP64 serial oracle, %d steps after %d warm-up steps" %
-                                       (desc, args.steps, args.warmup)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle (OpenMP build)",
+                             "cflags": " ".join(oracle.build.flags(True)), "host": host_cpu(),
+                             "sample": "%s, %d steps after %d warm-up steps, %d CG iterations" %
+                                       (sample_desc(w, desc), args.steps, args.warmup, info["total_iters"])},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+# -------------------------------------------------- replica launch (N > 1)
+
+def launch_replicas(args, argv):
+    """Start N ranks of this script (one per GPU) with torch's launcher when
+    --gpus N > 1 is asked for without one; rank 0 prints the line."""
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=%d" % args.gpus,
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + argv
+    return subprocess.call(cmd)
+
+
+def run_replica_selftest(args):
+    """The multi-rank path of the bench without a GPU (gloo): every rank
+    reports a fixed local time (10 ms x (rank + 1)) for a fixed amount of
+    work, and rank 0 prints the whole-job line the GPU run would print."""
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        dist.init_process_group("gloo")
+    cells, steps = 1000, args.steps
+    ms_local = 10.0 * (rank + 1)
+    ms_max, value = replica_throughput(ms_local, cells * steps, world)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+                          "ms_per_step": ms_max / steps, "scaling": "weak", "impl": "selftest"}))
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def main():
@@ -610,9 +788,13 @@ def main():
     ap.add_argument("--size", type=lambda v: tuple(int(x) for x in v.lower().split("x")), default=None,
                     help="NXxNYxNZ: the workload's recipe on another grid (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--precision-steps", type=int, default=200,
+    ap.add_argument("--precision-steps", type=int, default=5000,
                     help="steps of the FP32-against-FP64 comparison on the strip film (0: skip)")
+    ap.add_argument("--full-steps", type=int, default=1000,
+                    help="steps of the untimed whole run of the tip film (iterations per step, true residual; 0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--replica-selftest", action="store_true",
+                    help="exercise the multi-rank launch and reduction on CPU (gloo), no GPU work")
     ap.add_argument("--films", type=int, default=64, help="films of the batch workload")
     ap.add_argument("--integrator", choices=("euler", "heun"), default="euler",
                     help="forward Euler or the paper's predictor-corrector")
@@ -627,7 +809,12 @@ def main():
                     help="launch every kernel from the host (profilers cannot see kernels inside CUDA graphs "
                          "with conditional nodes)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(launch_replicas(args, sys.argv[1:]))
+    if args.replica_selftest:
+        args.steps = 10 if args.steps is None else args.steps
+        run_replica_selftest(args)
+    elif args.impl == "reference":
         args.steps = 5 if args.steps is None else args.steps
         args.warmup = 3 if args.warmup is None else args.warmup
         run_reference(args)

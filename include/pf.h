@@ -13,8 +13,10 @@
  * div P (Eqs. rho, Poisson) with periodic x/y and per-cell Dirichlet
  * (electrode) or Neumann (open surface) z faces (Section Electrostatics
  * Calculation).  Time stepping is explicit forward Euler (Section Time
- * Integration); each Poisson solve is warm-started from the previous
- * potential (Section Numerical Performance).  The paper's finite-element
+ * Integration) or the paper's predictor-corrector.  Each Poisson solve is
+ * warm-started (Section Numerical Performance): by default from a polynomial
+ * extrapolation of the last potentials, with PF_FLAG_WARM_LAST from the last
+ * potential as in the paper.  The paper's finite-element
  * elastic solve is not part of this library: a fixed homogeneous misfit
  * strain is assumed folded into a1, a11, a12.
  *
@@ -28,8 +30,13 @@
  * Memory: every device buffer is owned by the caller (for example torch
  * tensors).  The library allocates no device memory and keeps only a small
  * pinned host mirror of its solver scalars.  All calls are issued on the CUDA
- * stream given to pf_create.  Calls return a pf_status and never abort; the
- * message of the last failure is available from pf_last_error.
+ * stream given to pf_create.  pf_step_async returns without waiting (when the
+ * steps run as CUDA graphs, the default); the other calls that report solver
+ * results (pf_step, pf_step_wait, pf_solve_potential, pf_adjoint_step,
+ * pf_diagnostics, pf_true_residual) wait for their work, because the
+ * statistics they return live on the device.  Calls return a pf_status and
+ * never abort; the message of the last failure is available from
+ * pf_last_error.
  */
 #ifndef PF_H
 #define PF_H
@@ -129,8 +136,22 @@ typedef struct {
  *                      extrapolates from that compensated potential: without
  *                      it the rounding of phi alone would leave a start
  *                      residual above a 1e-7 tolerance on large films.  phi
- *                      is still the solution rounded to FP32. */
-enum { PF_FLAG_NO_GRAPHS = 1, PF_FLAG_ADJOINT = 2, PF_FLAG_WARM_LAST = 4 };
+ *                      is still the solution rounded to FP32.
+ *   PF_FLAG_PLAIN_FP32 store the FP32 polarization state plainly.  Without it,
+ *                      FP32 forward-Euler contexts (not created with
+ *                      PF_FLAG_ADJOINT) keep the state as the compensated
+ *                      pair P + P_lo: P_lo (3N more FP32 values of workspace)
+ *                      holds the part of each updated value that the FP32 P
+ *                      cannot hold, and every step adds its increment to the
+ *                      pair exactly (TwoSum).  Plain FP32 loses the
+ *                      increments that fall below half an ulp of P, which near
+ *                      equilibrium is most of them: on the 256 x 256 x 64
+ *                      strip film the plain state drifts to a relative error
+ *                      of 4e-4 against FP64 in 5000 steps.  The driving force
+ *                      is still evaluated in FP32 from P; P is what the
+ *                      caller reads.  pf_bind zeroes P_lo; a caller that
+ *                      overwrites P between calls should bind again. */
+enum { PF_FLAG_NO_GRAPHS = 1, PF_FLAG_ADJOINT = 2, PF_FLAG_WARM_LAST = 4, PF_FLAG_PLAIN_FP32 = 8 };
 
 typedef struct {
   int32_t steps_done;        /* steps completed by this call */
@@ -145,6 +166,8 @@ typedef struct {
                                 device-driven Krylov loop, no host round trip);
                                 the others ran host-driven (profiling on, or
                                 graphs unavailable) */
+  int32_t max_iters;         /* most Poisson iterations of one solve in this call */
+  int32_t solves;            /* Poisson solves finished in this call */
 } pf_step_info;
 
 /* Per-kernel device-time statistics collected while profiling is on (see
@@ -199,17 +222,35 @@ pf_status pf_set_bc(pf_ctx* ctx, int32_t face, const int8_t* type_xy, const doub
  *   P <- P - dt L (df/dP - g Lap P - E),  E = -grad phi.
  * On return P = P_nsteps and phi is the last potential solved: with Euler
  * and poisson_every <= 1 the potential of P_{nsteps-1}, with Heun that of the
- * last predicted state.  Blocks
- * the host until the work is done.  A solve that hits poisson_maxit does not
- * stop the run: the step completes with the unconverged potential and the
- * call returns PF_ERR_NOCONV with info->nonconverged counting such solves.
- * info may be NULL. */
+ * last predicted state.  pf_step is pf_step_async followed by pf_step_wait:
+ * it blocks the host until the work is done, because info (iterations,
+ * residuals, non-convergence) is read back from the device.  A solve that
+ * hits poisson_maxit does not stop the run: the step completes with the
+ * unconverged potential and the call returns PF_ERR_NOCONV with
+ * info->nonconverged counting such solves.  info may be NULL. */
 pf_status pf_step(pf_ctx* ctx, int32_t nsteps, pf_step_info* info);
 
+/* Enqueue nsteps steps on the context's stream and return.  When the steps
+ * run as CUDA graphs (the default: no PF_FLAG_NO_GRAPHS, profiling off) the
+ * host does not wait: each step's Krylov loop is driven from the device.
+ * Host-driven steps poll the convergence flag and so block while issuing.
+ * Calls accumulate: their solver statistics stay on the device until
+ * pf_step_wait.  Until then the other entry points of this context (except
+ * pf_step, which joins the pending work) return PF_ERR_STATE.  P and phi hold
+ * the state of the last enqueued step once the stream reaches that point. */
+pf_status pf_step_async(pf_ctx* ctx, int32_t nsteps);
+
+/* Wait for the work of the pf_step_async calls since the last wait, and
+ * report it in info (may be NULL) as pf_step does; returns the status
+ * pf_step would have returned for all those steps. */
+pf_status pf_step_wait(pf_ctx* ctx, pf_step_info* info);
+
 /* Same as pf_step but P and phi live in host memory: both are copied to the
- * bound device buffers before every step and copied back after it (pinned
- * host memory makes the copies asynchronous).  This is the end-to-end entry
- * for callers that keep the state on the host. */
+ * device before every step and copied back after it (pinned host memory
+ * makes the copies asynchronous).  This is the end-to-end entry for callers
+ * that keep the state on the host.  The solver history (the extrapolation
+ * ring and, in FP32, the compensated remainders of phi and P) stays in the
+ * device workspace between steps. */
 pf_status pf_step_host(pf_ctx* ctx, void* P_host, void* phi_host, int32_t nsteps,
                        pf_step_info* info);
 
@@ -263,6 +304,21 @@ pf_status pf_adjoint_step(pf_ctx* ctx, const void* lam_in, void* lam_out, double
  * step descends.  Sums are reduced in a fixed order (reproducible). */
 pf_status pf_diagnostics(pf_ctx* ctx, double threshold, double* out);
 
+/* True residual of the stored potential: out[0] = ||b(P) - A phi||_2,
+ * out[1] = ||b(P)||_2 and out[2] = ||b(P) - A phi_c||_2 (host, 3 doubles),
+ * every operation in FP64 whatever the storage precision, for the bound phi
+ * and the current face voltages (Eqs. rho and Poisson with the face rules
+ * above; b projected to zero mean when no electrode exists).  The solver
+ * stops on its recursive residual; out[0] is the residual of the potential
+ * as stored (in FP32 mode, after rounding to FP32).  phi_c is the
+ * compensated potential of an FP32 time series after a pf_step (phi plus the
+ * remainder the FP32 phi cannot hold, see PF_FLAG_WARM_LAST): the solution
+ * the Krylov loop converged.  Without one, out[2] = out[0].  P: device, 3N
+ * values of the context precision, or NULL for the bound state (the
+ * potential after pf_step belongs to the state before the last update, so
+ * pass that state to check the last solve).  Blocks. */
+pf_status pf_true_residual(pf_ctx* ctx, const void* P, double* out);
+
 /* Turn per-kernel timing on (1) or off (0); turning it on clears the
  * counters.  While on, every launch is bracketed by CUDA events on the
  * context's stream (no extra synchronisation: the events are read at the
@@ -277,9 +333,11 @@ int32_t pf_profile_read(const pf_ctx* ctx, pf_kernel_stat* out, int32_t max);
 #define PF_NOALLOC_SCRATCH_BYTES (32u << 20)
 
 /* The Poisson solve of pf_solve_potential for callers that cannot allocate
- * device memory (code running inside CUDA-graph capture or replay, real-time
- * loops that must not touch an allocator, processes with a fixed memory
- * pool).  The paper has no counterpart: it is a deployment variant.
+ * device memory: real-time loops that must not stall on the allocator
+ * (cudaMalloc and cudaFree can synchronize the whole device), and processes
+ * whose device memory is reserved up front by another allocator (a fixed
+ * pool, or a framework that owns every byte).  The paper has no counterpart:
+ * it is a deployment variant.
  *   - No context and no workspace: every intermediate vector lives in one
  *     file-scope __device__ array of PF_NOALLOC_SCRATCH_BYTES (32 MiB) that
  *     every GPU loading the library keeps until the process exits; the call
@@ -288,14 +346,18 @@ int32_t pf_profile_read(const pf_ctx* ctx, pf_kernel_stat* out, int32_t max);
  *     800k cells in FP64, 1.6M in FP32) are rejected with PF_ERR_ARG.
  *   - params as for pf_create, restricted to solver = PF_PCG_JACOBI and
  *     has_eps = 0.  P (3N, input) and phi (N: initial guess in, potential out)
- *     are device pointers of the current device, 16-byte aligned, in the
- *     precision of params.  type_lo/type_hi (nx*ny int8, PF_NEUMANN or
- *     PF_DIRICHLET) and volt_lo/volt_hi (nx*ny double) are host arrays as in
- *     pf_set_bc; NULL means open face / 0 V.
- *   - Blocks until the solve is done; info as for pf_solve_potential.  On
+ *     are device (or managed) pointers of the current device, 16-byte
+ *     aligned, in the precision of params; other pointers give PF_ERR_ARG.
+ *     type_lo/type_hi (nx*ny int8, PF_NEUMANN or PF_DIRICHLET) and
+ *     volt_lo/volt_hi (nx*ny double) are host arrays as in pf_set_bc; NULL
+ *     means open face / 0 V.
+ *   - Blocks until the solve is done (it polls the convergence flag and
+ *     reads the solver scalars back); info as for pf_solve_potential.  So it
+ *     must not be called while its stream, or the legacy stream, is being
+ *     captured into a CUDA graph: it checks and returns PF_ERR_STATE.  On
  *     failure pf_last_error(NULL) holds the message.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call looks up the array's device address in the current device's
+ *     context (cudaGetSymbolAddress, which allocates nothing).
  *   - Every call on a device shares the array: calls that overlap on the GPU
  *     (other streams, other host threads) race.  The array keeps the last
  *     call's contents; each call rewrites what it reads. */

@@ -40,6 +40,7 @@ struct MgLevelHost {
   int fx, fy, fz;
   double ax, ay, az;
   size_t f, e, et, tlo, thi;
+  size_t eps = 0, invd = 0;       // coarse levels with a permittivity field: eps and 1/diag
   pf::MarchCfg mc;
   long long n() const { return (long long)nx * ny * nz; }
   long long nxy() const { return (long long)nx * ny; }
@@ -75,7 +76,7 @@ std::vector<MgLevelHost> mg_levels(const pf_params* p) {
 }
 
 struct Layout {
-  size_t P_alt, r, p0, p1, q, invd, hist[3], clo, cx, tlo, thi, vlo, vhi, ctr, xctr, part, S, diag, z, zt, total;
+  size_t P_alt, plo, r, p0, p1, q, invd, hist[3], clo, cx, tlo, thi, vlo, vhi, ctr, xctr, part, S, diag, z, zt, total;
   bool adj = false;               // psi and vzero exist (PF_FLAG_ADJOINT)
   size_t psi = 0, vzero = 0;      // adjoint potential; zero face voltages
   std::vector<MgLevelHost> mg;
@@ -97,7 +98,6 @@ bool params_valid(const pf_params* p, std::string* why) {
   if (p->periodic_z != 0 && p->periodic_z != 1) return fail("periodic_z must be 0 or 1");
   if (p->has_eps != 0 && p->has_eps != 1) return fail("has_eps must be 0 or 1");
   if (p->solver == PF_PCG_MG) {
-    if (p->has_eps) return fail("the multigrid preconditioner needs eps = 1 (has_eps = 0)");
     std::vector<MgLevelHost> L = mg_levels(p);
     if (L.size() < 2) return fail("multigrid needs at least one even grid dimension");
     if (L.back().n() > pf::MG_MAX_COARSE)
@@ -106,7 +106,8 @@ bool params_valid(const pf_params* p, std::string* why) {
   }
   for (double v : {p->a1, p->a11, p->a12, p->g, p->L, p->dt})
     if (!std::isfinite(v)) return fail("coefficients must be finite");
-  if (p->flags & ~(PF_FLAG_NO_GRAPHS | PF_FLAG_ADJOINT | PF_FLAG_WARM_LAST)) return fail("unknown bits in flags");
+  if (p->flags & ~(PF_FLAG_NO_GRAPHS | PF_FLAG_ADJOINT | PF_FLAG_WARM_LAST | PF_FLAG_PLAIN_FP32))
+    return fail("unknown bits in flags");
   if (p->integrator != PF_EULER && p->integrator != PF_HEUN) return fail("integrator must be PF_EULER or PF_HEUN");
   if (p->poisson_every < 0) return fail("poisson_every must be >= 0");
   if (p->n_air < 0 || p->n_air >= p->nz) return fail("n_air must be in 0 .. nz - 1");
@@ -127,6 +128,15 @@ bool extrapolates(const pf_params* p) {
 // problem is singular (all-periodic: its mean removal acts on phi alone).
 bool comp_buffers(const pf_params* p) { return extrapolates(p) && p->precision == PF_FP32; }
 
+// Is the FP32 polarization state kept compensated (P plus an FP32 remainder,
+// see k_tdgl)?  FP32 forward Euler, unless PF_FLAG_PLAIN_FP32 asks for the
+// plain state or the context serves the adjoint (whose recomputed segments
+// restart from stored states and must repeat the forward pass bit for bit).
+bool comp_state(const pf_params* p) {
+  return p->precision == PF_FP32 && p->integrator == PF_EULER &&
+         !(p->flags & (PF_FLAG_PLAIN_FP32 | PF_FLAG_ADJOINT));
+}
+
 Layout layout_of(const pf_params* p) {
   const size_t w = p->precision == PF_FP32 ? 4 : 8;
   const size_t n = (size_t)p->nx * p->ny * p->nz, nxy = (size_t)p->nx * p->ny;
@@ -138,6 +148,7 @@ Layout layout_of(const pf_params* p) {
     return o;
   };
   L.P_alt = take(3 * n * w);
+  L.plo = take(comp_state(p) ? 3 * n * w : 0);
   L.r = take(n * w);
   L.p0 = take(n * w);
   L.p1 = take(n * w);
@@ -183,6 +194,10 @@ Layout layout_of(const pf_params* p) {
         l.et = take((size_t)l.n() * w);
         l.tlo = take((size_t)l.nxy());
         l.thi = take((size_t)l.nxy());
+        if (p->has_eps) {
+          l.eps = take((size_t)l.n() * w);
+          l.invd = take((size_t)l.n() * w);
+        }
       }
     }
   }
@@ -237,6 +252,8 @@ struct pf_ctx {
   unsigned long long noise_seed = 0;
   int tile_bps = 0;               // blocks per SM requested by pf_set_tiling (0: as many as fit)
   cudaStream_t cap_stream = nullptr;
+  bool async_open = false;        // pf_step_async work enqueued since the last pf_step_wait
+  int64_t async_steps = 0;        // steps of that work
 
   // Profiling: events recorded between consecutive launches; each record
   // says which kernel family ran in the interval and what it moved.
@@ -372,6 +389,7 @@ pf::Dev<T> dev_view(pf_ctx* ctx) {
   d.bc.vhi = (const T*)(ws + L.vhi);
   d.part = (double*)(ws + L.part);
   d.S = (Scalars*)(ws + L.S);
+  d.plo = comp_state(&ctx->prm) ? (T*)(ws + L.plo) : nullptr;
   return d;
 }
 
@@ -407,8 +425,34 @@ pf::MgView<T> mg_view(pf_ctx* ctx, size_t k) {
   v.f = (T*)(ctx->ws + l.f);
   v.e = (T*)(ctx->ws + l.e);
   v.et = (T*)(ctx->ws + l.et);
+  v.eps = nullptr;
+  v.invd = nullptr;
+  if (ctx->prm.has_eps) {
+    v.eps = k == 0 ? (const T*)ctx->eps : (const T*)(ctx->ws + l.eps);
+    v.invd = (const T*)(ctx->ws + (k == 0 ? ctx->lay.invd : l.invd));
+  }
   v.mc = l.mc;
   return v;
+}
+
+// 1/diag(A) of the fine operator when a permittivity field is bound and, for
+// the multigrid preconditioner, every coarse level's permittivity and 1/diag
+// (after a bind or an electrode change).
+template <typename T>
+void refresh_invd(pf_ctx* ctx, const pf::LaunchCfg& L, bool count) {
+  if (!ctx->prm.has_eps || !ctx->invd_dirty) return;
+  const double N = (double)ctx->geo.n, w = sizeof(T);
+  if (count) before_launch(ctx);
+  pf::launch_invdiag<T>(L, ctx->geo, dev_view<T>(ctx));
+  if (count) after_launch(ctx, F_INVDIAG, 2 * N * w);
+  else ctx->launches += 1;
+  for (size_t k = 1; k < ctx->lay.mg.size(); ++k) {
+    const MgLevelHost& l = ctx->lay.mg[k];
+    pf::launch_mg_eps_level<T>(L, mg_view<T>(ctx, k - 1), mg_view<T>(ctx, k), (T*)(ctx->ws + l.eps),
+                               (T*)(ctx->ws + l.invd));
+    ctx->launches += 2;
+  }
+  ctx->invd_dirty = false;
 }
 
 // First level of the one-block V-cycle tail: the first level after the
@@ -440,14 +484,15 @@ void vcycle(pf_ctx* ctx, int j) {
   const double w = sizeof(T);
   pf::Scalars* S = (pf::Scalars*)(ctx->ws + ctx->lay.S);
   double* part = (double*)(ctx->ws + ctx->lay.part);
+  const double e = ctx->prm.has_eps ? 1.0 : 0.0;   // eps read with the field, 1/diag with f
   for (size_t k = 0; k < k0; ++k) {
     const pf::MgView<T> lv = mg_view<T>(ctx, k), cv = mg_view<T>(ctx, k + 1);
     const double N = (double)lv.g.n;
     before_launch(ctx);
     pf::launch_mg_pre<T>(ctx->L, lv, S);
-    after_launch(ctx, mg_fam(F_MG_PRE, k), 2 * N * w, 2, j);
+    after_launch(ctx, mg_fam(F_MG_PRE, k), (2 + 2 * e) * N * w, 2, j);
     pf::launch_mg_rr<T>(ctx->L, lv, cv, S);
-    after_launch(ctx, mg_fam(F_MG_RR, k), (2 + 1.0 / (lv.fx * lv.fy * lv.fz)) * N * w, 2, j);
+    after_launch(ctx, mg_fam(F_MG_RR, k), (2 + e + 1.0 / (lv.fx * lv.fy * lv.fz)) * N * w, 2, j);
   }
   if (k0 + 1 < nl) {
     pf::MgTail<T> t{};
@@ -474,9 +519,9 @@ void vcycle(pf_ctx* ctx, int j) {
     const double N = (double)lv.g.n;
     before_launch(ctx);
     pf::launch_mg_post1<T>(ctx->L, lv, cv, S);
-    after_launch(ctx, mg_fam(F_MG_POST1, k), (3 + 1.0 / (lv.fx * lv.fy * lv.fz)) * N * w, 2, j);
+    after_launch(ctx, mg_fam(F_MG_POST1, k), (3 + 2 * e + 1.0 / (lv.fx * lv.fy * lv.fz)) * N * w, 2, j);
     pf::launch_mg_post2<T>(ctx->L, lv, k == 0, part, S);
-    after_launch(ctx, mg_fam(F_MG_POST2, k), 3 * N * w, 2, j);
+    after_launch(ctx, mg_fam(F_MG_POST2, k), (3 + 2 * e) * N * w, 2, j);
   }
 }
 
@@ -589,12 +634,7 @@ pf_status solve(pf_ctx* ctx, const T* P, bool adj = false, bool step_solve = fal
   int& est_iters = adj ? ctx->est_iters_adj : ctx->est_iters;
   const Geo& g = ctx->geo;
   const double N = (double)g.n, w = sizeof(T), e = ctx->prm.has_eps ? 1.0 : 0.0;
-  if (ctx->prm.has_eps && ctx->invd_dirty) {
-    before_launch(ctx);
-    pf::launch_invdiag<T>(ctx->L, g, d);
-    after_launch(ctx, F_INVDIAG, 2 * N * w);
-    ctx->invd_dirty = false;
-  }
+  refresh_invd<T>(ctx, ctx->L, true);
   if (step_solve && plain_extrap(ctx)) {
     before_launch(ctx);
     launch_extrap_of<T>(ctx, ctx->L);
@@ -621,7 +661,8 @@ pf_status solve(pf_ctx* ctx, const T* P, bool adj = false, bool step_solve = fal
       const int it = issued + i + 1;
       before_launch(ctx);
       pf::launch_cg_p<T>(ctx->L, g, d, mg, it == 1);
-      after_launch(ctx, F_CG_P, (6 + 2 * e) * N * w, 1, it, (3 + 2 * e) * N * w);
+      // the multigrid first iteration stages z alone (p = z), except with eps
+      after_launch(ctx, F_CG_P, (6 + 2 * e) * N * w, 1, it, (mg && e == 0.0) ? 3 * N * w : (6 + 2 * e) * N * w);
       pf::launch_cg_r<T>(ctx->L, g, d, mg, 0, 0);
       after_launch(ctx, F_CG_R, (3 + e) * N * w, 1, it);
       if (mg) vcycle<T>(ctx, it);
@@ -813,12 +854,7 @@ bool run_steps_graph(pf_ctx* ctx, int nsteps, pf_status* st) {
     }
     ctx->graph_key = ctx->singular;
   }
-  if (ctx->prm.has_eps && ctx->invd_dirty) {
-    pf::Dev<T> d = dev_view<T>(ctx);
-    pf::launch_invdiag<T>(ctx->L, ctx->geo, d);
-    ctx->launches += 1;
-    ctx->invd_dirty = false;
-  }
+  refresh_invd<T>(ctx, ctx->L, false);
   const bool heun = ctx->prm.integrator == PF_HEUN;
   for (int s = 0; s < nsteps; ++s) {
     const int refresh = refresh_step(ctx) ? 1 : 0;
@@ -846,14 +882,28 @@ bool run_steps_graph(pf_ctx* ctx, int nsteps, pf_status* st) {
   return true;
 }
 
+// Copy the state back into the bound P buffer when the last step left it in
+// the workspace copy.
 template <typename T>
-pf_status run_steps(pf_ctx* ctx, int nsteps) {
+pf_status consolidate(pf_ctx* ctx) {
+  if (ctx->cur == 1) {
+    PF_CUDA(cudaMemcpyAsync(ctx->P_user, ctx->ws + ctx->lay.P_alt, sizeof(T) * 3 * (size_t)ctx->geo.n,
+                            cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->cur = 0;
+  }
+  return PF_OK;
+}
+
+// Run nsteps steps; with keep_parity the state may stay in the workspace copy
+// (ctx->cur = 1) for the caller to read or consolidate.
+template <typename T>
+pf_status run_steps(pf_ctx* ctx, int nsteps, bool keep_parity = false) {
   pf::Dev<T> d = dev_view<T>(ctx);
   const Geo& g = ctx->geo;
   T* Pbuf[2] = {(T*)ctx->P_user, (T*)(ctx->ws + ctx->lay.P_alt)};
   const double coef[5] = {ctx->prm.a1, ctx->prm.a11, ctx->prm.a12, ctx->prm.g, ctx->prm.dt * ctx->prm.L};
   const bool heun = ctx->prm.integrator == PF_HEUN;
-  const double tdgl_bytes = 7.0 * (double)g.n * sizeof(T);
+  const double tdgl_bytes = (comp_state(&ctx->prm) ? 13.0 : 7.0) * (double)g.n * sizeof(T);
   pf_status gst;
   if (run_steps_graph<T>(ctx, nsteps, &gst)) {
     if (gst != PF_OK) return gst;
@@ -885,12 +935,8 @@ pf_status run_steps(pf_ctx* ctx, int nsteps) {
     }
     ctx->nstep += 1;
   }
-  if (ctx->cur == 1) {
-    PF_CUDA(cudaMemcpyAsync(Pbuf[0], Pbuf[1], sizeof(T) * 3 * (size_t)g.n, cudaMemcpyDeviceToDevice,
-                            ctx->stream));
-    ctx->cur = 0;
-  }
-  return PF_OK;
+  if (keep_parity) return PF_OK;
+  return consolidate<T>(ctx);
 }
 
 // Copy the host face masks to the device: the fine level and, for the
@@ -951,6 +997,8 @@ pf_status finish_info(pf_ctx* ctx, int nsteps, pf_step_info* info) {
     const int64_t bodies = mg ? s.total_iters + s.zero_solves - ctx->graph_solves : s.total_iters;
     info->kernel_launches = ctx->launches + (ctx->graph_steps ? ctx->graph_fixed + bodies * per_iter : 0);
     info->graph_steps = ctx->graph_steps;
+    info->max_iters = s.max_iters;
+    info->solves = s.solves;
   }
   return result;
 }
@@ -958,6 +1006,14 @@ pf_status finish_info(pf_ctx* ctx, int nsteps, pf_step_info* info) {
 pf_status check_ready(pf_ctx* ctx) {
   if (!ctx) return PF_ERR_ARG;
   if (!ctx->bound) return ctx->fail(PF_ERR_STATE, "no buffers bound (call pf_bind first)");
+  return PF_OK;
+}
+
+// Bound, and no pf_step_async work waiting for its pf_step_wait.
+pf_status idle_ready(pf_ctx* ctx) {
+  const pf_status st = check_ready(ctx);
+  if (st != PF_OK) return st;
+  if (ctx->async_open) return ctx->fail(PF_ERR_STATE, "pf_step_async work is pending (call pf_step_wait first)");
   return PF_OK;
 }
 
@@ -1021,6 +1077,7 @@ pf_status pf_create(const pf_params* params, void* cuda_stream, pf_ctx** out) {
 
 pf_status pf_bind(pf_ctx* ctx, void* P, void* phi, const void* eps, void* workspace, size_t workspace_bytes) {
   if (!ctx) return PF_ERR_ARG;
+  if (ctx->async_open) return ctx->fail(PF_ERR_STATE, "pf_step_async work is pending (call pf_step_wait first)");
   ctx->bound = false;
   if (!P || !phi || !workspace) return ctx->fail(PF_ERR_ARG, "P, phi and workspace must be non-NULL");
   if (ctx->prm.has_eps && !eps) return ctx->fail(PF_ERR_ARG, "has_eps = 1 but eps is NULL");
@@ -1047,6 +1104,8 @@ pf_status pf_bind(pf_ctx* ctx, void* P, void* phi, const void* eps, void* worksp
   std::fill(ctx->thi_h.begin(), ctx->thi_h.end(), 0);
   recompute_singular(ctx);
   PF_CUDA(cudaMemsetAsync(ctx->ws + L.S, 0, sizeof(Scalars), ctx->stream));
+  if (comp_state(&ctx->prm))
+    PF_CUDA(cudaMemsetAsync(ctx->ws + L.plo, 0, 3 * (size_t)ctx->geo.n * sizeof(float), ctx->stream));
   if (L.adj) {
     const size_t w = ctx->prm.precision == PF_FP32 ? 4 : 8;
     PF_CUDA(cudaMemsetAsync(ctx->ws + L.psi, 0, (size_t)ctx->geo.n * w, ctx->stream));
@@ -1059,7 +1118,7 @@ pf_status pf_bind(pf_ctx* ctx, void* P, void* phi, const void* eps, void* worksp
 }
 
 pf_status pf_set_bc(pf_ctx* ctx, int32_t face, const int8_t* type_xy, const double* volts_xy) {
-  pf_status st = check_ready(ctx);
+  pf_status st = idle_ready(ctx);
   if (st != PF_OK) return st;
   if (face != PF_ZLO && face != PF_ZHI) return ctx->fail(PF_ERR_ARG, "face must be PF_ZLO or PF_ZHI");
   if (!type_xy) return ctx->fail(PF_ERR_ARG, "type_xy is NULL");
@@ -1097,19 +1156,47 @@ pf_status pf_set_bc(pf_ctx* ctx, int32_t face, const int8_t* type_xy, const doub
   return upload_masks(ctx);
 }
 
-pf_status pf_step(pf_ctx* ctx, int32_t nsteps, pf_step_info* info) {
+pf_status pf_step_async(pf_ctx* ctx, int32_t nsteps) {
   pf_status st = check_ready(ctx);
   if (st != PF_OK) return st;
   if (nsteps < 0) return ctx->fail(PF_ERR_ARG, "nsteps must be >= 0");
-  st = reset_scalars(ctx);
-  if (st != PF_OK) return st;
+  if (!ctx->async_open) {
+    st = reset_scalars(ctx);
+    if (st != PF_OK) return st;
+    ctx->async_open = true;
+    ctx->async_steps = 0;
+  }
   st = ctx->prm.precision == PF_FP32 ? run_steps<float>(ctx, nsteps) : run_steps<double>(ctx, nsteps);
+  if (st != PF_OK) {
+    ctx->async_open = false;
+    ctx->async_steps = 0;
+    return st;
+  }
+  ctx->async_steps += nsteps;
+  return PF_OK;
+}
+
+pf_status pf_step_wait(pf_ctx* ctx, pf_step_info* info) {
+  pf_status st = check_ready(ctx);
   if (st != PF_OK) return st;
-  return finish_info(ctx, nsteps, info);
+  if (!ctx->async_open) {          // nothing pending: an empty report
+    st = reset_scalars(ctx);
+    if (st != PF_OK) return st;
+  }
+  const int64_t n = ctx->async_steps;
+  ctx->async_open = false;
+  ctx->async_steps = 0;
+  return finish_info(ctx, (int)n, info);
+}
+
+pf_status pf_step(pf_ctx* ctx, int32_t nsteps, pf_step_info* info) {
+  const pf_status st = pf_step_async(ctx, nsteps);
+  if (st != PF_OK) return st;
+  return pf_step_wait(ctx, info);
 }
 
 pf_status pf_step_host(pf_ctx* ctx, void* P_host, void* phi_host, int32_t nsteps, pf_step_info* info) {
-  pf_status st = check_ready(ctx);
+  pf_status st = idle_ready(ctx);
   if (st != PF_OK) return st;
   if (!P_host || !phi_host) return ctx->fail(PF_ERR_ARG, "P_host and phi_host must be non-NULL");
   if (nsteps < 0) return ctx->fail(PF_ERR_ARG, "nsteps must be >= 0");
@@ -1117,19 +1204,55 @@ pf_status pf_step_host(pf_ctx* ctx, void* P_host, void* phi_host, int32_t nsteps
   const size_t n = (size_t)ctx->geo.n;
   st = reset_scalars(ctx);
   if (st != PF_OK) return st;
+  // The state goes to and comes from whichever polarization buffer the step
+  // reads and writes, so no device-side copy is needed between steps.
+  auto pbuf = [&]() -> void* { return ctx->cur ? (void*)(ctx->ws + ctx->lay.P_alt) : ctx->P_user; };
   for (int s = 0; s < nsteps; ++s) {
-    PF_CUDA(cudaMemcpyAsync(ctx->P_user, P_host, 3 * n * w, cudaMemcpyHostToDevice, ctx->stream));
+    PF_CUDA(cudaMemcpyAsync(pbuf(), P_host, 3 * n * w, cudaMemcpyHostToDevice, ctx->stream));
     PF_CUDA(cudaMemcpyAsync(ctx->phi, phi_host, n * w, cudaMemcpyHostToDevice, ctx->stream));
-    st = ctx->prm.precision == PF_FP32 ? run_steps<float>(ctx, 1) : run_steps<double>(ctx, 1);
+    st = ctx->prm.precision == PF_FP32 ? run_steps<float>(ctx, 1, true) : run_steps<double>(ctx, 1, true);
     if (st != PF_OK) return st;
-    PF_CUDA(cudaMemcpyAsync(P_host, ctx->P_user, 3 * n * w, cudaMemcpyDeviceToHost, ctx->stream));
+    PF_CUDA(cudaMemcpyAsync(P_host, pbuf(), 3 * n * w, cudaMemcpyDeviceToHost, ctx->stream));
     PF_CUDA(cudaMemcpyAsync(phi_host, ctx->phi, n * w, cudaMemcpyDeviceToHost, ctx->stream));
   }
+  st = ctx->prm.precision == PF_FP32 ? consolidate<float>(ctx) : consolidate<double>(ctx);
+  if (st != PF_OK) return st;
   return finish_info(ctx, nsteps, info);
 }
 
+pf_status pf_true_residual(pf_ctx* ctx, const void* P, double* out) {
+  pf_status st = idle_ready(ctx);
+  if (st != PF_OK) return st;
+  if (!out) return ctx->fail(PF_ERR_ARG, "out is NULL");
+  const size_t w = ctx->prm.precision == PF_FP32 ? 4 : 8;
+  if (P && (((uintptr_t)P % w) != 0 || !is_device_ptr(P)))
+    return ctx->fail(PF_ERR_ARG, "P must be NULL or an aligned device pointer");
+  const void* Pp = P ? P : ctx->P_user;
+  double* dres = (double*)(ctx->ws + ctx->lay.diag);
+  if (ctx->prm.precision == PF_FP32) {
+    pf::Dev<float> d = dev_view<float>(ctx);
+    if (compensated(ctx)) {             // the compensated potential: bound phi + remainder
+      pf::Dev<float> dc = d;
+      comp_view<float>(ctx, dc);
+      d.cp = dc.cp;
+    }
+    pf::launch_true_residual<float>(ctx->L, ctx->geo, d, (const float*)Pp, ctx->singular, dres);
+  } else {
+    pf::launch_true_residual<double>(ctx->L, ctx->geo, dev_view<double>(ctx), (const double*)Pp, ctx->singular,
+                                     dres);
+  }
+  PF_CUDA(cudaGetLastError());
+  double h[3];
+  PF_CUDA(cudaMemcpyAsync(h, dres, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  PF_CUDA(cudaStreamSynchronize(ctx->stream));
+  out[0] = std::sqrt(h[0]);
+  out[1] = std::sqrt(h[1]);
+  out[2] = std::sqrt(h[2]);
+  return PF_OK;
+}
+
 pf_status pf_solve_potential(pf_ctx* ctx, pf_step_info* info) {
-  pf_status st = check_ready(ctx);
+  pf_status st = idle_ready(ctx);
   if (st != PF_OK) return st;
   if (ctx->cur != 0) return ctx->fail(PF_ERR_STATE, "internal: state not in the bound P buffer");
   st = reset_scalars(ctx);
@@ -1144,7 +1267,7 @@ pf_status pf_solve_potential(pf_ctx* ctx, pf_step_info* info) {
 
 pf_status pf_adjoint_step(pf_ctx* ctx, const void* lam_in, void* lam_out, double* grad_params,
                           double* grad_volts, pf_step_info* info) {
-  pf_status st = check_ready(ctx);
+  pf_status st = idle_ready(ctx);
   if (st != PF_OK) return st;
   if (!ctx->lay.adj) return ctx->fail(PF_ERR_STATE, "the context was created without PF_FLAG_ADJOINT");
   if (ctx->prm.integrator != PF_EULER || ctx->prm.poisson_every > 1 || ctx->noise_sigma != 0.0 || ctx->prm.n_air > 0)
@@ -1196,7 +1319,7 @@ pf_status pf_adjoint_step(pf_ctx* ctx, const void* lam_in, void* lam_out, double
 }
 
 pf_status pf_diagnostics(pf_ctx* ctx, double threshold, double* out) {
-  pf_status st = check_ready(ctx);
+  pf_status st = idle_ready(ctx);
   if (st != PF_OK) return st;
   if (!out) return ctx->fail(PF_ERR_ARG, "out is NULL");
   if (!std::isfinite(threshold)) return ctx->fail(PF_ERR_ARG, "threshold must be finite");
@@ -1228,6 +1351,7 @@ pf_status pf_diagnostics(pf_ctx* ctx, double threshold, double* out) {
 
 pf_status pf_profile_enable(pf_ctx* ctx, int32_t enable) {
   if (!ctx) return PF_ERR_ARG;
+  if (ctx->async_open) return ctx->fail(PF_ERR_STATE, "pf_step_async work is pending (call pf_step_wait first)");
   if (enable != 0 && enable != 1) return ctx->fail(PF_ERR_ARG, "enable must be 0 or 1");
   ctx->prof = enable == 1;
   prof_reset(ctx);
@@ -1244,6 +1368,7 @@ int32_t pf_profile_read(const pf_ctx* ctx, pf_kernel_stat* out, int32_t max) {
 
 pf_status pf_set_noise(pf_ctx* ctx, double sigma, uint64_t seed) {
   if (!ctx) return PF_ERR_ARG;
+  if (ctx->async_open) return ctx->fail(PF_ERR_STATE, "pf_step_async work is pending (call pf_step_wait first)");
   if (!std::isfinite(sigma) || sigma < 0.0) return ctx->fail(PF_ERR_ARG, "sigma must be finite and >= 0");
   drop_graphs(ctx);
   ctx->noise_sigma = sigma;
@@ -1264,6 +1389,7 @@ pf_status pf_get_tiling(const pf_ctx* ctx, pf_tiling* out) {
 
 pf_status pf_set_tiling(pf_ctx* ctx, const pf_tiling* t) {
   if (!ctx) return PF_ERR_ARG;
+  if (ctx->async_open) return ctx->fail(PF_ERR_STATE, "pf_step_async work is pending (call pf_step_wait first)");
   if (!t) return ctx->fail(PF_ERR_ARG, "tiling is NULL");
   const int fp32 = ctx->prm.precision == PF_FP32;
   const int vmax = fp32 ? 4 : 2;
@@ -1450,6 +1576,7 @@ pf_status pf_batch_create(pf_ctx* const* films, int32_t nfilms, void* workspace,
   for (int i = 0; i < nfilms; ++i) {
     pf_ctx* c = films[i];
     if (!c || !c->bound) return gfail(PF_ERR_ARG, "every film must be a bound context");
+    if (c->async_open) return gfail(PF_ERR_STATE, "a film has pf_step_async work pending (call pf_step_wait first)");
     for (int j = 0; j < i; ++j)
       if (films[j] == c) return gfail(PF_ERR_ARG, "a film appears twice");
     const pf_ctx* f0 = films[0];
@@ -1533,6 +1660,7 @@ pf_status pf_batch_step(pf_batch* b, int32_t nsteps, pf_step_info* info) {
   pf_ctx* f0 = b->films[0];
   for (pf_ctx* c : b->films) {
     if (!c->bound) return b->fail(PF_ERR_STATE, "a film is no longer bound");
+    if (c->async_open) return b->fail(PF_ERR_STATE, "a film has pf_step_async work pending");
     if (c->nstep != f0->nstep || c->cur != 0) return b->fail(PF_ERR_STATE, "films are no longer at the same step");
   }
   bool stale = false;
@@ -1544,12 +1672,8 @@ pf_status pf_batch_step(pf_batch* b, int32_t nsteps, pf_step_info* info) {
   for (pf_ctx* c : b->films) {
     pf_status st = reset_scalars(c);
     if (st != PF_OK) return b->fail(st, "film: %s", c->err.c_str());
-    if (c->prm.has_eps && c->invd_dirty) {
-      if (c->prm.precision == PF_FP32) pf::launch_invdiag<float>(c->L, c->geo, dev_view<float>(c));
-      else pf::launch_invdiag<double>(c->L, c->geo, dev_view<double>(c));
-      c->launches += 1;
-      c->invd_dirty = false;
-    }
+    if (c->prm.precision == PF_FP32) refresh_invd<float>(c, c->L, false);
+    else refresh_invd<double>(c, c->L, false);
   }
   const bool heun = f0->prm.integrator == PF_HEUN;
   for (int s = 0; s < nsteps; ++s) {
@@ -1591,6 +1715,8 @@ pf_status pf_batch_step(pf_batch* b, int32_t nsteps, pf_step_info* info) {
     if (st == PF_ERR_NONFINITE || (st == PF_ERR_NOCONV && worst == PF_OK)) worst = st;
     sum.last_iters = std::max(sum.last_iters, fi.last_iters);
     sum.total_iters += fi.total_iters;
+    sum.max_iters = std::max(sum.max_iters, fi.max_iters);
+    sum.solves += fi.solves;
     sum.last_relres = std::max(sum.last_relres, fi.last_relres);
     sum.nonconverged += fi.nonconverged;
     sum.kernel_launches += fi.kernel_launches;

@@ -263,7 +263,10 @@ static void launch_cg_p_v(const LaunchCfg& L, const Geo& g, const Dev<T>& d) {
 
 template <typename T>
 void launch_cg_p(const LaunchCfg& L, const Geo& g, const Dev<T>& d, int mg, int first) {
-  if (mg && first) launch_cg_p_v<T, false, true, true>(L, g, d);
+  // with a permittivity field the multigrid form stages eps too (field-buffer
+  // march; its first iteration reads the first-iteration flag of the solver)
+  if (mg && d.eps) launch_cg_p_v<T, true, true>(L, g, d);
+  else if (mg && first) launch_cg_p_v<T, false, true, true>(L, g, d);
   else if (mg) launch_cg_p_v<T, false, true>(L, g, d);
   else if (d.eps) launch_cg_p_v<T, true, false>(L, g, d);
   else launch_cg_p_v<T, false, false>(L, g, d);

@@ -106,6 +106,8 @@ struct Scalars {
   unsigned long long sched_next;   // dynamic tile scheduler: next tile
   unsigned sched_done;             // blocks that ran out of tiles
   int zero_solves;                 // solves that ended with no iteration (per pf_step call)
+  int max_iters;                   // most iterations of one solve (per pf_step call)
+  int solves;                      // solves finished (per pf_step call)
 };
 
 // ---------------------------------------------------------------- reductions

@@ -117,4 +117,127 @@ template void launch_diag<float>(const LaunchCfg&, const Geo&, const Dev<float>&
 template void launch_diag<double>(const LaunchCfg&, const Geo&, const Dev<double>&, const double*, const double*,
                                   double*);
 
+// ------------------------------------------------------------ true residual
+//
+// ||b(P) - A phi||_2^2 and ||b(P)||_2^2 of a stored state, every operation in
+// FP64 whatever the storage precision.  The Krylov loop stops on its
+// recursive residual; this is the residual of the potential actually stored
+// (in FP32 mode, after rounding to FP32).  b and A follow the face rules of k_rhs and
+// apply_field (Eqs. rho, Poisson: face values of P are the mean inside, P_cell
+// at an electrode, 0 at an open face; Dirichlet faces add 2 eps_c (phi_c - V)
+// / dx^2, open faces nothing; interior face permittivity is the harmonic mean).
+// Singular problems (no electrode) use b - mean(b), the system the solver
+// solves: MEAN = true sums b alone.  One thread per cell, neighbours read from
+// global memory (a diagnostic, not on the hot path).
+// An FP32 time series also keeps the part of the last solution that the
+// stored phi cannot hold (see k_cg_finish_comp: after solve k the remainder
+// buffer holds that part plus the next start's increment c_{k+1}, which sits
+// in ring slot (k + 1) mod 3).  With cp.lo set, the third sum is the residual
+// of that compensated potential phi + (lo - c_{k+1}), formed in FP64.
+template <typename T, bool EPS, bool MEAN>
+__global__ void __launch_bounds__(256) k_true_res(Geo g, Bc<T> bc, const T* __restrict__ P, const T* __restrict__ phi,
+                                                  const T* __restrict__ eps, Comp<T> cp, double mb, double* part,
+                                                  unsigned* ticket, double* out) {
+  constexpr int NV = MEAN ? 1 : 3;
+  const long long ks = cp.lo ? *cp.nsolve : 0;
+  const T* cn = ks >= 1 ? cp.ring[ks % 3] : nullptr;
+  auto phic = [&](long long c) -> double {
+    const double v = (double)phi[c];
+    return cn ? v + ((double)cp.lo[c] - (double)cn[c]) : v;
+  };
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const double ih = g.ih, ih2 = g.ih2;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.n; c += stride) {
+    const int x = (int)(c % g.nx);
+    const int y = (int)((c / g.nx) % g.ny);
+    const int z = (int)(c / g.nxy);
+    const long long xy = (long long)y * g.nx + x;
+    const long long zo = c - xy;
+    const long long nb[6] = {zo + (long long)y * g.nx + (x == 0 ? g.nx - 1 : x - 1),
+                             zo + (long long)y * g.nx + (x == g.nx - 1 ? 0 : x + 1),
+                             zo + (long long)(y == 0 ? g.ny - 1 : y - 1) * g.nx + x,
+                             zo + (long long)(y == g.ny - 1 ? 0 : y + 1) * g.nx + x,
+                             z > 0 ? c - g.nxy : (g.periodic_z ? c + (long long)(g.nz - 1) * g.nxy : -1),
+                             z < g.nz - 1 ? c + g.nxy : (g.periodic_z ? c - (long long)(g.nz - 1) * g.nxy : -1)};
+    const int dlo = nb[4] < 0 ? (int)bc.tlo[xy] : 0;
+    const int dhi = nb[5] < 0 ? (int)bc.thi[xy] : 0;
+    const double ec = EPS ? (double)eps[c] : 1.0;
+    // b = -div P + Dirichlet terms, faces in the order x-, x+, y-, y+, z-, z+
+    double div = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const T* Pa = P + a * g.n;
+      const double pc = (double)Pa[c];
+      const long long m = nb[2 * a], p = nb[2 * a + 1];
+      double fm, fp;
+      if (m >= 0) fm = 0.5 * (pc + (double)Pa[m]);
+      else fm = dlo ? pc : 0.0;
+      if (p >= 0) fp = 0.5 * (pc + (double)Pa[p]);
+      else fp = dhi ? pc : 0.0;
+      div += fp - fm;
+    }
+    double b = -div * ih - mb;
+    if (dlo) b += 2.0 * ec * (double)bc.vlo[xy] * ih2;
+    if (dhi) b += 2.0 * ec * (double)bc.vhi[xy] * ih2;
+    if (MEAN) {
+      acc[0] += b;
+      continue;
+    }
+    const double fc = (double)phi[c], gc = phic(c);
+    double Af = 0.0, Ag = 0.0;
+    for (int f = 0; f < 6; ++f) {
+      if (nb[f] >= 0) {
+        const double en = EPS ? (double)eps[nb[f]] : 1.0;
+        const double ef = EPS ? 2.0 * ec * en / (ec + en) : 1.0;
+        Af += ef * (fc - (double)phi[nb[f]]);
+        Ag += ef * (gc - phic(nb[f]));
+      } else if ((f == 4 && dlo) || (f == 5 && dhi)) {
+        Af += 2.0 * ec * fc;
+        Ag += 2.0 * ec * gc;
+      }
+    }
+    const double r = b - Af * ih2, rg = b - Ag * ih2;
+    acc[0] += r * r;
+    acc[1] += b * b;
+    acc[NV - 1] += rg * rg;
+  }
+  if (!publish_partials<NV, 256>(acc, part, ticket)) return;
+  double sum[NV];
+  gather_partials<NV, 256>(part, gridDim.x, sum);
+  if (threadIdx.x != 0) return;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = sum[k];
+  *ticket = 0;
+}
+
+template <typename T, bool EPS>
+static void true_res_t(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, int singular, double* out) {
+  const int grid = std::max(1, std::min(L.flat_grid, MAX_GRID));
+  double mb = 0.0;
+  if (singular) {
+    k_true_res<T, EPS, true><<<grid, 256, 0, L.stream>>>(g, d.bc, P, d.phi, d.eps, d.cp, 0.0, d.part, &d.S->ticket,
+                                                         out);
+    // the mean of b is read back by the host between the passes (a diagnostic)
+    double sb = 0.0;
+    if (cudaMemcpyAsync(&sb, out, sizeof(double), cudaMemcpyDeviceToHost, L.stream) != cudaSuccess ||
+        cudaStreamSynchronize(L.stream) != cudaSuccess)
+      return;
+    mb = sb / (double)g.n;
+  }
+  k_true_res<T, EPS, false><<<grid, 256, 0, L.stream>>>(g, d.bc, P, d.phi, d.eps, d.cp, mb, d.part, &d.S->ticket,
+                                                        out);
+}
+
+template <typename T>
+void launch_true_residual(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, int singular, double* out) {
+  if (d.eps) true_res_t<T, true>(L, g, d, P, singular, out);
+  else true_res_t<T, false>(L, g, d, P, singular, out);
+}
+
+template void launch_true_residual<float>(const LaunchCfg&, const Geo&, const Dev<float>&, const float*, int, double*);
+template void launch_true_residual<double>(const LaunchCfg&, const Geo&, const Dev<double>&, const double*, int,
+                                           double*);
+
 }  // namespace pf

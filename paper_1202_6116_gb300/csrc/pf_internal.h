@@ -55,6 +55,7 @@ struct Dev {
   double* part;
   Scalars* S;
   Comp<T> cp;
+  T* plo;            // remainder of a compensated FP32 polarization state (3N), or nullptr
 };
 
 // One multigrid level as the kernels see it.
@@ -68,6 +69,8 @@ struct MgView {
   T* f;               // right-hand side (level 0: the CG residual r)
   T* e;               // correction (level 0: z = M^-1 r)
   T* et;              // second buffer of the Jacobi sweeps
+  const T* eps;       // cell permittivity of this level (nullptr: eps = 1)
+  const T* invd;      // 1/diag of this level's operator (with eps only)
   MarchCfg mc;
 };
 
@@ -130,6 +133,14 @@ void launch_tdgl_adj(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T*
 // f(P), the squared face differences of P, and P.E(phi); coef = {a1, a11, a12, thr}.
 template <typename T>
 void launch_diag(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, const double* coef, double* out);
+
+// True residual (pf_diag.cu): out[0] = ||b(P) - A phi||^2, out[1] = ||b(P)||^2,
+// out[2] = the first for the compensated potential when d.cp.lo is set (else
+// equal to out[0]), in FP64 (b projected to zero mean when singular).  out:
+// device, 3 doubles.
+// Blocks the host between its two passes when singular.
+template <typename T>
+void launch_true_residual(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, int singular, double* out);
 
 // One film of a batch as the batch kernels see it (device table).
 struct BatchFilm {
@@ -239,5 +250,9 @@ template <typename T>
 void launch_mg_post2(const LaunchCfg& L, const MgView<T>& lv, int last, double* part, Scalars* S);
 template <typename T>
 int mg_blocks_per_sm();
+// Permittivity of a coarse level (the mean of the fine children, into ceps)
+// and 1/diag of its operator (into cinvd).
+template <typename T>
+void launch_mg_eps_level(const LaunchCfg& L, const MgView<T>& fine, const MgView<T>& coarse, T* ceps, T* cinvd);
 
 }  // namespace pf

@@ -122,6 +122,8 @@ __global__ void __launch_bounds__(NTHREADS) k_cg_finish(Geo g, T* __restrict__ x
       if (S->iter == 0) S->zero_solves += 1;
       S->total_iters += S->iter;
       S->last_iters = S->iter;
+      S->solves += 1;
+      if (S->iter > S->max_iters) S->max_iters = S->iter;
       if (S->status != 0) S->nonconv += 1;
       S->ticket = 0;
     }
@@ -227,6 +229,8 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_cg_finish_comp(long long n, fl
     if (S->iter == 0) S->zero_solves += 1;
     S->total_iters += S->iter;
     S->last_iters = S->iter;
+    S->solves += 1;
+    if (S->iter > S->max_iters) S->max_iters = S->iter;
     if (S->status != 0) S->nonconv += 1;
     S->ticket = 0;
     *cp.nsolve = k + 1;

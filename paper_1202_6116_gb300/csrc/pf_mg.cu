@@ -12,6 +12,11 @@
 // positive definite preconditioner.  The coarsest level (<= MG_MAX_COARSE cells) is
 // solved by FP64 conjugate gradients inside one thread block.
 //
+// With a permittivity field every level carries its own cell permittivity
+// (level 0: the bound eps; a coarse cell: the mean of its children) and 1/diag
+// of its operator (precomputed); faces weigh the harmonic mean of the two
+// cells' eps, an electrode face 2 eps_c, as on the finest level.
+//
 // Per level and V-cycle (nu = 2):
 //   k_mg_pre     e = two Jacobi sweeps from zero (the first sweep w1 f/diag
 //                is formed on the fly, halo included)   reads f, writes e
@@ -81,13 +86,52 @@ __device__ __forceinline__ T mg_inv_bt(const MgView<T>& L, int xy, int z, T inv_
   return bt ? mg_inv(L, xy, z, inv_int) : inv_int;
 }
 
-template <typename T, int VX>
-using MgPipeD0 = Pipe<T, void, MTX, MTY, VX, 1, 0, MG_D>;
-template <typename T, int VX>
-using MgPipeP = Pipe<T, void, MTX, MTY, VX, 1, 1, MG_D, 1>;
-// stencil read straight from the staged planes (no field buffer)
-template <typename T, int VX>
-using MgPipeD = Pipe<T, void, MTX, MTY, VX, 1, 1, MG_D>;
+// A v at a level with cell permittivities (v and eps carried together).
+template <typename T>
+__device__ __forceinline__ T apply_aniso_eps(const Stencil7<EpsVal<T>>& s, int dlo, int dhi, T ax, T ay, T az,
+                                             const bool bt) {
+  const T ec = s.c.e, vc = s.c.v;
+  const T sx = hmean2(ec, s.xm.e) * (vc - s.xm.v) + hmean2(ec, s.xp.e) * (vc - s.xp.v);
+  const T sy = hmean2(ec, s.ym.e) * (vc - s.ym.v) + hmean2(ec, s.yp.e) * (vc - s.yp.v);
+  T sz = T(0);
+  if (bt) {
+    if (s.zb >= 0) sz += hmean2(ec, s.zm.e) * (vc - s.zm.v);
+    else if (dlo) sz += T(2) * ec * vc;
+    if (s.za >= 0) sz += hmean2(ec, s.zp.e) * (vc - s.zp.v);
+    else if (dhi) sz += T(2) * ec * vc;
+  } else {
+    sz = hmean2(ec, s.zm.e) * (vc - s.zm.v) + hmean2(ec, s.zp.e) * (vc - s.zp.v);
+  }
+  return ax * sx + ay * sy + az * sz;
+}
+
+// Field kv with the permittivity of field ke, as one stencil.
+template <typename T, int NF>
+__device__ __forceinline__ Stencil7<EpsVal<T>> pick_eps(const Stencil7<Raw<T, NF>>& s, int kv, int ke) {
+  Stencil7<EpsVal<T>> o;
+  o.c = EpsVal<T>{s.c.v[kv], s.c.v[ke]};
+  o.xm = EpsVal<T>{s.xm.v[kv], s.xm.v[ke]};
+  o.xp = EpsVal<T>{s.xp.v[kv], s.xp.v[ke]};
+  o.ym = EpsVal<T>{s.ym.v[kv], s.ym.v[ke]};
+  o.yp = EpsVal<T>{s.yp.v[kv], s.yp.v[ke]};
+  o.zm = EpsVal<T>{s.zm.v[kv], s.zm.v[ke]};
+  o.zp = EpsVal<T>{s.zp.v[kv], s.zp.v[ke]};
+  o.zb = s.zb;
+  o.za = s.za;
+  return o;
+}
+
+// Staged planes of the sweeps (E: with a permittivity field, eps staged with
+// halo beside the field, 1/diag staged at the own cells -- and with halo in
+// the pre-smoother, whose first sweep is formed at all seven cells).
+template <typename T, int VX, bool E = false>
+using MgPipeD0 = Pipe<T, void, MTX, MTY, VX, E ? 3 : 1, 0, MG_D>;
+template <typename T, int VX, bool E = false>
+using MgPipeP = Pipe<T, void, MTX, MTY, VX, E ? 2 : 1, E ? 2 : 1, MG_D, 1>;
+template <typename T, int VX, bool E = false>
+using MgPipeR = Pipe<T, void, MTX, MTY, VX, E ? 2 : 1, 1, MG_D>;
+template <typename T, int VX, bool E = false>
+using MgPipeD = Pipe<T, void, MTX, MTY, VX, E ? 2 : 1, E ? 2 : 1, MG_D>;
 
 // ------------------------------------------------------------------ kernels
 
@@ -96,57 +140,79 @@ using MgPipeD = Pipe<T, void, MTX, MTY, VX, 1, 1, MG_D>;
 // A e1).  Away from the z faces the diagonal is one constant, so A e1 =
 // w1 diag^-1 A f there; on the planes next to a z face and their neighbour
 // planes e1 is formed per neighbour with its own diagonal.
-template <typename T, int VX>
+template <typename T, int VX, bool EPS>
 __global__ void __launch_bounds__(MTX* MTY) k_mg_pre(MgView<T> L, Scalars* S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   if (S->done) return;
+  constexpr int NH = EPS ? 3 : 1;          // f (, eps, 1/diag)
   const T om1 = mg_omega1<T>(), om2 = mg_omega2<T>(), inv_int = mg_inv_int(L);
   const T w1 = om1 * inv_int;
-  const T* hsrc[1] = {L.f};
+  const T* hsrc[NH];
+  hsrc[0] = L.f;
+  if constexpr (EPS) {
+    hsrc[1] = L.eps;
+    hsrc[2] = L.invd;
+  }
   const T* osrc[1] = {nullptr};
   const int nx = L.g.nx, nz = L.g.nz;
   const bool zfaces = !L.g.periodic_z;
   TileGeo<MTX, MTY, VX> s;
-  auto emit = [&](int xy, int z, const Stencil7<Raw<T, 1>>& sr, const T (&)[1], const bool bt) -> T {
+  auto emit = [&](int xy, int z, const Stencil7<Raw<T, NH>>& sr, const T (&)[1], const bool bt) -> T {
     const Stencil7<T> f = pick(sr, 0);
-    const bool near = zfaces && (z == 1 || z == nz - 2);
-    if (!bt && !near) {
-      const T Ae1 = w1 * apply_aniso(f, 0, 0, L.ax, L.ay, L.az, false);
-      return w1 * f.c + om2 * inv_int * (f.c - Ae1);
-    }
-    Stencil7<T> e1;
-    const T ic = mg_inv(L, xy, z, inv_int);
-    e1.c = om1 * ic * f.c;
-    if (bt) {
-      const int x = xy % nx, rb = xy - x;
-      const int xm = rb + (x == 0 ? nx - 1 : x - 1), xp = rb + (x == nx - 1 ? 0 : x + 1);
-      const int y = xy / nx;
-      const int ym = (y == 0 ? L.g.ny - 1 : y - 1) * nx + x, yp = (y == L.g.ny - 1 ? 0 : y + 1) * nx + x;
-      e1.xm = om1 * mg_inv(L, xm, z, inv_int) * f.xm;
-      e1.xp = om1 * mg_inv(L, xp, z, inv_int) * f.xp;
-      e1.ym = om1 * mg_inv(L, ym, z, inv_int) * f.ym;
-      e1.yp = om1 * mg_inv(L, yp, z, inv_int) * f.yp;
+    if constexpr (EPS) {
+      // first sweep e1 = w1 f / diag at all seven cells, then the second
+      Stencil7<EpsVal<T>> e1 = pick_eps(sr, 0, 1);
+      e1.c.v = om1 * sr.c.v[2] * f.c;
+      e1.xm.v = om1 * sr.xm.v[2] * f.xm;
+      e1.xp.v = om1 * sr.xp.v[2] * f.xp;
+      e1.ym.v = om1 * sr.ym.v[2] * f.ym;
+      e1.yp.v = om1 * sr.yp.v[2] * f.yp;
+      e1.zm.v = f.zb >= 0 ? om1 * sr.zm.v[2] * f.zm : T(0);
+      e1.zp.v = f.za >= 0 ? om1 * sr.zp.v[2] * f.zp : T(0);
+      const int dlo = (bt && f.zb < 0) ? (int)L.tlo[xy] : 0;
+      const int dhi = (bt && f.za < 0) ? (int)L.thi[xy] : 0;
+      const T Ae1 = apply_aniso_eps(e1, dlo, dhi, L.ax, L.ay, L.az, bt);
+      return e1.c.v + om2 * sr.c.v[2] * (f.c - Ae1);
     } else {
-      e1.xm = w1 * f.xm;
-      e1.xp = w1 * f.xp;
-      e1.ym = w1 * f.ym;
-      e1.yp = w1 * f.yp;
+      const bool near = zfaces && (z == 1 || z == nz - 2);
+      if (!bt && !near) {
+        const T Ae1 = w1 * apply_aniso(f, 0, 0, L.ax, L.ay, L.az, false);
+        return w1 * f.c + om2 * inv_int * (f.c - Ae1);
+      }
+      Stencil7<T> e1;
+      const T ic = mg_inv(L, xy, z, inv_int);
+      e1.c = om1 * ic * f.c;
+      if (bt) {
+        const int x = xy % nx, rb = xy - x;
+        const int xm = rb + (x == 0 ? nx - 1 : x - 1), xp = rb + (x == nx - 1 ? 0 : x + 1);
+        const int y = xy / nx;
+        const int ym = (y == 0 ? L.g.ny - 1 : y - 1) * nx + x, yp = (y == L.g.ny - 1 ? 0 : y + 1) * nx + x;
+        e1.xm = om1 * mg_inv(L, xm, z, inv_int) * f.xm;
+        e1.xp = om1 * mg_inv(L, xp, z, inv_int) * f.xp;
+        e1.ym = om1 * mg_inv(L, ym, z, inv_int) * f.ym;
+        e1.yp = om1 * mg_inv(L, yp, z, inv_int) * f.yp;
+      } else {
+        e1.xm = w1 * f.xm;
+        e1.xp = w1 * f.xp;
+        e1.ym = w1 * f.ym;
+        e1.yp = w1 * f.yp;
+      }
+      e1.zm = f.zb >= 0 ? om1 * mg_inv(L, xy, z - 1, inv_int) * f.zm : T(0);
+      e1.zp = f.za >= 0 ? om1 * mg_inv(L, xy, z + 1, inv_int) * f.zp : T(0);
+      e1.zb = f.zb;
+      e1.za = f.za;
+      const int dlo = (bt && f.zb < 0) ? (int)L.tlo[xy] : 0;
+      const int dhi = (bt && f.za < 0) ? (int)L.thi[xy] : 0;
+      const T Ae1 = apply_aniso(e1, dlo, dhi, L.ax, L.ay, L.az, bt);
+      return e1.c + om2 * ic * (f.c - Ae1);
     }
-    e1.zm = f.zb >= 0 ? om1 * mg_inv(L, xy, z - 1, inv_int) * f.zm : T(0);
-    e1.zp = f.za >= 0 ? om1 * mg_inv(L, xy, z + 1, inv_int) * f.zp : T(0);
-    e1.zb = f.zb;
-    e1.za = f.za;
-    const int dlo = (bt && f.zb < 0) ? (int)L.tlo[xy] : 0;
-    const int dhi = (bt && f.za < 0) ? (int)L.thi[xy] : 0;
-    const T Ae1 = apply_aniso(e1, dlo, dhi, L.ax, L.ay, L.az, bt);
-    return e1.c + om2 * ic * (f.c - Ae1);
   };
   auto post = [&](int z, const T (&ov)[VX]) { store_n<T, VX>(L.e + (long long)z * L.g.nxy + s.xy, ov); };
   const TileSched ts{&S->sched_next, &S->sched_done};
   for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
-    march_direct<T, T, MTX, MTY, VX, 1, 0, MG_D>(L.g, s, smem, hsrc, osrc, emit, post);
+    march_direct<T, T, MTX, MTY, VX, NH, 0, MG_D>(L.g, s, smem, hsrc, osrc, emit, post);
   }
   sched_finish(ts);
 }
@@ -155,25 +221,28 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_pre(MgView<T> L, Scalars* S) {
 // in registers across consecutive planes of the march), 2 rows (tile rows 2k,
 // 2k+1 share a warp: lane ^ 16), 2 columns (inside the thread's vector, or
 // lane ^ 1 when a thread owns one cell).
-template <typename T, int VX>
+template <typename T, int VX, bool EPS>
 __global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Scalars* S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   static_assert(MTX == 16, "row pairs share a warp");
   if (S->done) return;
-  const T* hsrc[1] = {L.e};
+  constexpr int NH = EPS ? 2 : 1;          // e (, eps)
+  const T* hsrc[NH];
+  hsrc[0] = L.e;
+  if constexpr (EPS) hsrc[1] = L.eps;
   const T* osrc[1] = {L.f};
   const T scale = T(1) / T(L.fx * L.fy * L.fz);
   TileGeo<MTX, MTY, VX> s;
   T racc[VX];
 #pragma unroll
   for (int i = 0; i < VX; ++i) racc[i] = T(0);
-  auto emit = [&](int xy, int, const Stencil7<Raw<T, 1>>& sr, const T (&o)[1], const bool bt) -> T {
-    const Stencil7<T> st = pick(sr, 0);
+  auto emit = [&](int xy, int, const Stencil7<Raw<T, NH>>& sr, const T (&o)[1], const bool bt) -> T {
     const bool B = bt;
-    const int dlo = (B && st.zb < 0) ? (int)L.tlo[xy] : 0;
-    const int dhi = (B && st.za < 0) ? (int)L.thi[xy] : 0;
-    return o[0] - apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az, bt);
+    const int dlo = (B && sr.zb < 0) ? (int)L.tlo[xy] : 0;
+    const int dhi = (B && sr.za < 0) ? (int)L.thi[xy] : 0;
+    if constexpr (EPS) return o[0] - apply_aniso_eps(pick_eps(sr, 0, 1), dlo, dhi, L.ax, L.ay, L.az, bt);
+    else return o[0] - apply_aniso(pick(sr, 0), dlo, dhi, L.ax, L.ay, L.az, bt);
   };
   auto post = [&](int z, const T (&rv)[VX]) {
 #pragma unroll
@@ -211,7 +280,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Sc
   const TileSched ts{&S->sched_next, &S->sched_done};
   for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
-    march_direct<T, T, MTX, MTY, VX, 1, 1, MG_D>(L.g, s, smem, hsrc, osrc, emit, post);
+    march_direct<T, T, MTX, MTY, VX, NH, 1, MG_D>(L.g, s, smem, hsrc, osrc, emit, post);
   }
   sched_finish(ts);
 }
@@ -219,61 +288,92 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Sc
 // Prolongation + correction fused into the first post-smoothing sweep: the
 // stencil field is e + e_c(parent), the parents staged with the fine planes
 // and combined with e at each of the seven cells.
-template <typename T, int VX>
+template <typename T, int VX, bool EPS>
 __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_mg_post1(MgView<T> L, MgView<T> C, Scalars* S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   if (S->done) return;
+  constexpr int NH = EPS ? 2 : 1;          // e (, eps); the parents come as field NH
+  constexpr int NO = EPS ? 2 : 1;          // f (, 1/diag)
   const T om = mg_omega2<T>(), inv_int = mg_inv_int(L);
-  const T* hsrc[1] = {L.e};
-  const T* osrc[1] = {L.f};
+  const T* hsrc[NH];
+  hsrc[0] = L.e;
+  if constexpr (EPS) hsrc[1] = L.eps;
+  const T* osrc[NO];
+  osrc[0] = L.f;
+  if constexpr (EPS) osrc[1] = L.invd;
   const ParentSrc<T> par{C.e, L.fx, L.fy, L.fz, C.g.nx, C.g.nxy};
   TileGeo<MTX, MTY, VX> s;
-  auto emit = [&](int xy, int z, const Stencil7<Raw<T, 2>>& sr, const T (&o)[1], const bool bt) -> T {
+  auto emit = [&](int xy, int z, const Stencil7<Raw<T, NH + 1>>& sr, const T (&o)[NO], const bool bt) -> T {
     Stencil7<T> st;
-    st.c = sr.c.v[0] + sr.c.v[1];
-    st.xm = sr.xm.v[0] + sr.xm.v[1];
-    st.xp = sr.xp.v[0] + sr.xp.v[1];
-    st.ym = sr.ym.v[0] + sr.ym.v[1];
-    st.yp = sr.yp.v[0] + sr.yp.v[1];
-    st.zm = sr.zm.v[0] + sr.zm.v[1];
-    st.zp = sr.zp.v[0] + sr.zp.v[1];
+    st.c = sr.c.v[0] + sr.c.v[NH];
+    st.xm = sr.xm.v[0] + sr.xm.v[NH];
+    st.xp = sr.xp.v[0] + sr.xp.v[NH];
+    st.ym = sr.ym.v[0] + sr.ym.v[NH];
+    st.yp = sr.yp.v[0] + sr.yp.v[NH];
+    st.zm = sr.zm.v[0] + sr.zm.v[NH];
+    st.zp = sr.zp.v[0] + sr.zp.v[NH];
     st.zb = sr.zb;
     st.za = sr.za;
     const bool B = bt;
     const int dlo = (B && st.zb < 0) ? (int)L.tlo[xy] : 0;
     const int dhi = (B && st.za < 0) ? (int)L.thi[xy] : 0;
-    const T Ae = apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az, bt);
-    return st.c + om * mg_inv_bt(L, xy, z, inv_int, bt) * (o[0] - Ae);
+    if constexpr (EPS) {
+      Stencil7<EpsVal<T>> se = pick_eps(sr, 0, 1);
+      se.c.v = st.c;
+      se.xm.v = st.xm;
+      se.xp.v = st.xp;
+      se.ym.v = st.ym;
+      se.yp.v = st.yp;
+      se.zm.v = st.zm;
+      se.zp.v = st.zp;
+      const T Ae = apply_aniso_eps(se, dlo, dhi, L.ax, L.ay, L.az, bt);
+      return st.c + om * o[1] * (o[0] - Ae);
+    } else {
+      const T Ae = apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az, bt);
+      return st.c + om * mg_inv_bt(L, xy, z, inv_int, bt) * (o[0] - Ae);
+    }
   };
   auto post = [&](int z, const T (&ov)[VX]) { store_n<T, VX>(L.et + (long long)z * L.g.nxy + s.xy, ov); };
   const TileSched ts{&S->sched_next, &S->sched_done};
   for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
-    march_direct<T, T, MTX, MTY, VX, 1, 1, MG_D, 1>(L.g, s, smem, hsrc, osrc, emit, post, par);
+    march_direct<T, T, MTX, MTY, VX, NH, NO, MG_D, 1>(L.g, s, smem, hsrc, osrc, emit, post, par);
   }
   sched_finish(ts);
 }
 
 // Last post-smoothing sweep.  On the finest level (LAST) it also forms
 // r.z (f = r, e = z): the last block sets beta = (r.z)_new / (r.z)_old.
-template <typename T, bool LAST, int VX>
+template <typename T, bool LAST, int VX, bool EPS>
 __global__ void __launch_bounds__(MTX* MTY) k_mg_post2(MgView<T> L, double* part, Scalars* S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   if (S->done) return;
+  constexpr int NH = EPS ? 2 : 1;          // et (, eps)
+  constexpr int NO = EPS ? 2 : 1;          // f (, 1/diag)
   const T om = mg_omega1<T>(), inv_int = mg_inv_int(L);
-  const T* hsrc[1] = {L.et};
-  const T* osrc[1] = {L.f};
+  const T* hsrc[NH];
+  hsrc[0] = L.et;
+  if constexpr (EPS) hsrc[1] = L.eps;
+  const T* osrc[NO];
+  osrc[0] = L.f;
+  if constexpr (EPS) osrc[1] = L.invd;
   Acc<T> arz;
   TileGeo<MTX, MTY, VX> s;
-  auto emit = [&](int xy, int z, const Stencil7<Raw<T, 1>>& sr, const T (&o)[1], const bool bt) -> T {
-    const Stencil7<T> st = pick(sr, 0);
+  auto emit = [&](int xy, int z, const Stencil7<Raw<T, NH>>& sr, const T (&o)[NO], const bool bt) -> T {
     const bool B = bt;
-    const int dlo = (B && st.zb < 0) ? (int)L.tlo[xy] : 0;
-    const int dhi = (B && st.za < 0) ? (int)L.thi[xy] : 0;
-    const T Ae = apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az, bt);
-    const T e = st.c + om * mg_inv_bt(L, xy, z, inv_int, bt) * (o[0] - Ae);
+    const int dlo = (B && sr.zb < 0) ? (int)L.tlo[xy] : 0;
+    const int dhi = (B && sr.za < 0) ? (int)L.thi[xy] : 0;
+    T e;
+    if constexpr (EPS) {
+      const T Ae = apply_aniso_eps(pick_eps(sr, 0, 1), dlo, dhi, L.ax, L.ay, L.az, bt);
+      e = sr.c.v[0] + om * o[1] * (o[0] - Ae);
+    } else {
+      const Stencil7<T> st = pick(sr, 0);
+      const T Ae = apply_aniso(st, dlo, dhi, L.ax, L.ay, L.az, bt);
+      e = st.c + om * mg_inv_bt(L, xy, z, inv_int, bt) * (o[0] - Ae);
+    }
     if (LAST) arz.add(o[0], e);
     return e;
   };
@@ -282,7 +382,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_post2(MgView<T> L, double* part
   for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
     arz = Acc<T>();
-    march_direct<T, T, MTX, MTY, VX, 1, 1, MG_D>(L.g, s, smem, hsrc, osrc, emit, post);
+    march_direct<T, T, MTX, MTY, VX, NH, NO, MG_D>(L.g, s, smem, hsrc, osrc, emit, post);
     if (LAST) {
       double v[1] = {arz.value()};
       tile_partials<1, MTX * MTY>(v, part, t);
@@ -311,25 +411,47 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_post2(MgView<T> L, double* part
 
 // ------------------------------------------------------ coarsest-level solve
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
-  v = warp_sum(v);
-  __syncthreads();                 // red[] may still be read from the previous call
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
+// Sum over a warp with every lane receiving the total.  The butterfly adds
+// the same two partial sums in every lane of a pair, so all lanes end with
+// bitwise the same value (addition is commutative).
+__device__ __forceinline__ double warp_sum_all(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Barrier of the first nw warps of the block (named barrier 1; one warp:
+// a warp barrier).
+__device__ __forceinline__ void warps_sync(int nw) {
+  if (nw == 1) __syncwarp();
+  else asm volatile("bar.sync 1, %0;\n" ::"r"(nw * 32) : "memory");
+}
+
+// Sum over the first nw warps, the same value in every thread (fixed order).
+__device__ __forceinline__ double warps_sum(double v, int nw, double* red) {
+  v = warp_sum_all(v);
+  if (nw == 1) return v;
+  warps_sync(nw);                  // red[] may still be read from the previous sum
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  warps_sync(nw);
   double s = 0.0;
-  for (int i = 0; i < nw; ++i) s += red[i];   // same order in every thread
+  for (int i = 0; i < nw; ++i) s += red[i];
   return s;
 }
 
-// Conjugate gradients on the coarsest level, FP64, one block, one cell per
-// thread (n <= MG_MAX_COARSE <= blockDim.x), to a relative residual of 1e-12.
-// With no electrode the level is singular: the right-hand side and the
-// solution are projected to zero mean.  Every thread of the block calls it.
+// Jacobi-preconditioned conjugate gradients on the coarsest level, FP64, one
+// cell per thread in the first ceil(n / 32) warps of the block (the other
+// warps return at once; the caller's next __syncthreads joins them), to a
+// relative residual of 1e-12.  The diagonal scaling matters where a
+// permittivity field makes the coarse operator's diagonal vary by orders of
+// magnitude.  With no electrode the level is singular: the right-hand side and
+// the solution are projected to zero mean.
 template <typename T>
 __device__ __forceinline__ void mg_coarse_solve(const MgView<T>& C, const T* cf, T* ce, int singular, double* ps,
                                                 double* red) {
   const int n = (int)C.g.n, tid = threadIdx.x;
+  const int nw = (n + 31) >> 5;
+  if (tid >= nw * 32) return;
   const bool on = tid < n;
   int x = 0, y = 0, z = 0;
   if (on) {
@@ -349,39 +471,58 @@ __device__ __forceinline__ void mg_coarse_solve(const MgView<T>& C, const T* cf,
   const double ax = C.ax, ay = C.ay, az = C.az;
   const int dlo = (on && zb < 0) ? (int)C.tlo[xy] : 0;
   const int dhi = (on && za < 0) ? (int)C.thi[xy] : 0;
+  // face weights: 1, or the harmonic mean of the cells' eps (electrode: 2 eps_c)
+  double wxm = 1.0, wxp = 1.0, wym = 1.0, wyp = 1.0, wzm = 1.0, wzp = 1.0, wd = 1.0;
+  if (C.eps && on) {
+    const double ec = (double)C.eps[tid];
+    auto hm = [&](int nb) { const double en = (double)C.eps[nb]; return 2.0 * ec * en / (ec + en); };
+    wxm = hm(xm);
+    wxp = hm(xp);
+    wym = hm(ym);
+    wyp = hm(yp);
+    wzm = zm >= 0 ? hm(zm) : 0.0;
+    wzp = zp >= 0 ? hm(zp) : 0.0;
+    wd = ec;
+  }
   auto apply = [&](const double* v) -> double {
     const double c = v[tid];
     double sz = 0.0;
-    if (zm >= 0) sz += c - v[zm];
-    else if (dlo) sz += 2.0 * c;
-    if (zp >= 0) sz += c - v[zp];
-    else if (dhi) sz += 2.0 * c;
-    return ax * ((c - v[xm]) + (c - v[xp])) + ay * ((c - v[ym]) + (c - v[yp])) + az * sz;
+    if (zm >= 0) sz += wzm * (c - v[zm]);
+    else if (dlo) sz += 2.0 * wd * c;
+    if (zp >= 0) sz += wzp * (c - v[zp]);
+    else if (dhi) sz += 2.0 * wd * c;
+    return ax * (wxm * (c - v[xm]) + wxp * (c - v[xp])) + ay * (wym * (c - v[ym]) + wyp * (c - v[yp])) + az * sz;
   };
+  double dg = ax * (wxm + wxp) + ay * (wym + wyp);
+  dg += az * ((zm >= 0 ? wzm : (dlo ? 2.0 * wd : 0.0)) + (zp >= 0 ? wzp : (dhi ? 2.0 * wd : 0.0)));
+  const double dinv = (on && dg > 0.0) ? 1.0 / dg : 0.0;
   double b = on ? (double)cf[tid] : 0.0;
-  if (singular) b -= block_sum(b, red) / n;
+  if (singular) b -= warps_sum(b, nw, red) / n;
   double xv = 0.0, r = b;
-  double rr = block_sum(r * r, red);
-  const double bb = rr;
+  const double bb = warps_sum(r * r, nw, red);
   if (bb > 0.0) {
-    double p = r;
+    double zv = r * dinv;
+    double p = zv;
+    double rz = warps_sum(r * zv, nw, red);
     for (int it = 0; it < 4 * n + 20; ++it) {
-      __syncthreads();             // ps[] may still be read from the previous iteration
+      warps_sync(nw);              // ps[] may still be read from the previous iteration
       if (on) ps[tid] = p;
-      __syncthreads();
+      warps_sync(nw);
       const double q = on ? apply(ps) : 0.0;
-      const double pq = block_sum(p * q, red);
+      const double pq = warps_sum(p * q, nw, red);
       if (!(pq > 0.0)) break;
-      const double a = rr / pq;
+      const double a = rz / pq;
       xv += a * p;
       r -= a * q;
-      const double rrn = block_sum(r * r, red);
+      const double rrn = warps_sum(r * r, nw, red);
       if (rrn <= 1e-24 * bb) break;
-      p = r + (rrn / rr) * p;
-      rr = rrn;
+      zv = r * dinv;
+      const double rzn = warps_sum(r * zv, nw, red);
+      p = zv + (rzn / rz) * p;
+      rz = rzn;
     }
   }
-  if (singular) xv -= block_sum(on ? xv : 0.0, red) / n;
+  if (singular) xv -= warps_sum(on ? xv : 0.0, nw, red) / n;
   if (on) ce[tid] = (T)xv;
 }
 
@@ -395,33 +536,72 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_coarse(MgView<T> C, int si
 
 // ------------------------------------------------------------ the V-cycle tail
 
-// A v at cell c of a small level, neighbours read from global memory.
+// Column walk of a small level: thread t of the block takes the columns t,
+// t + blockDim.x, ... of the nx x ny plane and walks them along z, so the
+// in-plane neighbour offsets, the face masks and the boundary diagonals are
+// formed once per column instead of from the linear index at every cell.
+struct TailCol {
+  int xy;                   // the column (y nx + x)
+  int dxm, dxp, dym, dyp;   // offsets of the in-plane neighbours (periodic wrap)
+  int dlo, dhi;             // electrode masks of the column's z faces
+};
+
+template <typename T, class Body>
+__device__ __forceinline__ void tail_cols(const MgView<T>& L, Body body) {
+  const int nx = L.g.nx, ny = L.g.ny, nxy = (int)L.g.nxy;
+  for (int col = threadIdx.x; col < nxy; col += blockDim.x) {
+    const int y = col / nx, x = col - y * nx;
+    TailCol o;
+    o.xy = col;
+    o.dxm = x == 0 ? nx - 1 : -1;
+    o.dxp = x == nx - 1 ? -(nx - 1) : 1;
+    o.dym = y == 0 ? (ny - 1) * nx : -nx;
+    o.dyp = y == ny - 1 ? -(ny - 1) * nx : nx;
+    o.dlo = L.g.periodic_z ? 0 : (int)L.tlo[col];
+    o.dhi = L.g.periodic_z ? 0 : (int)L.thi[col];
+    body(o, x, y);
+  }
+}
+
+// (A v) at plane z of a column and 1/diag there: the same operator, face
+// order and diagonal as the sweep kernels (per-direction 1/h^2; with eps the
+// harmonic-mean face weights and the precomputed 1/diag).
 template <typename T>
-__device__ __forceinline__ T tail_apply(const MgView<T>& L, const T* v, int c, T& inv) {
-  const int nx = L.g.nx, ny = L.g.ny, nz = L.g.nz, nxy = (int)L.g.nxy;
-  const int x = c % nx, y = (c / nx) % ny, z = c / nxy;
-  const int r0 = c - x, p0 = c - y * nx - x;
+__device__ __forceinline__ T col_apply(const MgView<T>& L, const T* v, const TailCol& o, int z, T& inv) {
+  const int nz = L.g.nz, nxy = (int)L.g.nxy;
+  const int c = z * nxy + o.xy;
   const T vc = v[c];
-  const T sx = (vc - v[r0 + (x == 0 ? nx - 1 : x - 1)]) + (vc - v[r0 + (x == nx - 1 ? 0 : x + 1)]);
-  const T sy = (vc - v[p0 + (y == 0 ? ny - 1 : y - 1) * nx + x]) + (vc - v[p0 + (y == ny - 1 ? 0 : y + 1) * nx + x]);
+  const int zm = z > 0 ? c - nxy : (L.g.periodic_z ? c + (nz - 1) * nxy : -1);
+  const int zp = z < nz - 1 ? c + nxy : (L.g.periodic_z ? c - (nz - 1) * nxy : -1);
+  if (L.eps) {
+    const T ec = L.eps[c];
+    auto face = [&](int nb) { return hmean2(ec, L.eps[nb]) * (vc - v[nb]); };
+    const T sx = face(c + o.dxm) + face(c + o.dxp);
+    const T sy = face(c + o.dym) + face(c + o.dyp);
+    T sz = T(0);
+    if (zm >= 0) sz += face(zm);
+    else if (o.dlo) sz += T(2) * ec * vc;
+    if (zp >= 0) sz += face(zp);
+    else if (o.dhi) sz += T(2) * ec * vc;
+    inv = L.invd[c];
+    return L.ax * sx + L.ay * sy + L.az * sz;
+  }
+  const T sx = (vc - v[c + o.dxm]) + (vc - v[c + o.dxp]);
+  const T sy = (vc - v[c + o.dym]) + (vc - v[c + o.dyp]);
   T sz = T(0);
-  const int xy = y * nx + x;
   int cz = 2;
-  if (z > 0) sz += vc - v[c - nxy];
-  else if (L.g.periodic_z) sz += vc - v[c + (nz - 1) * nxy];
-  else { cz += 2 * (int)L.tlo[xy] - 1; if (L.tlo[xy]) sz += T(2) * vc; }
-  if (z < nz - 1) sz += vc - v[c + nxy];
-  else if (L.g.periodic_z) sz += vc - v[c - (nz - 1) * nxy];
-  else { cz += 2 * (int)L.thi[xy] - 1; if (L.thi[xy]) sz += T(2) * vc; }
-  if (L.g.periodic_z) cz = 2;
+  if (zm >= 0) sz += vc - v[zm];
+  else { cz += 2 * o.dlo - 1; if (o.dlo) sz += T(2) * vc; }
+  if (zp >= 0) sz += vc - v[zp];
+  else { cz += 2 * o.dhi - 1; if (o.dhi) sz += T(2) * vc; }
   inv = T(1) / (T(2) * L.ax + T(2) * L.ay + T(cz) * L.az);
   return L.ax * sx + L.ay * sy + L.az * sz;
 }
 
 // The V-cycle below level k0 (all levels small) in one block: per level two
-// pre-smoothing sweeps from zero, residual and restriction, the coarsest
-// solve, then prolongation and two post-smoothing sweeps, each phase a loop
-// over the level's cells followed by a block barrier.  Same operators,
+// pre-smoothing sweeps from zero, the residual, its restriction, the coarsest
+// solve, then prolongation and two post-smoothing sweeps, each phase a walk
+// over the level's columns followed by a block barrier.  Same operators,
 // weights and transfers as the one-kernel-per-phase path above it.  Every
 // level's f, e, e_tmp live in shared memory (t.off[k]: offset of level k's
 // three arrays, in elements); the first level's f comes from and its e goes
@@ -448,34 +628,49 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int sing
     const MgView<T>& L = t.lv[k];
     const MgView<T>& C = t.lv[k + 1];
     T *f = F(k), *e = E(k), *et = ET(k);
-    const int n = (int)L.g.n;
-    for (int c = threadIdx.x; c < n; c += nt) {
-      T inv;
-      tail_apply(L, f, c, inv);                        // only the diagonal is needed here
-      et[c] = om1 * inv * f[c];
-    }
+    const int nxy = (int)L.g.nxy, nz = L.g.nz;
+    tail_cols(L, [&](const TailCol& o, int, int) {
+      for (int z = 0; z < nz; ++z) {
+        T inv;
+        col_apply(L, f, o, z, inv);                       // only the diagonal is needed here
+        const int c = z * nxy + o.xy;
+        et[c] = om1 * inv * f[c];
+      }
+    });
     __syncthreads();
-    for (int c = threadIdx.x; c < n; c += nt) {
-      T inv;
-      const T Ae = tail_apply(L, et, c, inv);
-      e[c] = et[c] + om2 * inv * (f[c] - Ae);
-    }
+    tail_cols(L, [&](const TailCol& o, int, int) {
+      for (int z = 0; z < nz; ++z) {
+        T inv;
+        const T Ae = col_apply(L, et, o, z, inv);
+        const int c = z * nxy + o.xy;
+        e[c] = et[c] + om2 * inv * (f[c] - Ae);
+      }
+    });
     __syncthreads();
-    const int nc = (int)C.g.n;
+    // the residual (into e_tmp, free again), then the sum of each coarse
+    // cell's children in the order dz, dy, dx
+    tail_cols(L, [&](const TailCol& o, int, int) {
+      for (int z = 0; z < nz; ++z) {
+        T inv;
+        const T Ae = col_apply(L, e, o, z, inv);
+        const int c = z * nxy + o.xy;
+        et[c] = f[c] - Ae;
+      }
+    });
+    __syncthreads();
     const T scale = T(1) / T(L.fx * L.fy * L.fz);
     T* fc = F(k + 1);
-    for (int cc = threadIdx.x; cc < nc; cc += nt) {
-      const int X = cc % C.g.nx, Y = (cc / C.g.nx) % C.g.ny, Z = cc / (int)C.g.nxy;
-      T acc = T(0);
-      for (int dz = 0; dz < L.fz; ++dz)
-        for (int dy = 0; dy < L.fy; ++dy)
-          for (int dx = 0; dx < L.fx; ++dx) {
-            const int c = ((Z * L.fz + dz) * L.g.ny + Y * L.fy + dy) * L.g.nx + X * L.fx + dx;
-            T inv;
-            acc += f[c] - tail_apply(L, e, c, inv);
-          }
-      fc[cc] = acc * scale;
-    }
+    const int ncxy = (int)C.g.nxy, ncz = C.g.nz;
+    tail_cols(C, [&](const TailCol& o, int X, int Y) {
+      for (int Z = 0; Z < ncz; ++Z) {
+        T acc = T(0);
+        for (int dz = 0; dz < L.fz; ++dz)
+          for (int dy = 0; dy < L.fy; ++dy)
+            for (int dx = 0; dx < L.fx; ++dx)
+              acc += et[((Z * L.fz + dz) * L.g.ny + Y * L.fy + dy) * L.g.nx + X * L.fx + dx];
+        fc[Z * ncxy + o.xy] = acc * scale;
+      }
+    });
     __syncthreads();
   }
   mg_coarse_solve(t.lv[t.nl - 1], F(t.nl - 1), E(t.nl - 1), singular, ps, red);
@@ -485,24 +680,30 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int sing
     const MgView<T>& C = t.lv[k + 1];
     T *f = F(k), *e = E(k), *et = ET(k);
     const T* ec = E(k + 1);
-    const int n = (int)L.g.n;
-    for (int c = threadIdx.x; c < n; c += nt) {
-      const int x = c % L.g.nx, y = (c / L.g.nx) % L.g.ny, z = c / (int)L.g.nxy;
-      e[c] += ec[((z >> (L.fz - 1)) * C.g.ny + (y >> (L.fy - 1))) * C.g.nx + (x >> (L.fx - 1))];
-    }
+    const int nxy = (int)L.g.nxy, nz = L.g.nz;
+    tail_cols(L, [&](const TailCol& o, int x, int y) {
+      const int pxy = (y >> (L.fy - 1)) * C.g.nx + (x >> (L.fx - 1));
+      for (int z = 0; z < nz; ++z) e[z * nxy + o.xy] += ec[(z >> (L.fz - 1)) * (int)C.g.nxy + pxy];
+    });
     __syncthreads();
-    for (int c = threadIdx.x; c < n; c += nt) {
-      T inv;
-      const T Ae = tail_apply(L, e, c, inv);
-      et[c] = e[c] + om2 * inv * (f[c] - Ae);
-    }
+    tail_cols(L, [&](const TailCol& o, int, int) {
+      for (int z = 0; z < nz; ++z) {
+        T inv;
+        const T Ae = col_apply(L, e, o, z, inv);
+        const int c = z * nxy + o.xy;
+        et[c] = e[c] + om2 * inv * (f[c] - Ae);
+      }
+    });
     __syncthreads();
     T* eo = k == 0 ? t.lv[0].e : e;                    // the first level's result goes to global memory
-    for (int c = threadIdx.x; c < n; c += nt) {
-      T inv;
-      const T Ae = tail_apply(L, et, c, inv);
-      eo[c] = et[c] + om1 * inv * (f[c] - Ae);
-    }
+    tail_cols(L, [&](const TailCol& o, int, int) {
+      for (int z = 0; z < nz; ++z) {
+        T inv;
+        const T Ae = col_apply(L, et, o, z, inv);
+        const int c = z * nxy + o.xy;
+        eo[c] = et[c] + om1 * inv * (f[c] - Ae);
+      }
+    });
     __syncthreads();
   }
 }
@@ -533,55 +734,67 @@ static int mg_grid(K kernel, size_t bytes, long long ntiles, int& res) {
   return (int)std::min<long long>(ntiles, std::min(res, MAX_GRID));
 }
 
-template <typename T, int VX>
+template <typename T, int VX, bool E>
 static void pre_v(const LaunchCfg& L, const MgView<T>& lv, Scalars* S) {
   static bool f = false;
   static int res = 0;
-  const size_t bytes = MgPipeD0<T, VX>::bytes();
-  smem_once(k_mg_pre<T, VX>, bytes, f);
-  const int grid = mg_grid(k_mg_pre<T, VX>, bytes, lv.mc.ntiles, res);
-  k_mg_pre<T, VX><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, S);
+  const size_t bytes = MgPipeD0<T, VX, E>::bytes();
+  smem_once(k_mg_pre<T, VX, E>, bytes, f);
+  const int grid = mg_grid(k_mg_pre<T, VX, E>, bytes, lv.mc.ntiles, res);
+  k_mg_pre<T, VX, E><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, S);
 }
-template <typename T, int VX>
+template <typename T, int VX, bool E>
 static void rr_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
   static bool f = false;
   static int res = 0;
-  const size_t bytes = MgPipeD<T, VX>::bytes();
-  smem_once(k_mg_rr<T, VX>, bytes, f);
-  const int grid = mg_grid(k_mg_rr<T, VX>, bytes, lv.mc.ntiles, res);
-  k_mg_rr<T, VX><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, cv, S);
+  const size_t bytes = MgPipeR<T, VX, E>::bytes();
+  smem_once(k_mg_rr<T, VX, E>, bytes, f);
+  const int grid = mg_grid(k_mg_rr<T, VX, E>, bytes, lv.mc.ntiles, res);
+  k_mg_rr<T, VX, E><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, cv, S);
 }
-template <typename T, int VX>
+template <typename T, int VX, bool E>
 static void post1_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
   static bool f = false;
   static int res = 0;
-  const size_t bytes = MgPipeP<T, VX>::bytes();
-  smem_once(k_mg_post1<T, VX>, bytes, f);
-  const int grid = mg_grid(k_mg_post1<T, VX>, bytes, lv.mc.ntiles, res);
-  k_mg_post1<T, VX><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, cv, S);
+  const size_t bytes = MgPipeP<T, VX, E>::bytes();
+  smem_once(k_mg_post1<T, VX, E>, bytes, f);
+  const int grid = mg_grid(k_mg_post1<T, VX, E>, bytes, lv.mc.ntiles, res);
+  k_mg_post1<T, VX, E><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, cv, S);
 }
-template <typename T, bool LAST, int VX>
+template <typename T, bool LAST, int VX, bool E>
 static void post2_v(const LaunchCfg& L, const MgView<T>& lv, double* part, Scalars* S) {
   static bool f = false;
   static int res = 0;
-  const size_t bytes = MgPipeD<T, VX>::bytes();
-  smem_once(k_mg_post2<T, LAST, VX>, bytes, f);
-  const int grid = mg_grid(k_mg_post2<T, LAST, VX>, bytes, lv.mc.ntiles, res);
-  k_mg_post2<T, LAST, VX><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, part, S);
+  const size_t bytes = MgPipeD<T, VX, E>::bytes();
+  smem_once(k_mg_post2<T, LAST, VX, E>, bytes, f);
+  const int grid = mg_grid(k_mg_post2<T, LAST, VX, E>, bytes, lv.mc.ntiles, res);
+  k_mg_post2<T, LAST, VX, E><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, part, S);
 }
 
 constexpr int vec_of(size_t bytes) { return (int)(16 / bytes); }
 
 template <typename T>
 void launch_mg_pre(const LaunchCfg& L, const MgView<T>& lv, Scalars* S) {
-  if (lv.mc.vx > 1) pre_v<T, vec_of(sizeof(T))>(L, lv, S);
-  else pre_v<T, 1>(L, lv, S);
+  constexpr int V = vec_of(sizeof(T));
+  if (lv.eps) {
+    if (lv.mc.vx > 1) pre_v<T, V, true>(L, lv, S);
+    else pre_v<T, 1, true>(L, lv, S);
+  } else {
+    if (lv.mc.vx > 1) pre_v<T, V, false>(L, lv, S);
+    else pre_v<T, 1, false>(L, lv, S);
+  }
 }
 
 template <typename T>
 void launch_mg_rr(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
-  if (lv.mc.vx > 1) rr_v<T, vec_of(sizeof(T))>(L, lv, cv, S);
-  else rr_v<T, 1>(L, lv, cv, S);
+  constexpr int V = vec_of(sizeof(T));
+  if (lv.eps) {
+    if (lv.mc.vx > 1) rr_v<T, V, true>(L, lv, cv, S);
+    else rr_v<T, 1, true>(L, lv, cv, S);
+  } else {
+    if (lv.mc.vx > 1) rr_v<T, V, false>(L, lv, cv, S);
+    else rr_v<T, 1, false>(L, lv, cv, S);
+  }
 }
 
 template <typename T>
@@ -592,20 +805,85 @@ void launch_mg_coarse(const LaunchCfg& L, const MgView<T>& cv, int singular, Sca
 
 template <typename T>
 void launch_mg_post1(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
-  if (lv.mc.vx > 1) post1_v<T, vec_of(sizeof(T))>(L, lv, cv, S);
-  else post1_v<T, 1>(L, lv, cv, S);
+  constexpr int V = vec_of(sizeof(T));
+  if (lv.eps) {
+    if (lv.mc.vx > 1) post1_v<T, V, true>(L, lv, cv, S);
+    else post1_v<T, 1, true>(L, lv, cv, S);
+  } else {
+    if (lv.mc.vx > 1) post1_v<T, V, false>(L, lv, cv, S);
+    else post1_v<T, 1, false>(L, lv, cv, S);
+  }
+}
+
+template <typename T, bool E>
+static void post2_e(const LaunchCfg& L, const MgView<T>& lv, int last, double* part, Scalars* S) {
+  constexpr int V = vec_of(sizeof(T));
+  if (last) {
+    if (lv.mc.vx > 1) post2_v<T, true, V, E>(L, lv, part, S);
+    else post2_v<T, true, 1, E>(L, lv, part, S);
+  } else {
+    if (lv.mc.vx > 1) post2_v<T, false, V, E>(L, lv, part, S);
+    else post2_v<T, false, 1, E>(L, lv, part, S);
+  }
 }
 
 template <typename T>
 void launch_mg_post2(const LaunchCfg& L, const MgView<T>& lv, int last, double* part, Scalars* S) {
-  constexpr int V = vec_of(sizeof(T));
-  if (last) {
-    if (lv.mc.vx > 1) post2_v<T, true, V>(L, lv, part, S);
-    else post2_v<T, true, 1>(L, lv, part, S);
-  } else {
-    if (lv.mc.vx > 1) post2_v<T, false, V>(L, lv, part, S);
-    else post2_v<T, false, 1>(L, lv, part, S);
+  if (lv.eps) post2_e<T, true>(L, lv, last, part, S);
+  else post2_e<T, false>(L, lv, last, part, S);
+}
+
+// ------------------------------------------------ permittivity of the levels
+
+// Coarse cell permittivity: the mean of its children's.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mg_eps_restrict(MgView<T> F, MgView<T> C, T* __restrict__ ceps) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const T scale = T(1) / T(F.fx * F.fy * F.fz);
+  for (long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x; cc < C.g.n; cc += stride) {
+    const int X = (int)(cc % C.g.nx), Y = (int)((cc / C.g.nx) % C.g.ny), Z = (int)(cc / C.g.nxy);
+    T acc = T(0);
+    for (int dz = 0; dz < F.fz; ++dz)
+      for (int dy = 0; dy < F.fy; ++dy)
+        for (int dx = 0; dx < F.fx; ++dx)
+          acc += F.eps[((long long)(Z * F.fz + dz) * F.g.ny + Y * F.fy + dy) * F.g.nx + X * F.fx + dx];
+    ceps[cc] = acc * scale;
   }
+}
+
+// 1/diag of a level's operator with cell permittivities: the face weights
+// (harmonic means; an electrode face 2 eps_c) times 1/h^2 per direction.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mg_invdiag(MgView<T> L, T* __restrict__ invd) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int nx = L.g.nx, ny = L.g.ny, nz = L.g.nz;
+  const long long nxy = L.g.nxy;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < L.g.n; c += stride) {
+    const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / nxy);
+    const long long r0 = c - x, p0 = c - (long long)y * nx - x;
+    const T ec = L.eps[c];
+    const T sx = hmean2(ec, L.eps[r0 + (x == 0 ? nx - 1 : x - 1)]) + hmean2(ec, L.eps[r0 + (x == nx - 1 ? 0 : x + 1)]);
+    const T sy = hmean2(ec, L.eps[p0 + (long long)(y == 0 ? ny - 1 : y - 1) * nx + x]) +
+                 hmean2(ec, L.eps[p0 + (long long)(y == ny - 1 ? 0 : y + 1) * nx + x]);
+    const long long xy = (long long)y * nx + x;
+    T sz = T(0);
+    if (z > 0) sz += hmean2(ec, L.eps[c - nxy]);
+    else if (L.g.periodic_z) sz += hmean2(ec, L.eps[c + (nz - 1) * nxy]);
+    else if (L.tlo[xy]) sz += T(2) * ec;
+    if (z < nz - 1) sz += hmean2(ec, L.eps[c + nxy]);
+    else if (L.g.periodic_z) sz += hmean2(ec, L.eps[c - (nz - 1) * nxy]);
+    else if (L.thi[xy]) sz += T(2) * ec;
+    invd[c] = T(1) / (L.ax * sx + L.ay * sy + L.az * sz);
+  }
+}
+
+template <typename T>
+void launch_mg_eps_level(const LaunchCfg& L, const MgView<T>& fine, const MgView<T>& coarse, T* ceps, T* cinvd) {
+  const int g1 = (int)std::max<long long>(1, std::min<long long>((coarse.g.n + 255) / 256, 4096));
+  k_mg_eps_restrict<T><<<g1, 256, 0, L.stream>>>(fine, coarse, ceps);
+  MgView<T> c = coarse;
+  c.eps = ceps;
+  k_mg_invdiag<T><<<g1, 256, 0, L.stream>>>(c, cinvd);
 }
 
 template <typename T>
@@ -618,10 +896,10 @@ void launch_mg_tail(const LaunchCfg& L, const MgTail<T>& t, int singular, Scalar
 template <typename T>
 int mg_blocks_per_sm() {
   constexpr int V = vec_of(sizeof(T));
-  allow_smem(k_mg_post1<T, V>, MgPipeP<T, V>::bytes());
+  allow_smem(k_mg_post1<T, V, false>, MgPipeP<T, V>::bytes());
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mg_post1<T, V>, MTX * MTY, MgPipeP<T, V>::bytes()) !=
-      cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mg_post1<T, V, false>, MTX * MTY,
+                                                    MgPipeP<T, V>::bytes()) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
@@ -635,6 +913,7 @@ int mg_blocks_per_sm() {
   template void launch_mg_tail<T>(const LaunchCfg&, const MgTail<T>&, int, Scalars*);            \
   template void launch_mg_post1<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*); \
   template void launch_mg_post2<T>(const LaunchCfg&, const MgView<T>&, int, double*, Scalars*);        \
+  template void launch_mg_eps_level<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, T*, T*);  \
   template int mg_blocks_per_sm<T>();
 
 PF_MG_INSTANTIATE(float)

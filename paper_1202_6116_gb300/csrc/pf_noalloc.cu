@@ -1,18 +1,23 @@
 // pf_solve_potential_noalloc: the Jacobi-PCG Poisson solve for callers that
 // cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is
-// being captured or replayed around it, real-time loops that must not touch
-// the allocator, and hosts whose memory pool is fixed up front.  This entry
-// point takes the inputs and the output from the caller and keeps every
-// intermediate vector (r, p, q, face masks, reduction partials, solver
-// scalars) in one file-scope __device__ array of PF_NOALLOC_SCRATCH_BYTES.
-// Every GPU that loads the library holds that array until the process exits.
+// Some callers cannot call cudaMalloc: real-time loops that must not stall on
+// the allocator (cudaMalloc and cudaFree can synchronize the device), and
+// processes whose device memory is reserved up front by another allocator
+// (a fixed pool, or a framework that owns every byte).  This entry point takes
+// the inputs and the output from the caller and keeps every intermediate
+// vector (r, p, q, face masks, reduction partials, solver scalars) in one
+// file-scope __device__ array of PF_NOALLOC_SCRATCH_BYTES.  Every GPU that
+// loads the library holds that array until the process exits.
 //
-// The array's name is only a host-side stand-in in host code, so the device
-// address is looked up with cudaGetSymbolAddress once per device (with that
-// device current) on the first call made on it, and passed to the kernels.
-// Calls share the array: concurrent or overlapping calls race.
+// The call blocks (it polls the solver's convergence flag and reads its
+// scalars back), so it must not be made while its stream, or the legacy
+// stream, is being captured into a CUDA graph: it checks and refuses.
+//
+// The array's name is only a host-side stand-in in host code, so every call
+// looks up the device address with cudaGetSymbolAddress (with the caller's
+// device current) and passes it to the kernels.  Calls share the array:
+// concurrent or overlapping calls race.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,17 +31,25 @@
 namespace {
 
 constexpr size_t kScratchBytes = PF_NOALLOC_SCRATCH_BYTES;
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
-
-void* g_scratch_dev[kMaxDevices];          // device address of g_noalloc_scratch, per device
 
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
 pf_status fail(pf_status st, const char* msg) {
   pf::set_global_error(msg);
   return st;
+}
+
+// Is p device (or managed) memory that device dev can address as its own?
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 struct Layout {
@@ -178,6 +191,8 @@ pf_status solve(const pf_params* prm, cudaStream_t st, char* base, const Layout&
     info->status = result;
     info->kernel_launches = launches + (singular ? 1 : 0);
     info->graph_steps = 0;
+    info->max_iters = host.max_iters;
+    info->solves = host.solves;
   }
   return result;
 }
@@ -190,6 +205,20 @@ pf_status pf_solve_potential_noalloc(const pf_params* params, void* cuda_stream,
                                      const int8_t* type_lo, const double* volt_lo, const int8_t* type_hi,
                                      const double* volt_hi, pf_step_info* info) {
   if (!params) return fail(PF_ERR_ARG, "params is NULL");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // The solve synchronizes the stream and copies from host buffers: neither
+  // is legal while the stream (or the legacy stream) is being captured, so
+  // this is checked before any other CUDA call.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const cudaError_t ce = cudaStreamIsCapturing(st, &cap);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    pf::set_global_error("the allocation-free solve cannot run during stream capture (it blocks)",
+                         cudaGetErrorString(ce));
+    return PF_ERR_STATE;
+  }
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(PF_ERR_STATE, "the allocation-free solve cannot run while its stream is being captured (it blocks)");
   if (params->solver != PF_PCG_JACOBI || params->has_eps)
     return fail(PF_ERR_ARG, "the allocation-free solve supports solver PF_PCG_JACOBI with has_eps = 0");
   if (pf_workspace_bytes(params) == 0) return fail(PF_ERR_ARG, "invalid parameters");
@@ -216,14 +245,13 @@ pf_status pf_solve_potential_noalloc(const pf_params* params, void* cuda_stream,
   }
   int dev = 0;
   NA_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return fail(PF_ERR_ARG, "device ordinal out of range");
-  if (!g_scratch_dev[dev]) {
-    void* ptr = nullptr;
-    NA_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-    g_scratch_dev[dev] = ptr;
-  }
-  char* base = (char*)g_scratch_dev[dev];
-  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (!on_device(P, dev) || !on_device(phi, dev))
+    return fail(PF_ERR_ARG, "P and phi must be device (or managed) memory of the current device");
+  // Device address of the array in this device's context, looked up on every
+  // call (cheap, allocates nothing, and stays right across cudaDeviceReset).
+  void* ptr = nullptr;
+  NA_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+  char* base = (char*)ptr;
   if (params->precision == PF_FP32)
     return solve<float>(params, st, base, Ly, (const float*)P, (float*)phi, type_lo, volt_lo, type_hi, volt_hi,
                         singular, info);

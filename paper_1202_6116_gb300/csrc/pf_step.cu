@@ -12,6 +12,12 @@
 //           (Eq. TDGL with Eqs. F_bulk, dF_grad/dP, F_elec; Section Time Integration).
 //           Planes z >= zair are air: P = 0 there, and the film's top plane has
 //           no z+ neighbour in the Laplacian (free surface).
+//           COMP = true (FP32 forward Euler): the state is the compensated
+//           pair P + P_lo, P_lo the part of the exact sum that the FP32 P
+//           cannot hold (a second FP32 field, own cells only, updated in
+//           place).  The increment dt R is added to the pair by TwoSum, so
+//           increments far below half an FP32 ulp of P still accumulate
+//           instead of being rounded away step after step.
 //           CORR = true is the corrector of the predictor-corrector scheme: P is
 //           the predicted state P^p, and the output overwrites the state P_n it
 //           started from with (P_n + P^p + dt R(P^p)) / 2 = P_n + dt (R(P_n) +
@@ -20,7 +26,7 @@
 // Both read P (3 components) and phi with their 6 neighbours; the neighbours
 // come straight from the staged planes (march_direct).  Algorithmic traffic
 // per cell: k_rhs reads 4 words (5 with a compensated start) and writes 1;
-// k_tdgl reads 4 and writes 3.
+// k_tdgl reads 4 and writes 3 (compensated state: reads 7, writes 6).
 #include "pf_internal.h"
 #include "pf_march.cuh"
 #include "pf_rng.cuh"
@@ -185,9 +191,26 @@ struct P3 {
   T x, y, z;
 };
 
-template <typename T, bool CORR, bool NOISE, int VX>
-__global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __restrict__ P, T* __restrict__ Pn,
-                                                  const T* __restrict__ phi, Coef<T> k, Scalars* S, MarchCfg mc) {
+// Compensated state of one cell after a step: the new P and its remainder.
+template <typename T>
+struct P6 {
+  T x, y, z, lx, ly, lz;
+};
+
+// a + b = s + e exactly (TwoSum, Knuth): no condition on the magnitudes.
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T& s, T& e) {
+  s = a + b;
+  const T bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <typename T, bool CORR, bool NOISE, int VX, bool COMP = false>
+__global__ void __launch_bounds__(MTX* MTY, 2) k_tdgl(Geo g, Bc<T> bc, const T* __restrict__ P, T* __restrict__ Pn,
+                                                  const T* __restrict__ phi, Coef<T> k, Scalars* S, MarchCfg mc,
+                                                  T* __restrict__ Plo) {
+  static_assert(!(COMP && CORR), "the compensated state is a forward-Euler mode");
+  using Out = typename std::conditional<COMP, P6<T>, P3<T>>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   const T h = T(0.5), ih = T(g.ih), ih2 = T(g.ih2);
@@ -196,7 +219,8 @@ __global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __r
   const T* hsrc[4] = {P, P + g.n, P + 2 * g.n, phi};
   const T* osrc[1] = {nullptr};
   TileGeo<MTX, MTY, VX> s;
-  auto emit = [&](int xy, int z, const Stencil7<Raw<T, 4>>& st, const T (&)[1], bool) -> P3<T> {
+  T lov[3][VX];                      // remainders of the own vector (COMP), loaded with its first cell
+  auto emit = [&](int xy, int z, const Stencil7<Raw<T, 4>>& st, const T (&)[1], bool) -> Out {
     // E = -grad phi from face values (mean inside, V at an electrode, phi_cell at an open face)
     const T fc = st.c.v[3];
     T E[3];
@@ -209,7 +233,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __r
     else fhi = bc.thi[xy] ? bc.vhi[xy] : fc;
     E[2] = -(fhi - flo) * ih;
     T p[3] = {st.c.v[0], st.c.v[1], st.c.v[2]};
-    T out[3];
+    T inc[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int j = (i + 1) % 3, l = (i + 2) % 3;
@@ -223,17 +247,37 @@ __global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __r
       if (st.zb >= 0) lap += st.zm.v[i] - p[i];
       if (st.za >= 0 && (z + 1 < g.zair || g.zair == g.nz)) lap += st.zp.v[i] - p[i];   // free surface under air
       lap *= ih2;
-      out[i] = p[i] + k.dtL * (-hi + k.g * lap + E[i]);
+      inc[i] = k.dtL * (-hi + k.g * lap + E[i]);
     }
-    if constexpr (NOISE && !CORR) {
-      T gz[3];
-      gauss3<T>((unsigned long long)z * g.nxy + xy, nstep, k.seed, gz);
+    T gz[3] = {T(0), T(0), T(0)};
+    if constexpr (NOISE && !CORR) gauss3<T>((unsigned long long)z * g.nxy + xy, nstep, k.seed, gz);
+    if constexpr (COMP) {
+      const int iv = xy - s.xy;                     // index inside the own vector
+      if (iv == 0) {
+        const long long c0 = (long long)z * g.nxy + s.xy;
+        load_n<T, VX>(Plo + c0, lov[0]);
+        load_n<T, VX>(Plo + g.n + c0, lov[1]);
+        load_n<T, VX>(Plo + 2 * g.n + c0, lov[2]);
+      }
+      T hv[3], lv[3];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) out[i] += k.amp * gz[i];
+      for (int i = 0; i < 3; ++i) {
+        T d = lov[i][iv] + inc[i];
+        if constexpr (NOISE) d += k.amp * gz[i];
+        two_sum(p[i], d, hv[i], lv[i]);
+      }
+      return Out{hv[0], hv[1], hv[2], lv[0], lv[1], lv[2]};
+    } else {
+      T out[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        out[i] = p[i] + inc[i];
+        if constexpr (NOISE && !CORR) out[i] += k.amp * gz[i];
+      }
+      return Out{out[0], out[1], out[2]};
     }
-    return P3<T>{out[0], out[1], out[2]};
   };
-  auto post = [&](int z, const P3<T> (&ov)[VX]) {
+  auto post = [&](int z, const Out (&ov)[VX]) {
     const long long c = (long long)z * g.nxy + s.xy;
     T a[VX], b[VX], d[VX];
     if (z >= g.zair) {                 // air layers carry no polarization
@@ -242,7 +286,24 @@ __global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __r
       store_n<T, VX>(Pn + c, a);
       store_n<T, VX>(Pn + g.n + c, b);
       store_n<T, VX>(Pn + 2 * g.n + c, d);
+      if constexpr (COMP) {
+        store_n<T, VX>(Plo + c, a);
+        store_n<T, VX>(Plo + g.n + c, b);
+        store_n<T, VX>(Plo + 2 * g.n + c, d);
+      }
       return;
+    }
+    if constexpr (COMP) {
+      T la[VX], lb[VX], ld[VX];
+#pragma unroll
+      for (int i = 0; i < VX; ++i) {
+        la[i] = ov[i].lx;
+        lb[i] = ov[i].ly;
+        ld[i] = ov[i].lz;
+      }
+      store_n<T, VX>(Plo + c, la);
+      store_n<T, VX>(Plo + g.n + c, lb);
+      store_n<T, VX>(Plo + 2 * g.n + c, ld);
     }
 #pragma unroll
     for (int i = 0; i < VX; ++i) {
@@ -282,7 +343,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_tdgl(Geo g, Bc<T> bc, const T* __r
   const TileSched ts{&S->sched_next, &S->sched_done};
   for (long long t = sched_take(ts, &tile_slot); t < mc.ntiles; t = sched_take(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(g, t, mc);
-    march_direct<T, P3<T>, MTX, MTY, VX, 4, 0, STEP_D>(g, s, smem, hsrc, osrc, emit, post);
+    march_direct<T, Out, MTX, MTY, VX, 4, 0, STEP_D>(g, s, smem, hsrc, osrc, emit, post);
   }
   // sched_finish, with the step counter advanced by the last block to finish
   if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -354,20 +415,28 @@ void launch_rhs(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, c
   rhs_v<T, false>(L, g, d, P, cond, use_cond);
 }
 
-template <typename T, bool CORR, bool NOISE, int VX>
+template <typename T, bool CORR, bool NOISE, int VX, bool COMP>
 static void tdgl_t(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, T* Pn, const Coef<T>& k) {
   static bool f = false;
   const size_t bytes = StepPipe<T, false, VX>::bytes();
-  smem_attr(k_tdgl<T, CORR, NOISE, VX>, bytes, f);
-  k_tdgl<T, CORR, NOISE, VX><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(g, d.bc, P, Pn, d.phi, k, d.S,
-                                                                               L.march);
+  smem_attr(k_tdgl<T, CORR, NOISE, VX, COMP>, bytes, f);
+  k_tdgl<T, CORR, NOISE, VX, COMP><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(g, d.bc, P, Pn, d.phi, k, d.S,
+                                                                                     L.march, d.plo);
 }
 
 template <typename T, bool CORR, bool NOISE>
 static void tdgl_v(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, T* Pn, const Coef<T>& k) {
   constexpr int V = 16 / sizeof(T);
-  if (L.march.vx == V) tdgl_t<T, CORR, NOISE, V>(L, g, d, P, Pn, k);
-  else tdgl_t<T, CORR, NOISE, 1>(L, g, d, P, Pn, k);
+  // the compensated state exists for FP32 forward Euler (d.plo set)
+  if constexpr (!CORR && std::is_same<T, float>::value) {
+    if (d.plo) {
+      if (L.march.vx == V) tdgl_t<T, CORR, NOISE, V, true>(L, g, d, P, Pn, k);
+      else tdgl_t<T, CORR, NOISE, 1, true>(L, g, d, P, Pn, k);
+      return;
+    }
+  }
+  if (L.march.vx == V) tdgl_t<T, CORR, NOISE, V, false>(L, g, d, P, Pn, k);
+  else tdgl_t<T, CORR, NOISE, 1, false>(L, g, d, P, Pn, k);
 }
 
 template <typename T>

@@ -70,6 +70,19 @@ class Film:
         st, info = pf.pf_step(self.ctx, nsteps, ok)
         return st, info.as_dict()
 
+    def step_async(self, nsteps=1):
+        """Enqueue steps without waiting (see pf_step_async); wait() reports them."""
+        pf.pf_step_async(self.ctx, nsteps)
+
+    def wait(self, ok=(pf.PF_OK,)):
+        st, info = pf.pf_step_wait(self.ctx, ok)
+        return st, info.as_dict()
+
+    def true_residual(self, P=None):
+        """FP64 (||b(P) - A phi||, ||b(P)||, ||b(P) - A phi_c||) of the bound
+        potential and of the compensated one."""
+        return pf.pf_true_residual(self.ctx, P)
+
     def solve_potential(self, ok=(pf.PF_OK,)):
         st, info = pf.pf_solve_potential(self.ctx, ok)
         return st, info.as_dict()

@@ -22,12 +22,14 @@ PF_EULER, PF_HEUN = 0, 1
 PF_FLAG_NO_GRAPHS = 1
 PF_FLAG_ADJOINT = 2
 PF_FLAG_WARM_LAST = 4
+PF_FLAG_PLAIN_FP32 = 8
 
 STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_CUDA", 3: "PF_ERR_NOCONV", 4: "PF_ERR_NONFINITE",
                 5: "PF_ERR_TIMEOUT", 6: "PF_ERR_STATE", 7: "PF_ERR_NOTIMPL"}
 
 # Every symbol the header declares.
-EXPORTS = ["pf_workspace_bytes", "pf_create", "pf_bind", "pf_set_bc", "pf_step", "pf_step_host",
+EXPORTS = ["pf_workspace_bytes", "pf_create", "pf_bind", "pf_set_bc", "pf_step", "pf_step_async", "pf_step_wait",
+           "pf_step_host", "pf_true_residual",
            "pf_solve_potential", "pf_adjoint_step", "pf_diagnostics", "pf_profile_enable", "pf_profile_read", "pf_destroy",
            "pf_last_error", "pf_solve_potential_noalloc", "pf_set_noise", "pf_get_tiling", "pf_set_tiling",
            "pf_batch_workspace_bytes", "pf_batch_create", "pf_batch_set_ramp", "pf_batch_step",
@@ -48,7 +50,8 @@ class pf_params(C.Structure):
 class pf_step_info(C.Structure):
     _fields_ = [("steps_done", C.c_int32), ("last_iters", C.c_int32), ("total_iters", C.c_int64),
                 ("last_relres", C.c_double), ("nonconverged", C.c_int32), ("status", C.c_int32),
-                ("kernel_launches", C.c_int64), ("graph_steps", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("graph_steps", C.c_int64),
+                ("max_iters", C.c_int32), ("solves", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -91,6 +94,12 @@ def lib():
         L.pf_set_bc.argtypes = [vp, i32, vp, vp]
         L.pf_step.restype = i32
         L.pf_step.argtypes = [vp, i32, C.POINTER(pf_step_info)]
+        L.pf_step_async.restype = i32
+        L.pf_step_async.argtypes = [vp, i32]
+        L.pf_step_wait.restype = i32
+        L.pf_step_wait.argtypes = [vp, C.POINTER(pf_step_info)]
+        L.pf_true_residual.restype = i32
+        L.pf_true_residual.argtypes = [vp, vp, vp]
         L.pf_step_host.restype = i32
         L.pf_step_host.argtypes = [vp, vp, vp, i32, C.POINTER(pf_step_info)]
         L.pf_solve_potential.restype = i32
@@ -185,6 +194,27 @@ def pf_step(ctx, nsteps, ok=(PF_OK,)):
     st = lib().pf_step(ctx, nsteps, C.byref(info))
     check(st, ctx, ok)
     return st, info
+
+
+def pf_step_async(ctx, nsteps):
+    """Enqueue nsteps steps; statistics stay on the device until pf_step_wait."""
+    return check(lib().pf_step_async(ctx, int(nsteps)), ctx)
+
+
+def pf_step_wait(ctx, ok=(PF_OK,)):
+    info = pf_step_info()
+    st = lib().pf_step_wait(ctx, C.byref(info))
+    check(st, ctx, ok)
+    return st, info
+
+
+def pf_true_residual(ctx, P=None):
+    """(||b(P) - A phi||_2, ||b(P)||_2, ||b(P) - A phi_c||_2) in FP64 for the
+    bound phi and the compensated potential phi_c; P: a device tensor of the
+    state (None: the bound P)."""
+    out = (C.c_double * 3)()
+    check(lib().pf_true_residual(ctx, _addr(P), C.cast(out, C.c_void_p)), ctx)
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 def pf_step_host(ctx, P_host, phi_host, nsteps, ok=(PF_OK,)):

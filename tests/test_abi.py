@@ -88,7 +88,7 @@ def test_workspace_bytes_and_validation(L):
     q.periodic_z = 0
     assert pf.pf_workspace_bytes(q) > 0
     q = good_params()
-    q.flags = 8
+    q.flags = 16
     assert pf.pf_workspace_bytes(q) == 0
     q.flags = pf.PF_FLAG_WARM_LAST
     assert 0 < pf.pf_workspace_bytes(q) < pf.pf_workspace_bytes(good_params())   # no history fields
@@ -114,11 +114,11 @@ def test_workspace_of_the_extrapolated_start():
     n = 32 * 32 * 32
     for prec, word, fields in ((pf.PF_FP64, 8, 3), (pf.PF_FP32, 4, 5)):
         p.precision = prec
-        p.flags, p.integrator = 0, pf.PF_EULER
+        p.flags, p.integrator = pf.PF_FLAG_PLAIN_FP32, pf.PF_EULER
         extrap = pf.pf_workspace_bytes(p)
-        p.flags = pf.PF_FLAG_WARM_LAST
+        p.flags = pf.PF_FLAG_WARM_LAST | pf.PF_FLAG_PLAIN_FP32
         last = pf.pf_workspace_bytes(p)
-        p.flags, p.integrator = 0, pf.PF_HEUN
+        p.flags, p.integrator = pf.PF_FLAG_PLAIN_FP32, pf.PF_HEUN
         heun = pf.pf_workspace_bytes(p)
         assert extrap - last == fields * n * word
         assert heun == last
@@ -126,3 +126,29 @@ def test_workspace_of_the_extrapolated_start():
     for order in (1, 2, 3):                       # the order changes no layout
         p.extrap_order = order
         assert pf.pf_workspace_bytes(p) == extrap
+
+
+def test_workspace_of_the_compensated_state():
+    """FP32 forward Euler keeps the polarization as P plus an FP32 remainder
+    (three more fields) unless PF_FLAG_PLAIN_FP32 is set; FP64, the
+    predictor-corrector and adjoint contexts have none."""
+    p = good_params()
+    p.nx, p.ny, p.nz = 32, 32, 32
+    n = 32 * 32 * 32
+    p.precision = pf.PF_FP32
+    comp = pf.pf_workspace_bytes(p)
+    p.flags = pf.PF_FLAG_PLAIN_FP32
+    plain = pf.pf_workspace_bytes(p)
+    assert comp - plain == 3 * n * 4
+    p.flags = pf.PF_FLAG_ADJOINT
+    adj = pf.pf_workspace_bytes(p)
+    p.flags = pf.PF_FLAG_ADJOINT | pf.PF_FLAG_PLAIN_FP32
+    assert adj == pf.pf_workspace_bytes(p)
+    p.flags, p.integrator = 0, pf.PF_HEUN
+    heun = pf.pf_workspace_bytes(p)
+    p.flags = pf.PF_FLAG_PLAIN_FP32
+    assert heun == pf.pf_workspace_bytes(p)
+    p.integrator, p.flags, p.precision = pf.PF_EULER, 0, pf.PF_FP64
+    b64 = pf.pf_workspace_bytes(p)
+    p.flags = pf.PF_FLAG_PLAIN_FP32
+    assert b64 == pf.pf_workspace_bytes(p)

@@ -70,3 +70,55 @@ def test_air_layers_and_the_adjoint():
         pf.pf_adjoint_step(f.ctx, lam, torch.zeros_like(f.P), torch.zeros(4, dtype=torch.float64, device=f.P.device))
     assert e.value.status == pf.PF_ERR_NOTIMPL
     f.close()
+
+
+@pytest.mark.parametrize("shape,n_air", [((32, 24, 13), 4), ((32, 32, 16), 5)])
+def test_mg_open_air_matches_oracle(shape, n_air):
+    """The permittivity-aware multigrid preconditioner (coarse eps = mean of
+    the children, harmonic-mean faces on every level) on the open-air film:
+    FP64 parity with the oracle's Jacobi-PCG at tight tolerances."""
+    nx, ny, nz = shape
+    w = W.film_open_air(nx, ny, nz, n_air=n_air, steps=6, precision="fp64").with_(rtol=1e-13, solver="mg",
+                                                                                    maxit=400)
+    f = Film(w)
+    st, info = f.step(6)
+    P, phi = f.numpy()
+    f.close()
+    Po, phio, sto, _ = O.step_ex(oracle_grid(w), oracle_params(w, 1e-14), w.P0, None, 6)
+    assert st == pf.PF_OK and sto == O.OK
+    assert relerr(P, Po) <= FP64_TOL
+    assert relerr(phi, phio) <= FP64_TOL
+
+
+def test_mg_random_permittivity_matches_oracle():
+    from helpers import mixed_workload
+    w = mixed_workload(32, 16, 8, 43, eps=True, steps=4, rtol=1e-13).with_(solver="mg", maxit=400)
+    f = Film(w)
+    st, _ = f.step(4)
+    P, phi = f.numpy()
+    f.close()
+    Po, phio, sto, _ = O.step(oracle_grid(w), oracle_params(w, 1e-14), w.P0, None, 4)
+    assert st == pf.PF_OK
+    assert relerr(P, Po) <= FP64_TOL
+    assert relerr(phi, phio) <= FP64_TOL
+
+
+def test_mg_cuts_the_air_film_iterations():
+    """At the open-air recipe's 100:1 permittivity contrast, multigrid needs
+    a small fraction of Jacobi-PCG's iterations per solve, and the FP32
+    results agree with the FP64 oracle."""
+    w = W.film_open_air(64, 64, 37, n_air=5, steps=10)
+    its = {}
+    Ps = {}
+    for solver, maxit in (("pcg", 5000), ("mg", 400)):
+        f = Film(w.with_(solver=solver, maxit=maxit))
+        st, info = f.step(10)
+        assert st == pf.PF_OK
+        its[solver] = info["total_iters"] / info["solves"]
+        Ps[solver], _ = f.numpy()
+        f.close()
+    print("iterations per solve: Jacobi %.1f, multigrid %.1f" % (its["pcg"], its["mg"]))
+    assert its["mg"] <= 30
+    assert its["mg"] <= 0.25 * its["pcg"]
+    Po, _, st, _ = O.step_ex(oracle_grid(w), oracle_params(w, 1e-12), w.P0, None, 10)
+    assert relerr(Ps["mg"], Po) <= FP32_TOL

@@ -49,3 +49,23 @@ def test_two_gloo_replicas_share_the_slowest_time():
 def test_single_rank_needs_no_process_group():
     import bench
     assert bench.replica_throughput(200.0, 500, 1) == (200.0, pytest.approx(2500.0))
+
+
+def test_bench_launches_replicas_itself():
+    """`bench.py --gpus 2` with no launcher around it starts two ranks itself
+    (torch's launcher, rendezvous on 127.0.0.1); the self-test mode runs the
+    same rank arithmetic on gloo without a GPU, and rank 0 alone prints."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--replica-selftest",
+                        "--steps", "10"], capture_output=True, text=True, timeout=300, env=env, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1                              # rank 0 only
+    line = lines[0]
+    assert line["n_gpus"] == 2
+    assert line["ms_per_step"] == pytest.approx(20.0 / 10)   # the slower rank: 10 ms x 2
+    assert line["value"] == pytest.approx(2 * 1000 * 10 / 0.020)

@@ -1,11 +1,12 @@
 """The allocation-free Poisson solve against the regular entry point.
 
 pf_solve_potential_noalloc serves callers that cannot allocate device memory
-(graph capture, allocator-free real-time loops, fixed memory pools): it keeps
-its scratch in a library-owned device array instead of a caller workspace.
-Its result must match pf_solve_potential on the same inputs, call after call
-(the array keeps the previous call's contents, so the second call checks that
-nothing stale leaks in).  This file is collected last on purpose.
+(real-time loops that must not stall on the allocator, processes whose device
+memory a fixed pool or another framework owns): it keeps its scratch in a
+library-owned device array instead of a caller workspace.  Its result must
+match pf_solve_potential on the same inputs, call after call (the array keeps
+the previous call's contents, so the second call checks that nothing stale
+leaks in), and the FP64 oracle.  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -15,7 +16,8 @@ from paper_1202_6116_gb300 import build as B
 from paper_1202_6116_gb300 import pf
 from paper_1202_6116_gb300.film import Film, make_params
 
-from helpers import mixed_workload, relerr
+import oracle as O
+from helpers import mixed_workload, oracle_grid, relerr
 
 pytestmark = pytest.mark.gpu
 
@@ -57,12 +59,55 @@ def test_noalloc_matches_regular_solve_twice(precision, tol):
         assert ginfo["last_iters"] == rinfo["last_iters"]
 
 
+def test_noalloc_matches_oracle():
+    w = mixed_workload(40, 24, 12, 34, precision="fp64", rtol=1e-13, amp=0.5)
+    got, info = noalloc_solve(w)
+    phio = O.solve_potential(oracle_grid(w), w.P0, rtol=1e-14)[0]
+    assert relerr(got, phio) <= 1e-10
+    assert info["last_iters"] > 0
+
+
 def test_noalloc_rejects_oversized_grids():
-    w = mixed_workload(256, 256, 64, 33)       # 4.2M cells in FP64: beyond the 32 MiB array
+    # 1M cells in FP64 need 32 MiB for the four Krylov vectors alone: just
+    # beyond the array.  The buffers are full size, so that a failing size
+    # check would give a wrong result here, never an out-of-bounds access.
+    w = mixed_workload(128, 128, 64, 33)
     dt = torch.float64
-    P = torch.zeros((3, 1, 1, 8), dtype=dt, device="cuda")
-    phi = torch.zeros((1, 1, 8), dtype=dt, device="cuda")
+    P = torch.zeros((3,) + w.shape, dtype=dt, device="cuda")
+    phi = torch.zeros(w.shape, dtype=dt, device="cuda")
     with pytest.raises(pf.PfError) as e:
         pf.pf_solve_potential_noalloc(make_params(w), None, P, phi)
     assert e.value.status == pf.PF_ERR_ARG
     assert "scratch" in pf.pf_last_error(None)
+
+
+def test_noalloc_rejects_host_pointers():
+    w = mixed_workload(16, 8, 4, 35)
+    P = torch.zeros((3,) + w.shape, dtype=torch.float64)          # host memory
+    phi = torch.zeros(w.shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(pf.PfError) as e:
+        pf.pf_solve_potential_noalloc(make_params(w), None, P, phi)
+    assert e.value.status == pf.PF_ERR_ARG
+    assert "device" in pf.pf_last_error(None)
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The call blocks, so it refuses to run while its stream is being
+    captured (PF_ERR_STATE), before it enqueues anything."""
+    w = mixed_workload(16, 8, 4, 36)
+    P = torch.as_tensor(w.P0, dtype=torch.float64, device="cuda").contiguous()
+    phi = torch.zeros(w.shape, dtype=torch.float64, device="cuda")
+    x = torch.zeros(4, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    status = {}
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            x.add_(1.0)
+            status["st"], _ = pf.pf_solve_potential_noalloc(make_params(w), s.cuda_stream, P, phi,
+                                                            ok=(pf.PF_OK, pf.PF_ERR_STATE))
+    assert status["st"] == pf.PF_ERR_STATE
+    assert "captur" in pf.pf_last_error(None)
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(x[0]) == 1.0
