@@ -232,7 +232,10 @@ pf_status pf_step(pf_ctx* ctx, int32_t nsteps, pf_step_info* info);
 
 /* Enqueue nsteps steps on the context's stream and return.  When the steps
  * run as CUDA graphs (the default: no PF_FLAG_NO_GRAPHS, profiling off) the
- * host does not wait: each step's Krylov loop is driven from the device.
+ * host does not wait: each step's Krylov loop is driven from the device, and
+ * forward-Euler steps that all solve the potential go out as pairs inside one
+ * persistent graph launch (a device-counted while loop), however many there
+ * are.
  * Host-driven steps poll the convergence flag and so block while issuing.
  * Calls accumulate: their solver statistics stay on the device until
  * pf_step_wait.  Until then the other entry points of this context (except
@@ -400,10 +403,12 @@ pf_status pf_get_tiling(const pf_ctx* ctx, pf_tiling* out);
 pf_status pf_set_tiling(pf_ctx* ctx, const pf_tiling* tiling);
 
 /* ------------------------------------------------------------------- batch
- * Many independent films advanced together: every batch step is ONE CUDA
- * graph launch holding, per film, its whole time step (its device-driven
- * Krylov loops included) as an independent branch, so small films run
- * concurrently and fill the GPU.  Before the branches one kernel applies the
+ * Many independent films advanced together: a batch step is a CUDA graph
+ * holding, per film, its whole time step (its device-driven Krylov loops
+ * included) as an independent branch, so small films run concurrently and
+ * fill the GPU; a multi-step call of forward-Euler films that solve every
+ * step is ONE persistent graph launch (pairs of batch steps in a
+ * device-counted while loop).  Before the branches one kernel applies the
  * films' electrode voltage ramps; after them one kernel records the
  * polarization-voltage loops (the switching observable of Section Results).
  * The films keep their own contexts, buffers and boundary masks; the batch

@@ -76,7 +76,8 @@ std::vector<MgLevelHost> mg_levels(const pf_params* p) {
 }
 
 struct Layout {
-  size_t P_alt, plo, r, p0, p1, q, invd, hist[3], clo, cx, tlo, thi, vlo, vhi, ctr, xctr, part, S, diag, z, zt, total;
+  size_t P_alt, plo, r, p0, p1, q, invd, hist[3], clo, cx, tlo, thi, vlo, vhi, ctr, xctr, part, S, diag, loop, z, zt,
+      total;
   bool adj = false;               // psi and vzero exist (PF_FLAG_ADJOINT)
   size_t psi = 0, vzero = 0;      // adjoint potential; zero face voltages
   std::vector<MgLevelHost> mg;
@@ -148,7 +149,7 @@ Layout layout_of(const pf_params* p) {
     return o;
   };
   L.P_alt = take(3 * n * w);
-  L.plo = take(comp_state(p) ? 3 * n * w : 0);
+  L.plo = take(comp_state(p) ? 3 * n * 2 : 0);          // bf16
   L.r = take(n * w);
   L.p0 = take(n * w);
   L.p1 = take(n * w);
@@ -170,6 +171,7 @@ Layout layout_of(const pf_params* p) {
   L.part = take(sizeof(double) * std::max<size_t>((size_t)pf::MAX_GRID * pf::MAX_NV, pf::MAX_NV * max_tiles));
   L.S = take(sizeof(Scalars));
   L.diag = take(8 * sizeof(double));
+  L.loop = take(2 * sizeof(long long));   // bodies left in a persistent step loop
   if (p->flags & PF_FLAG_ADJOINT) {
     L.adj = true;
     L.psi = take(n * w);
@@ -241,6 +243,8 @@ struct pf_ctx {
   // without the potential solve); each Krylov loop is a conditional while
   // node driven from the device.  Captured on first use.
   cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraphExec_t gloop = nullptr;   // persistent loop: two steps per body, many steps per launch
+  bool loop_broken = false;          // the loop graph cannot be built here: one launch per step
   int graph_key = -1;             // singular flag the graphs were captured for
   bool graphs_broken = false;     // capture not possible: host-driven loop
   int64_t graph_steps = 0;        // steps of the current call run as graphs
@@ -389,7 +393,7 @@ pf::Dev<T> dev_view(pf_ctx* ctx) {
   d.bc.vhi = (const T*)(ws + L.vhi);
   d.part = (double*)(ws + L.part);
   d.S = (Scalars*)(ws + L.S);
-  d.plo = comp_state(&ctx->prm) ? (T*)(ws + L.plo) : nullptr;
+  d.plo = comp_state(&ctx->prm) ? (unsigned short*)(ws + L.plo) : nullptr;
   return d;
 }
 
@@ -662,7 +666,9 @@ pf_status solve(pf_ctx* ctx, const T* P, bool adj = false, bool step_solve = fal
       before_launch(ctx);
       pf::launch_cg_p<T>(ctx->L, g, d, mg, it == 1);
       // the multigrid first iteration stages z alone (p = z), except with eps
-      after_launch(ctx, F_CG_P, (6 + 2 * e) * N * w, 1, it, (mg && e == 0.0) ? 3 * N * w : (6 + 2 * e) * N * w);
+      // the second iteration of a compensated multigrid solve reads no x (still 0)
+      const double cgp = (comp && mg && e == 0.0 && it == 2 ? 5 : 6 + 2 * e) * N * w;
+      after_launch(ctx, F_CG_P, cgp, 1, it, (mg && e == 0.0) ? 3 * N * w : (6 + 2 * e) * N * w);
       pf::launch_cg_r<T>(ctx->L, g, d, mg, 0, 0);
       after_launch(ctx, F_CG_R, (3 + e) * N * w, 1, it);
       if (mg) vcycle<T>(ctx, it);
@@ -681,7 +687,11 @@ pf_status solve(pf_ctx* ctx, const T* P, bool adj = false, bool step_solve = fal
   if (!s.zero_x) est_iters = std::max(1, s.iter);
   before_launch(ctx);
   pf::launch_cg_finish<T>(ctx->L, g, d, ctx->singular);
-  after_launch(ctx, F_FINISH, (comp ? (s.pending ? 12.0 : 11.0) : s.zero_x ? 1.0 : (s.pending ? 3.0 : 1.0)) * N * w);
+  // compensated: read hi, s, three slots (+ p when an update is owed, + x once
+  // written), write hi, s, two slots
+  after_launch(ctx, F_FINISH,
+               (comp ? 9.0 + (s.pending ? 1.0 : 0.0) + (s.xzero ? 0.0 : 1.0)
+                     : s.zero_x ? 1.0 : (s.pending ? 3.0 : 1.0)) * N * w);
   if (ctx->singular) {
     pf::launch_sub_mean<T>(ctx->L, g, d);
     after_launch(ctx, F_SUB_MEAN, 2 * N * w);
@@ -695,6 +705,8 @@ void drop_graphs(pf_ctx* ctx) {
     if (e) cudaGraphExecDestroy(e);
     e = nullptr;
   }
+  if (ctx->gloop) cudaGraphExecDestroy(ctx->gloop);
+  ctx->gloop = nullptr;
   ctx->graph_key = -1;
 }
 
@@ -830,6 +842,49 @@ pf_status capture_step(pf_ctx* ctx, int cur, int refresh, cudaGraphExec_t* out) 
   return PF_OK;
 }
 
+// One graph running pairs of forward-Euler steps in a device-driven while
+// loop: a conditional node whose body is the step from buffer 0, the step
+// from buffer 1 and k_loop_next, which counts the bodies down (every step
+// solves the potential: poisson_every <= 1).  A multi-step call then costs
+// one graph launch however many steps it takes.
+template <typename T>
+pf_status capture_loop(pf_ctx* ctx, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  cudaGraphConditionalHandle h = 0;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    std::vector<cudaGraphNode_t> deps;
+    e = append_step<T>(ctx, body, deps, 0, 1, ctx->cap_stream);
+    if (e == cudaSuccess) e = append_step<T>(ctx, body, deps, 1, 1, ctx->cap_stream);
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, deps.data(), nullptr, deps.size(),
+                                        cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      pf::launch_loop_next((long long*)(ctx->ws + ctx->lay.loop), h, ctx->cap_stream);
+      cudaGraph_t g2 = body;
+      e = cudaStreamEndCapture(ctx->cap_stream, &g2);
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ctx->fail(PF_ERR_CUDA, "step loop graph: %s", cudaGetErrorString(e));
+  }
+  *out = exec;
+  return PF_OK;
+}
+
 // Graph-launched steps: no host round trip inside a step.  Returns false
 // (nothing launched) when graphs cannot be used here.
 template <typename T>
@@ -856,6 +911,31 @@ bool run_steps_graph(pf_ctx* ctx, int nsteps, pf_status* st) {
   }
   refresh_invd<T>(ctx, ctx->L, false);
   const bool heun = ctx->prm.integrator == PF_HEUN;
+  // many forward-Euler steps that all solve: pairs of them in one persistent launch
+  if (!heun && ctx->prm.poisson_every <= 1 && ctx->cur == 0 && nsteps >= 4 && !ctx->loop_broken) {
+    if (!ctx->gloop && capture_loop<T>(ctx, &ctx->gloop) != PF_OK) {
+      ctx->loop_broken = true;           // one launch per step from here on
+      ctx->err.clear();
+    }
+    if (ctx->gloop) {
+      const long long pairs = nsteps / 2;
+      pf::launch_loop_set((long long*)(ctx->ws + ctx->lay.loop), pairs, ctx->stream);
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaGraphLaunch(ctx->gloop, ctx->stream);
+      if (e != cudaSuccess) {
+        *st = ctx->cuda_fail(e, "persistent step loop");
+        return true;
+      }
+      int64_t fixed = 0, per_iter = 0;
+      step_kernel_counts(ctx, 1, &fixed, &per_iter);
+      ctx->graph_fixed += 2 * pairs * fixed + pairs;   // and the counter kernel of every body
+      ctx->launches += 1;                              // the count setter
+      ctx->graph_solves += 2 * pairs;
+      ctx->graph_steps += 2 * pairs;
+      ctx->nstep += 2 * pairs;
+      nsteps -= (int)(2 * pairs);
+    }
+  }
   for (int s = 0; s < nsteps; ++s) {
     const int refresh = refresh_step(ctx) ? 1 : 0;
     const int slot = ctx->cur * 2 + refresh;
@@ -903,7 +983,8 @@ pf_status run_steps(pf_ctx* ctx, int nsteps, bool keep_parity = false) {
   T* Pbuf[2] = {(T*)ctx->P_user, (T*)(ctx->ws + ctx->lay.P_alt)};
   const double coef[5] = {ctx->prm.a1, ctx->prm.a11, ctx->prm.a12, ctx->prm.g, ctx->prm.dt * ctx->prm.L};
   const bool heun = ctx->prm.integrator == PF_HEUN;
-  const double tdgl_bytes = (comp_state(&ctx->prm) ? 13.0 : 7.0) * (double)g.n * sizeof(T);
+  // compensated state: 3 bf16 remainders read and written, 6 half-words = 3 words
+  const double tdgl_bytes = (comp_state(&ctx->prm) ? 10.0 : 7.0) * (double)g.n * sizeof(T);
   pf_status gst;
   if (run_steps_graph<T>(ctx, nsteps, &gst)) {
     if (gst != PF_OK) return gst;
@@ -1105,7 +1186,7 @@ pf_status pf_bind(pf_ctx* ctx, void* P, void* phi, const void* eps, void* worksp
   recompute_singular(ctx);
   PF_CUDA(cudaMemsetAsync(ctx->ws + L.S, 0, sizeof(Scalars), ctx->stream));
   if (comp_state(&ctx->prm))
-    PF_CUDA(cudaMemsetAsync(ctx->ws + L.plo, 0, 3 * (size_t)ctx->geo.n * sizeof(float), ctx->stream));
+    PF_CUDA(cudaMemsetAsync(ctx->ws + L.plo, 0, 3 * (size_t)ctx->geo.n * sizeof(unsigned short), ctx->stream));
   if (L.adj) {
     const size_t w = ctx->prm.precision == PF_FP32 ? 4 : 8;
     PF_CUDA(cudaMemsetAsync(ctx->ws + L.psi, 0, (size_t)ctx->geo.n * w, ctx->stream));
@@ -1439,12 +1520,14 @@ struct pf_batch {
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
   char* ws = nullptr;
-  size_t off_state = 0, off_table = 0, off_part = 0, off_hist = 0;
+  size_t off_state = 0, off_table = 0, off_part = 0, off_hist = 0, off_loop = 0;
   int64_t max_records = 0;
   int record_every = 1;
   long long max_nxy = 0;
   std::vector<pf::BatchFilm> table;
   cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraphExec_t gloop = nullptr;   // persistent loop: two batch steps per body
+  bool loop_broken = false;
   std::vector<uint64_t> gen;         // film generations the graphs were captured for
   std::vector<pf_step_info> infos;
   std::string err;
@@ -1465,7 +1548,7 @@ namespace {
 thread_local char g_batch_error[512];
 
 struct BatchLayout {
-  size_t state, table, part, hist, total;
+  size_t state, table, part, hist, loop, total;
 };
 
 BatchLayout batch_layout(int nfilms, int64_t max_records) {
@@ -1480,6 +1563,7 @@ BatchLayout batch_layout(int nfilms, int64_t max_records) {
   L.table = take(sizeof(pf::BatchFilm) * (size_t)nfilms);
   L.part = take(sizeof(double) * 3 * pf::BATCH_REC_BLOCKS * (size_t)nfilms);
   L.hist = take(sizeof(double) * 4 * (size_t)nfilms * (size_t)max_records);
+  L.loop = take(2 * sizeof(long long));   // bodies left in a persistent batch loop
   L.total = off;
   return L;
 }
@@ -1489,6 +1573,8 @@ void batch_drop_graphs(pf_batch* b) {
     if (e) cudaGraphExecDestroy(e);
     e = nullptr;
   }
+  if (b->gloop) cudaGraphExecDestroy(b->gloop);
+  b->gloop = nullptr;
 }
 
 pf_status batch_upload_table(pf_batch* b) {
@@ -1503,48 +1589,97 @@ pf_status batch_upload_table(pf_batch* b) {
 
 // One batch step as a graph: the ramp kernel, every film's step as an
 // independent branch after it, the loop record after all of them.
-pf_status batch_capture(pf_batch* b, int cur, int refresh, cudaGraphExec_t* out) {
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaError_t e = cudaGraphCreate(&graph, 0);
+// Append one batch step (ramp, every film's step from buffer cur, loop record)
+// to graph after the nodes deps; on return deps holds the record node.
+cudaError_t batch_append(pf_batch* b, cudaGraph_t graph, std::vector<cudaGraphNode_t>& deps, int cur, int refresh) {
+  cudaError_t e = cudaSuccess;
   const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
   const pf::BatchFilm* table = (const pf::BatchFilm*)(b->ws + b->off_table);
   pf::BatchState* bs = (pf::BatchState*)(b->ws + b->off_state);
   const int nf = (int)b->films.size();
-  auto segment = [&](std::vector<cudaGraphNode_t>& deps, auto&& body) {
+  auto segment = [&](std::vector<cudaGraphNode_t>& dp, auto&& body) {
     if (e != cudaSuccess) return;
-    e = cudaStreamBeginCaptureToGraph(b->cap, graph, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
-                                      mode);
+    e = cudaStreamBeginCaptureToGraph(b->cap, graph, dp.empty() ? nullptr : dp.data(), nullptr, dp.size(), mode);
     if (e != cudaSuccess) return;
     body();
     cudaStreamCaptureStatus cs;
     const cudaGraphNode_t* fr = nullptr;
     size_t nfr = 0;
     e = cudaStreamGetCaptureInfo(b->cap, &cs, nullptr, nullptr, &fr, nullptr, &nfr);
-    if (e == cudaSuccess) deps.assign(fr, fr + nfr);
+    if (e == cudaSuccess) dp.assign(fr, fr + nfr);
     cudaGraph_t g_out = graph;
     const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g_out);
     if (e == cudaSuccess) e = e2;
   };
-  std::vector<cudaGraphNode_t> ramp;
+  std::vector<cudaGraphNode_t> ramp = deps;
   segment(ramp, [&] { pf::launch_batch_ramp(table, nf, b->max_nxy, bs, b->cap); });
   std::vector<cudaGraphNode_t> joined;
   for (pf_ctx* c : b->films) {
     if (e != cudaSuccess) break;
-    std::vector<cudaGraphNode_t> deps = ramp;
-    e = c->prm.precision == PF_FP32 ? append_step<float>(c, graph, deps, cur, refresh, b->cap)
-                                    : append_step<double>(c, graph, deps, cur, refresh, b->cap);
-    joined.insert(joined.end(), deps.begin(), deps.end());
+    std::vector<cudaGraphNode_t> dp = ramp;
+    e = c->prm.precision == PF_FP32 ? append_step<float>(c, graph, dp, cur, refresh, b->cap)
+                                    : append_step<double>(c, graph, dp, cur, refresh, b->cap);
+    joined.insert(joined.end(), dp.begin(), dp.end());
   }
   const int buf = b->films[0]->prm.integrator == PF_HEUN ? cur : cur ^ 1;
   double* part = (double*)(b->ws + b->off_part);
   double* hist = (double*)(b->ws + b->off_hist);
   segment(joined, [&] { pf::launch_batch_record(table, nf, buf, bs, part, hist, b->cap); });
+  deps = joined;
+  return e;
+}
+
+pf_status batch_capture(pf_batch* b, int cur, int refresh, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  std::vector<cudaGraphNode_t> deps;
+  if (e == cudaSuccess) e = batch_append(b, graph, deps, cur, refresh);
   if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
   if (graph) cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return b->fail(PF_ERR_CUDA, "batch graph capture: %s", cudaGetErrorString(e));
+  }
+  *out = exec;
+  return PF_OK;
+}
+
+// The persistent form: pairs of batch steps (buffer 0, then buffer 1) in a
+// device-driven while loop counted down by k_loop_next, so that a whole
+// pf_batch_step call is one graph launch.
+pf_status batch_capture_loop(pf_batch* b, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  cudaGraphConditionalHandle h = 0;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    std::vector<cudaGraphNode_t> deps;
+    e = batch_append(b, body, deps, 0, 1);
+    if (e == cudaSuccess) e = batch_append(b, body, deps, 1, 1);
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(b->cap, body, deps.data(), nullptr, deps.size(),
+                                        cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      pf::launch_loop_next((long long*)(b->ws + b->off_loop), h, b->cap);
+      cudaGraph_t g2 = body;
+      e = cudaStreamEndCapture(b->cap, &g2);
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return b->fail(PF_ERR_CUDA, "batch step loop graph: %s", cudaGetErrorString(e));
   }
   *out = exec;
   return PF_OK;
@@ -1593,6 +1728,7 @@ pf_status pf_batch_create(pf_ctx* const* films, int32_t nfilms, void* workspace,
   b->off_table = L.table;
   b->off_part = L.part;
   b->off_hist = L.hist;
+  b->off_loop = L.loop;
   b->max_records = max_records;
   b->record_every = record_every;
   b->gen.assign(nfilms, 0);
@@ -1676,6 +1812,36 @@ pf_status pf_batch_step(pf_batch* b, int32_t nsteps, pf_step_info* info) {
     else refresh_invd<double>(c, c->L, false);
   }
   const bool heun = f0->prm.integrator == PF_HEUN;
+  auto book = [&](int refresh, long long steps) {    // host bookkeeping of graph-run steps
+    for (pf_ctx* c : b->films) {
+      int64_t fixed = 0, per_iter = 0;
+      step_kernel_counts(c, refresh, &fixed, &per_iter);
+      c->graph_fixed += steps * fixed;
+      c->graph_solves += refresh ? steps * (heun ? 2 : 1) : 0;
+      c->graph_steps += steps;
+      if (!heun && (steps & 1)) c->cur ^= 1;
+      c->nstep += steps;
+    }
+  };
+  long long loop_launches = 0;
+  // many forward-Euler steps that all solve: pairs of batch steps in one persistent launch
+  if (!heun && f0->prm.poisson_every <= 1 && f0->cur == 0 && nsteps >= 4 && !b->loop_broken) {
+    if (!b->gloop && batch_capture_loop(b, &b->gloop) != PF_OK) {
+      b->loop_broken = true;             // one launch per batch step from here on
+      b->err.clear();
+    }
+    if (b->gloop) {
+      const long long pairs = nsteps / 2;
+      pf::launch_loop_set((long long*)(b->ws + b->off_loop), pairs, b->stream);
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaGraphLaunch(b->gloop, b->stream);
+      if (e != cudaSuccess) return b->fail(PF_ERR_CUDA, "persistent batch loop: %s", cudaGetErrorString(e));
+      book(1, 2 * pairs);
+      loop_launches = 1 + pairs;                     // the count setter and every body's counter
+      nsteps -= (int)(2 * pairs);
+    }
+  }
+  const int total_steps = nsteps + (int)(2 * (loop_launches > 0 ? loop_launches - 1 : 0));
   for (int s = 0; s < nsteps; ++s) {
     const int refresh = refresh_step(f0) ? 1 : 0;
     const int cur = f0->cur;
@@ -1686,16 +1852,9 @@ pf_status pf_batch_step(pf_batch* b, int32_t nsteps, pf_step_info* info) {
     }
     const cudaError_t e = cudaGraphLaunch(b->gexec[slot], b->stream);
     if (e != cudaSuccess) return b->fail(PF_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
-    for (pf_ctx* c : b->films) {
-      int64_t fixed = 0, per_iter = 0;
-      step_kernel_counts(c, refresh, &fixed, &per_iter);
-      c->graph_fixed += fixed;
-      c->graph_solves += refresh ? (heun ? 2 : 1) : 0;
-      c->graph_steps += 1;
-      if (!heun) c->cur ^= 1;
-      c->nstep += 1;
-    }
+    book(refresh, 1);
   }
+  nsteps = total_steps;
   pf_status worst = PF_OK;
   pf_step_info sum{};
   sum.steps_done = nsteps;
@@ -1722,7 +1881,7 @@ pf_status pf_batch_step(pf_batch* b, int32_t nsteps, pf_step_info* info) {
     sum.kernel_launches += fi.kernel_launches;
     sum.graph_steps = nsteps;
   }
-  sum.kernel_launches += 2LL * nsteps;   // the ramp and record kernels
+  sum.kernel_launches += 2LL * nsteps + loop_launches;   // the ramp and record kernels (and loop counters)
   sum.status = worst;
   if (info) *info = sum;
   if (worst != PF_OK) b->fail(worst, "%s", worst == PF_ERR_NONFINITE ? "a film went non-finite" : "a Poisson solve hit poisson_maxit");

@@ -37,6 +37,9 @@ __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g
   static_assert(!FIRST || DIRECT, "the first-iteration form is the direct one");
   if (S->done) return;
   const int first = FIRST ? 1 : S->first;
+  // x still 0 (the correction of a compensated start, not written yet): the
+  // deferred update writes alpha p_old without reading x
+  const int xz = S->xzero;
   const T beta = first ? T(0) : T(S->beta);
   const T alpha = T(S->alpha);
   const int pb = S->pbuf;
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g
     const T qv = apply_bt(st, dlo, dhi, ih2, bt);
     const T pc = field_value<T>(st.c);
     apq.add(pc, qv);
-    return Out{first ? o[0] : o[0] + alpha * h[1], pc, qv};
+    return Out{first ? o[0] : (xz ? alpha * h[1] : o[0] + alpha * h[1]), pc, qv};
   };
   auto post = [&](int z, const Out (&ov)[VX]) {
     const long long c = (long long)z * g.nxy + s.xy;
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g
     const int dhi = (B && st.za < 0) ? (int)bc.thi[xy] : 0;
     const T qv = apply_bt(st, dlo, dhi, ih2, bt);
     apq.add(st.c, qv);
-    return Out{first ? o[0] : o[0] + alpha * sr.c.v[1], st.c, qv};
+    return Out{first ? o[0] : (xz ? alpha * sr.c.v[1] : o[0] + alpha * sr.c.v[1]), st.c, qv};
   };
   const TileSched ts{&S->sched_next, &S->sched_done};
   for (long long t = sched_take(ts, &tile_slot); t < mc.ntiles; t = sched_take(ts, &tile_slot)) {
@@ -133,7 +136,12 @@ __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g
       march_direct<T, Out, MTX, MTY, VX, 1, 0, CG_D>(g, s, smem, hs1, os1, emit_f, post);
     } else if constexpr (DIRECT) {
       static_assert(MG && !EPS, "the direct form is the multigrid search direction with eps = 1");
-      march_direct<T, Out, MTX, MTY, VX, NH, 1, CG_D>(g, s, smem, hsrc, osrc, emit_d, post);
+      if (xz) {                        // x is not read: stage z and p_old alone
+        const T* const os0[1] = {nullptr};
+        march_direct<T, Out, MTX, MTY, VX, NH, 0, CG_D>(g, s, smem, hsrc, os0, emit_d, post);
+      } else {
+        march_direct<T, Out, MTX, MTY, VX, NH, 1, CG_D>(g, s, smem, hsrc, osrc, emit_d, post);
+      }
     } else {
       march<T, F, Out, MTX, MTY, VX, NH, 1, CG_D>(g, s, smem, hsrc, osrc, val, emit, post);
     }
@@ -149,6 +157,7 @@ __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g
       S->pq = pq;
       S->iter += 1;
       S->pbuf = pb ^ 1;
+      if (!first) S->xzero = 0;        // this launch wrote x
       S->first = 0;
       if (!(pq > 0.0)) {               // breakdown (or NaN): stop with the current iterate
         if (!isfinite(pq)) S->nonfinite = 1;

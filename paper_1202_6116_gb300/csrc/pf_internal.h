@@ -55,7 +55,7 @@ struct Dev {
   double* part;
   Scalars* S;
   Comp<T> cp;
-  T* plo;            // remainder of a compensated FP32 polarization state (3N), or nullptr
+  unsigned short* plo;   // remainder of a compensated FP32 polarization state (3N bf16), or nullptr
 };
 
 // One multigrid level as the kernels see it.
@@ -133,6 +133,11 @@ void launch_tdgl_adj(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T*
 // f(P), the squared face differences of P, and P.E(phi); coef = {a1, a11, a12, thr}.
 template <typename T>
 void launch_diag(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, const double* coef, double* out);
+
+// Persistent step loops (pf_kernels.cu): the count of loop bodies left, and
+// the body's last kernel (counts down, sets the while condition).
+void launch_loop_set(long long* left, long long n, cudaStream_t st);
+void launch_loop_next(long long* left, cudaGraphConditionalHandle h, cudaStream_t st);
 
 // True residual (pf_diag.cu): out[0] = ||b(P) - A phi||^2, out[1] = ||b(P)||^2,
 // out[2] = the first for the compensated potential when d.cp.lo is set (else

@@ -145,8 +145,10 @@ __global__ void __launch_bounds__(NTHREADS) k_cg_finish(Geo g, T* __restrict__ x
 //   c_{k+1} from D_k, D_{k-1}, D_{k-2} -> slot k + 1 (D_{k-2} read first)
 //   s = lo + c_{k+1}, x = 0 (the next solve's start), and the count k + 1.
 // A reset history starts with s = 0, slot 0 = 0, x = 0 and k = 0.
-// Per cell: read x, p, hi, s and three slots; write hi, s, two slots and x
-// (flat, 16-byte vectors).
+// x is not zeroed for the next solve: the solver state says when it is still
+// 0 (unwritten since the start, S->xzero), and then it is not read.
+// Per cell: read x (when written), p, hi, s and three slots; write hi, s and
+// two slots (flat, 16-byte vectors).
 __device__ __forceinline__ void finish_comp_cell(bool zero, long long k, int kcap, float dx, float& hi, float& sv,
                                                  float& ck, float d1, float& dm2) {
   float nlo, dk;
@@ -173,6 +175,7 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_cg_finish_comp(long long n, fl
   __shared__ bool last;
   const bool zero = S->zero_x;
   const int pend = S->pending;
+  const int xz = S->xzero;
   const float alpha = float(S->alpha);
   const float* __restrict__ p = S->pbuf ? p1 : p0;
   const long long k = *cp.nsolve;
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_cg_finish_comp(long long n, fl
   const long long nvec = n / 4;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < nvec; i += stride) {
-    float4 xv = reinterpret_cast<const float4*>(x)[i];
+    float4 xv = xz ? z4 : reinterpret_cast<const float4*>(x)[i];
     if (pend) {
       const float4 pv = reinterpret_cast<const float4*>(p)[i];
       xv.x += alpha * pv.x;
@@ -204,17 +207,16 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_cg_finish_comp(long long n, fl
     reinterpret_cast<float4*>(cp.lo)[i] = sv;
     reinterpret_cast<float4*>(rk)[i] = c;
     reinterpret_cast<float4*>(r2)[i] = b;
-    reinterpret_cast<float4*>(x)[i] = z4;
   }
   for (long long i = nvec * 4 + blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += stride) {
-    const float dx = pend ? x[i] + alpha * p[i] : x[i];
+    const float xi = xz ? 0.0f : x[i];
+    const float dx = pend ? xi + alpha * p[i] : xi;
     float h = cp.hi[i], sv = cp.lo[i], c = rk[i], b = k >= 2 ? r2[i] : 0.0f;
     finish_comp_cell(zero, k, cp.kcap, dx, h, sv, c, k >= 1 ? r1[i] : 0.0f, b);
     cp.hi[i] = h;
     cp.lo[i] = sv;
     rk[i] = c;
     r2[i] = b;
-    x[i] = 0.0f;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -380,5 +382,24 @@ void launch_extrap(const LaunchCfg& L, long long n, T* phi, T* const ring[3], lo
 
 PF_INSTANTIATE(float)
 PF_INSTANTIATE(double)
+
+// ------------------------------------------------------- persistent step loops
+// A whole multi-step call can run as ONE graph launch: a conditional while
+// node whose body holds two time steps (one from each polarization buffer)
+// and, last, k_loop_next, which counts the bodies down and sets the loop
+// condition.  k_loop_set writes the count before the launch.
+__global__ void k_loop_set(long long* left, long long n) { *left = n; }
+
+__global__ void k_loop_next(long long* left, cudaGraphConditionalHandle h) {
+  const long long v = *left - 1;
+  *left = v;
+  cudaGraphSetConditional(h, v > 0 ? 1u : 0u);
+}
+
+void launch_loop_set(long long* left, long long n, cudaStream_t st) { k_loop_set<<<1, 1, 0, st>>>(left, n); }
+
+void launch_loop_next(long long* left, cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_loop_next<<<1, 1, 0, st>>>(left, h);
+}
 
 }  // namespace pf

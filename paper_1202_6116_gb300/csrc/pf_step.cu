@@ -14,10 +14,12 @@
 //           no z+ neighbour in the Laplacian (free surface).
 //           COMP = true (FP32 forward Euler): the state is the compensated
 //           pair P + P_lo, P_lo the part of the exact sum that the FP32 P
-//           cannot hold (a second FP32 field, own cells only, updated in
-//           place).  The increment dt R is added to the pair by TwoSum, so
-//           increments far below half an FP32 ulp of P still accumulate
-//           instead of being rounded away step after step.
+//           cannot hold (own cells only, updated in place, stored as bf16:
+//           it is at most half an FP32 ulp of P, so its 8-bit significand
+//           still resolves increments down to about 2^-10 ulp of P).  The
+//           increment dt R is added to the pair by TwoSum, so increments far
+//           below half an FP32 ulp of P still accumulate instead of being
+//           rounded away step after step.
 //           CORR = true is the corrector of the predictor-corrector scheme: P is
 //           the predicted state P^p, and the output overwrites the state P_n it
 //           started from with (P_n + P^p + dt R(P^p)) / 2 = P_n + dt (R(P_n) +
@@ -26,7 +28,9 @@
 // Both read P (3 components) and phi with their 6 neighbours; the neighbours
 // come straight from the staged planes (march_direct).  Algorithmic traffic
 // per cell: k_rhs reads 4 words (5 with a compensated start) and writes 1;
-// k_tdgl reads 4 and writes 3 (compensated state: reads 7, writes 6).
+// k_tdgl reads 4 and writes 3 (compensated state: plus 3 half-words each way).
+#include <cuda_bf16.h>
+
 #include "pf_internal.h"
 #include "pf_march.cuh"
 #include "pf_rng.cuh"
@@ -155,6 +159,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_rhs(Geo g, Bc<T> bc, const T* __re
   S->iter = 0;
   S->first = 1;
   S->pending = 0;
+  S->xzero = COMP ? 1 : 0;            // a compensated start's correction begins at 0, unwritten
   S->status = 0;
   S->alpha = 0.0;
   S->beta = 0.0;
@@ -197,6 +202,34 @@ struct P6 {
   T x, y, z, lx, ly, lz;
 };
 
+// VX bf16 remainders <-> floats (8-byte accesses for a 4-cell vector).
+template <int VX>
+__device__ __forceinline__ void load_bf16(const unsigned short* p, float (&o)[VX]) {
+  if constexpr (VX == 4) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    o[0] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(u.x & 0xffffu)));
+    o[1] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(u.x >> 16)));
+    o[2] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(u.y & 0xffffu)));
+    o[3] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(u.y >> 16)));
+  } else {
+#pragma unroll
+    for (int i = 0; i < VX; ++i) o[i] = __bfloat162float(__ushort_as_bfloat16(p[i]));
+  }
+}
+template <int VX>
+__device__ __forceinline__ void store_bf16(unsigned short* p, const float (&v)[VX]) {
+  unsigned short b[VX];
+#pragma unroll
+  for (int i = 0; i < VX; ++i) b[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v[i]));
+  if constexpr (VX == 4) {
+    *reinterpret_cast<uint2*>(p) = make_uint2((unsigned)b[0] | ((unsigned)b[1] << 16),
+                                              (unsigned)b[2] | ((unsigned)b[3] << 16));
+  } else {
+#pragma unroll
+    for (int i = 0; i < VX; ++i) p[i] = b[i];
+  }
+}
+
 // a + b = s + e exactly (TwoSum, Knuth): no condition on the magnitudes.
 template <typename T>
 __device__ __forceinline__ void two_sum(T a, T b, T& s, T& e) {
@@ -208,7 +241,7 @@ __device__ __forceinline__ void two_sum(T a, T b, T& s, T& e) {
 template <typename T, bool CORR, bool NOISE, int VX, bool COMP = false>
 __global__ void __launch_bounds__(MTX* MTY, 2) k_tdgl(Geo g, Bc<T> bc, const T* __restrict__ P, T* __restrict__ Pn,
                                                   const T* __restrict__ phi, Coef<T> k, Scalars* S, MarchCfg mc,
-                                                  T* __restrict__ Plo) {
+                                                  unsigned short* __restrict__ Plo) {
   static_assert(!(COMP && CORR), "the compensated state is a forward-Euler mode");
   using Out = typename std::conditional<COMP, P6<T>, P3<T>>::type;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -255,9 +288,9 @@ __global__ void __launch_bounds__(MTX* MTY, 2) k_tdgl(Geo g, Bc<T> bc, const T* 
       const int iv = xy - s.xy;                     // index inside the own vector
       if (iv == 0) {
         const long long c0 = (long long)z * g.nxy + s.xy;
-        load_n<T, VX>(Plo + c0, lov[0]);
-        load_n<T, VX>(Plo + g.n + c0, lov[1]);
-        load_n<T, VX>(Plo + 2 * g.n + c0, lov[2]);
+        load_bf16<VX>(Plo + c0, lov[0]);
+        load_bf16<VX>(Plo + g.n + c0, lov[1]);
+        load_bf16<VX>(Plo + 2 * g.n + c0, lov[2]);
       }
       T hv[3], lv[3];
 #pragma unroll
@@ -287,9 +320,9 @@ __global__ void __launch_bounds__(MTX* MTY, 2) k_tdgl(Geo g, Bc<T> bc, const T* 
       store_n<T, VX>(Pn + g.n + c, b);
       store_n<T, VX>(Pn + 2 * g.n + c, d);
       if constexpr (COMP) {
-        store_n<T, VX>(Plo + c, a);
-        store_n<T, VX>(Plo + g.n + c, b);
-        store_n<T, VX>(Plo + 2 * g.n + c, d);
+        store_bf16<VX>(Plo + c, a);
+        store_bf16<VX>(Plo + g.n + c, b);
+        store_bf16<VX>(Plo + 2 * g.n + c, d);
       }
       return;
     }
@@ -301,9 +334,9 @@ __global__ void __launch_bounds__(MTX* MTY, 2) k_tdgl(Geo g, Bc<T> bc, const T* 
         lb[i] = ov[i].ly;
         ld[i] = ov[i].lz;
       }
-      store_n<T, VX>(Plo + c, la);
-      store_n<T, VX>(Plo + g.n + c, lb);
-      store_n<T, VX>(Plo + 2 * g.n + c, ld);
+      store_bf16<VX>(Plo + c, la);
+      store_bf16<VX>(Plo + g.n + c, lb);
+      store_bf16<VX>(Plo + 2 * g.n + c, ld);
     }
 #pragma unroll
     for (int i = 0; i < VX; ++i) {

@@ -130,7 +130,7 @@ def test_workspace_of_the_extrapolated_start():
 
 def test_workspace_of_the_compensated_state():
     """FP32 forward Euler keeps the polarization as P plus an FP32 remainder
-    (three more fields) unless PF_FLAG_PLAIN_FP32 is set; FP64, the
+    (3N bf16 values) unless PF_FLAG_PLAIN_FP32 is set; FP64, the
     predictor-corrector and adjoint contexts have none."""
     p = good_params()
     p.nx, p.ny, p.nz = 32, 32, 32
@@ -139,7 +139,7 @@ def test_workspace_of_the_compensated_state():
     comp = pf.pf_workspace_bytes(p)
     p.flags = pf.PF_FLAG_PLAIN_FP32
     plain = pf.pf_workspace_bytes(p)
-    assert comp - plain == 3 * n * 4
+    assert comp - plain == 3 * n * 2               # the remainder is stored in bf16
     p.flags = pf.PF_FLAG_ADJOINT
     adj = pf.pf_workspace_bytes(p)
     p.flags = pf.PF_FLAG_ADJOINT | pf.PF_FLAG_PLAIN_FP32
