@@ -591,6 +591,13 @@ void comp_view(pf_ctx* ctx, pf::Dev<T>& d) {
   d.phi = (T*)(ws + ctx->lay.cx);
 }
 
+// Does a graph-captured step solve run its second iteration outside the
+// Krylov loop too, with the form that reads no correction (compensated
+// multigrid solves with eps = 1)?
+bool peel_second(const pf_ctx* ctx) {
+  return compensated(ctx) && ctx->prm.solver == PF_PCG_MG && !ctx->prm.has_eps;
+}
+
 // Does a step solve start with k_extrap?  (Compensated series form their
 // start at the end of the solve before.)
 bool plain_extrap(const pf_ctx* ctx) { return extrapolates(&ctx->prm) && !compensated(ctx); }
@@ -664,7 +671,7 @@ pf_status solve(pf_ctx* ctx, const T* P, bool adj = false, bool step_solve = fal
     for (int i = 0; i < batch; ++i) {
       const int it = issued + i + 1;
       before_launch(ctx);
-      pf::launch_cg_p<T>(ctx->L, g, d, mg, it == 1);
+      pf::launch_cg_p<T>(ctx->L, g, d, mg, it == 1, comp && mg && e == 0.0 && it == 2);
       // the multigrid first iteration stages z alone (p = z), except with eps
       // the second iteration of a compensated multigrid solve reads no x (still 0)
       const double cgp = (comp && mg && e == 0.0 && it == 2 ? 5 : 6 + 2 * e) * N * w;
@@ -725,8 +732,9 @@ void step_kernel_counts(const pf_ctx* ctx, int refresh, int64_t* fixed, int64_t*
   const bool heun = ctx->prm.integrator == PF_HEUN;
   const int64_t per_solve = (ctx->singular ? 2 : 0) + 2 + vc + (plain_extrap(ctx) ? 1 : 0);
   *per_iter = 2 + vc;
-  // graph-captured multigrid solves run their first iteration outside the loop
-  const int64_t peeled = vc ? *per_iter : 0;
+  // graph-captured multigrid solves run their first iteration (compensated
+  // ones their first two) outside the loop
+  const int64_t peeled = vc ? *per_iter * (peel_second(ctx) ? 2 : 1) : 0;
   *fixed = (refresh ? (heun ? 2 : 1) * (per_solve + peeled) : 0) + (heun ? 2 : 1);
 }
 
@@ -785,6 +793,11 @@ cudaError_t append_step(pf_ctx* ctx, cudaGraph_t graph, std::vector<cudaGraphNod
         pf::launch_cg_p<T>(ctx->L, g, d, mg, 1);
         pf::launch_cg_r<T>(ctx->L, g, d, mg, h, 1);
         vcycle<T>(ctx, 1);
+        if (peel_second(ctx)) {  // and so does the second (x still 0, not read)
+          pf::launch_cg_p<T>(ctx->L, g, d, mg, 0, 1);
+          pf::launch_cg_r<T>(ctx->L, g, d, mg, h, 1);
+          vcycle<T>(ctx, 2);
+        }
       }
     });
     if (e != cudaSuccess) return;
@@ -1074,8 +1087,12 @@ pf_status finish_info(pf_ctx* ctx, int nsteps, pf_step_info* info) {
     step_kernel_counts(ctx, 1, &fixed, &per_iter);
     // graph-launched steps: kernels = fixed part + one loop body per iteration
     // (multigrid: per iteration after the first, which is in the fixed part)
+    // loop bodies: the iterations past the peeled ones, sum of max(0, iters - peeled)
     const int64_t mg = ctx->prm.solver == PF_PCG_MG;
-    const int64_t bodies = mg ? s.total_iters + s.zero_solves - ctx->graph_solves : s.total_iters;
+    const int64_t bodies = !mg ? s.total_iters
+                           : peel_second(ctx)
+                               ? s.total_iters - 2 * ctx->graph_solves + s.zero_solves + s.short_solves
+                               : s.total_iters + s.zero_solves - ctx->graph_solves;
     info->kernel_launches = ctx->launches + (ctx->graph_steps ? ctx->graph_fixed + bodies * per_iter : 0);
     info->graph_steps = ctx->graph_steps;
     info->max_iters = s.max_iters;

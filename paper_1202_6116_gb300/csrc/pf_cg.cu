@@ -25,7 +25,10 @@ using CgPipe = Pipe<T, typename FieldOf<T, EPS>::type, MTX, MTY, VX, EPS ? 4 : 2
 // buffer); otherwise p goes through the march's shared field buffer.
 // FIRST (direct form, launched for a solve's first iteration only): p = z,
 // and neither p_old nor x is read (1 word read, 2 written per cell).
-template <typename T, bool EPS, bool MG, int VX, bool DIRECT = false, bool FIRST = false>
+// SECOND (direct form, launched for a compensated solve's second iteration
+// only): the correction x is still 0, so the deferred update writes alpha
+// p_old without staging or reading x (2 words read, 3 written per cell).
+template <typename T, bool EPS, bool MG, int VX, bool DIRECT = false, bool FIRST = false, bool SECOND = false>
 __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g, Bc<T> bc, const T* __restrict__ eps,
                                                   const T* __restrict__ invd, const T* __restrict__ r, T* p0,
                                                   T* p1, T* __restrict__ q, T* __restrict__ x, double* part,
@@ -35,11 +38,12 @@ __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g
   using F = typename FieldOf<T, EPS>::type;
   constexpr int NH = EPS ? 4 : 2;          // r or z, p_old (, eps, 1/diag) with halo
   static_assert(!FIRST || DIRECT, "the first-iteration form is the direct one");
+  static_assert(!SECOND || (DIRECT && !FIRST), "the second-iteration form is the direct one");
   if (S->done) return;
   const int first = FIRST ? 1 : S->first;
   // x still 0 (the correction of a compensated start, not written yet): the
-  // deferred update writes alpha p_old without reading x
-  const int xz = S->xzero;
+  // deferred update writes alpha p_old and ignores the staged x
+  const int xz = SECOND ? 1 : S->xzero;
   const T beta = first ? T(0) : T(S->beta);
   const T alpha = T(S->alpha);
   const int pb = S->pbuf;
@@ -136,7 +140,7 @@ __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g
       march_direct<T, Out, MTX, MTY, VX, 1, 0, CG_D>(g, s, smem, hs1, os1, emit_f, post);
     } else if constexpr (DIRECT) {
       static_assert(MG && !EPS, "the direct form is the multigrid search direction with eps = 1");
-      if (xz) {                        // x is not read: stage z and p_old alone
+      if constexpr (SECOND) {          // x is not read: stage z and p_old alone
         const T* const os0[1] = {nullptr};
         march_direct<T, Out, MTX, MTY, VX, NH, 0, CG_D>(g, s, smem, hsrc, os0, emit_d, post);
       } else {
@@ -249,33 +253,34 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_cg_r(Geo g, Bc<T> bc, const T*
   }
 }
 
-template <typename T, bool EPS, bool MG, int VX, bool FIRST>
+template <typename T, bool EPS, bool MG, int VX, bool FIRST, bool SECOND>
 static void launch_cg_p_t(const LaunchCfg& L, const Geo& g, const Dev<T>& d) {
   constexpr bool DIRECT = MG && !EPS;
-  using PD = Pipe<T, void, MTX, MTY, VX, FIRST ? 1 : 2, FIRST ? 0 : 1, CG_D>;
+  using PD = Pipe<T, void, MTX, MTY, VX, FIRST ? 1 : 2, (FIRST || SECOND) ? 0 : 1, CG_D>;
   const size_t bytes = DIRECT ? PD::bytes() : CgPipe<T, EPS, VX>::bytes();
   static bool once = false;
   if (!once) {
-    allow_smem(k_cg_p<T, EPS, MG, VX, DIRECT, FIRST>, bytes);
+    allow_smem(k_cg_p<T, EPS, MG, VX, DIRECT, FIRST, SECOND>, bytes);
     once = true;
   }
-  k_cg_p<T, EPS, MG, VX, DIRECT, FIRST><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(
+  k_cg_p<T, EPS, MG, VX, DIRECT, FIRST, SECOND><<<L.march.grid, dim3(MTX, MTY), bytes, L.stream>>>(
       g, d.bc, d.eps, d.invd, MG ? d.z : d.r, d.p0, d.p1, d.q, d.phi, d.part, d.S, L.march);
 }
 
-template <typename T, bool EPS, bool MG, bool FIRST = false>
+template <typename T, bool EPS, bool MG, bool FIRST = false, bool SECOND = false>
 static void launch_cg_p_v(const LaunchCfg& L, const Geo& g, const Dev<T>& d) {
   constexpr int V = 16 / sizeof(T);
-  if (L.march.vx == V) launch_cg_p_t<T, EPS, MG, V, FIRST>(L, g, d);
-  else launch_cg_p_t<T, EPS, MG, 1, FIRST>(L, g, d);
+  if (L.march.vx == V) launch_cg_p_t<T, EPS, MG, V, FIRST, SECOND>(L, g, d);
+  else launch_cg_p_t<T, EPS, MG, 1, FIRST, SECOND>(L, g, d);
 }
 
 template <typename T>
-void launch_cg_p(const LaunchCfg& L, const Geo& g, const Dev<T>& d, int mg, int first) {
+void launch_cg_p(const LaunchCfg& L, const Geo& g, const Dev<T>& d, int mg, int first, int second) {
   // with a permittivity field the multigrid form stages eps too (field-buffer
   // march; its first iteration reads the first-iteration flag of the solver)
   if (mg && d.eps) launch_cg_p_v<T, true, true>(L, g, d);
   else if (mg && first) launch_cg_p_v<T, false, true, true>(L, g, d);
+  else if (mg && second) launch_cg_p_v<T, false, true, false, true>(L, g, d);
   else if (mg) launch_cg_p_v<T, false, true>(L, g, d);
   else if (d.eps) launch_cg_p_v<T, true, false>(L, g, d);
   else launch_cg_p_v<T, false, false>(L, g, d);
@@ -313,8 +318,8 @@ int march_blocks_per_sm(int fp32, int eps) {
   return eps ? occ_cg_p<double, true, 2>() : occ_cg_p<double, false, 2>();
 }
 
-template void launch_cg_p<float>(const LaunchCfg&, const Geo&, const Dev<float>&, int, int);
-template void launch_cg_p<double>(const LaunchCfg&, const Geo&, const Dev<double>&, int, int);
+template void launch_cg_p<float>(const LaunchCfg&, const Geo&, const Dev<float>&, int, int, int);
+template void launch_cg_p<double>(const LaunchCfg&, const Geo&, const Dev<double>&, int, int, int);
 template void launch_cg_r<float>(const LaunchCfg&, const Geo&, const Dev<float>&, int, cudaGraphConditionalHandle,
                                  int);
 template void launch_cg_r<double>(const LaunchCfg&, const Geo&, const Dev<double>&, int,

@@ -108,6 +108,7 @@ struct Scalars {
   int zero_solves;                 // solves that ended with no iteration (per pf_step call)
   int max_iters;                   // most iterations of one solve (per pf_step call)
   int solves;                      // solves finished (per pf_step call)
+  int short_solves;                // solves that ended after at most one iteration (per pf_step call)
   int xzero;                       // 1: the Krylov iterate is the correction of a compensated
                                    // start and is still 0 (its buffer holds stale values)
 };

@@ -91,8 +91,10 @@ void launch_rhs(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, c
                 int use_cond);
 // mg = 1: the search direction is built from z (multigrid-preconditioned
 // CG) instead of r/diag, and k_cg_r leaves r.z and beta to the V-cycle.
+// second = 1: the second iteration of a compensated multigrid solve (x still
+// 0, not staged; needs eps = 1).
 template <typename T>
-void launch_cg_p(const LaunchCfg& L, const Geo& g, const Dev<T>& d, int mg, int first = 0);
+void launch_cg_p(const LaunchCfg& L, const Geo& g, const Dev<T>& d, int mg, int first = 0, int second = 0);
 template <typename T>
 void launch_cg_r(const LaunchCfg& L, const Geo& g, const Dev<T>& d, int mg, cudaGraphConditionalHandle cond,
                  int use_cond);

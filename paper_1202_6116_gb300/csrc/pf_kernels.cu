@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cg_finish(Geo g, T* __restrict__ x
       S->last_iters = S->iter;
       S->solves += 1;
       if (S->iter > S->max_iters) S->max_iters = S->iter;
+    if (S->iter < 2) S->short_solves += 1;
       if (S->status != 0) S->nonconv += 1;
       S->ticket = 0;
     }
@@ -233,6 +234,7 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_cg_finish_comp(long long n, fl
     S->last_iters = S->iter;
     S->solves += 1;
     if (S->iter > S->max_iters) S->max_iters = S->iter;
+    if (S->iter < 2) S->short_solves += 1;
     if (S->status != 0) S->nonconv += 1;
     S->ticket = 0;
     *cp.nsolve = k + 1;

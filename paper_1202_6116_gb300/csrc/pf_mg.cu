@@ -540,6 +540,9 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_coarse(MgView<T> C, int si
 // t + blockDim.x, ... of the nx x ny plane and walks them along z, so the
 // in-plane neighbour offsets, the face masks and the boundary diagonals are
 // formed once per column instead of from the linear index at every cell.
+// When the level has fewer columns than the block has threads (a deep, narrow
+// level such as 8 x 8 x 37), each column is cut into z chunks walked by
+// different threads.  body(o, x, y, z0, z1) walks planes [z0, z1).
 struct TailCol {
   int xy;                   // the column (y nx + x)
   int dxm, dxp, dym, dyp;   // offsets of the in-plane neighbours (periodic wrap)
@@ -548,8 +551,11 @@ struct TailCol {
 
 template <typename T, class Body>
 __device__ __forceinline__ void tail_cols(const MgView<T>& L, Body body) {
-  const int nx = L.g.nx, ny = L.g.ny, nxy = (int)L.g.nxy;
-  for (int col = threadIdx.x; col < nxy; col += blockDim.x) {
+  const int nx = L.g.nx, ny = L.g.ny, nxy = (int)L.g.nxy, nz = L.g.nz;
+  const int nch = nxy >= (int)blockDim.x ? 1 : min(nz, (int)blockDim.x / nxy);   // z chunks per column
+  for (int item = threadIdx.x; item < nxy * nch; item += blockDim.x) {
+    const int col = item % nxy, ch = item / nxy;
+    const int z0 = (int)((long long)ch * nz / nch), z1 = (int)((long long)(ch + 1) * nz / nch);
     const int y = col / nx, x = col - y * nx;
     TailCol o;
     o.xy = col;
@@ -559,7 +565,7 @@ __device__ __forceinline__ void tail_cols(const MgView<T>& L, Body body) {
     o.dyp = y == ny - 1 ? -(ny - 1) * nx : nx;
     o.dlo = L.g.periodic_z ? 0 : (int)L.tlo[col];
     o.dhi = L.g.periodic_z ? 0 : (int)L.thi[col];
-    body(o, x, y);
+    body(o, x, y, z0, z1);
   }
 }
 
@@ -629,8 +635,8 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int sing
     const MgView<T>& C = t.lv[k + 1];
     T *f = F(k), *e = E(k), *et = ET(k);
     const int nxy = (int)L.g.nxy, nz = L.g.nz;
-    tail_cols(L, [&](const TailCol& o, int, int) {
-      for (int z = 0; z < nz; ++z) {
+    tail_cols(L, [&](const TailCol& o, int, int, int z0, int z1) {
+      for (int z = z0; z < z1; ++z) {
         T inv;
         col_apply(L, f, o, z, inv);                       // only the diagonal is needed here
         const int c = z * nxy + o.xy;
@@ -638,8 +644,8 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int sing
       }
     });
     __syncthreads();
-    tail_cols(L, [&](const TailCol& o, int, int) {
-      for (int z = 0; z < nz; ++z) {
+    tail_cols(L, [&](const TailCol& o, int, int, int z0, int z1) {
+      for (int z = z0; z < z1; ++z) {
         T inv;
         const T Ae = col_apply(L, et, o, z, inv);
         const int c = z * nxy + o.xy;
@@ -649,8 +655,8 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int sing
     __syncthreads();
     // the residual (into e_tmp, free again), then the sum of each coarse
     // cell's children in the order dz, dy, dx
-    tail_cols(L, [&](const TailCol& o, int, int) {
-      for (int z = 0; z < nz; ++z) {
+    tail_cols(L, [&](const TailCol& o, int, int, int z0, int z1) {
+      for (int z = z0; z < z1; ++z) {
         T inv;
         const T Ae = col_apply(L, e, o, z, inv);
         const int c = z * nxy + o.xy;
@@ -660,9 +666,9 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int sing
     __syncthreads();
     const T scale = T(1) / T(L.fx * L.fy * L.fz);
     T* fc = F(k + 1);
-    const int ncxy = (int)C.g.nxy, ncz = C.g.nz;
-    tail_cols(C, [&](const TailCol& o, int X, int Y) {
-      for (int Z = 0; Z < ncz; ++Z) {
+    const int ncxy = (int)C.g.nxy;
+    tail_cols(C, [&](const TailCol& o, int X, int Y, int z0, int z1) {
+      for (int Z = z0; Z < z1; ++Z) {
         T acc = T(0);
         for (int dz = 0; dz < L.fz; ++dz)
           for (int dy = 0; dy < L.fy; ++dy)
@@ -681,13 +687,13 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int sing
     T *f = F(k), *e = E(k), *et = ET(k);
     const T* ec = E(k + 1);
     const int nxy = (int)L.g.nxy, nz = L.g.nz;
-    tail_cols(L, [&](const TailCol& o, int x, int y) {
+    tail_cols(L, [&](const TailCol& o, int x, int y, int z0, int z1) {
       const int pxy = (y >> (L.fy - 1)) * C.g.nx + (x >> (L.fx - 1));
-      for (int z = 0; z < nz; ++z) e[z * nxy + o.xy] += ec[(z >> (L.fz - 1)) * (int)C.g.nxy + pxy];
+      for (int z = z0; z < z1; ++z) e[z * nxy + o.xy] += ec[(z >> (L.fz - 1)) * (int)C.g.nxy + pxy];
     });
     __syncthreads();
-    tail_cols(L, [&](const TailCol& o, int, int) {
-      for (int z = 0; z < nz; ++z) {
+    tail_cols(L, [&](const TailCol& o, int, int, int z0, int z1) {
+      for (int z = z0; z < z1; ++z) {
         T inv;
         const T Ae = col_apply(L, e, o, z, inv);
         const int c = z * nxy + o.xy;
@@ -696,8 +702,8 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int sing
     });
     __syncthreads();
     T* eo = k == 0 ? t.lv[0].e : e;                    // the first level's result goes to global memory
-    tail_cols(L, [&](const TailCol& o, int, int) {
-      for (int z = 0; z < nz; ++z) {
+    tail_cols(L, [&](const TailCol& o, int, int, int z0, int z1) {
+      for (int z = z0; z < z1; ++z) {
         T inv;
         const T Ae = col_apply(L, et, o, z, inv);
         const int c = z * nxy + o.xy;
