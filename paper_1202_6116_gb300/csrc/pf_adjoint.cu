@@ -99,6 +99,8 @@ __global__ void __launch_bounds__(MTX* MTY) k_tdgl_adj(Geo g, Bc<T> bc, const T*
     return L3<T>{out[0], out[1], out[2]};
   };
   auto post = [&](int z, const L3<T> (&ov)[VX]) {
+#pragma unroll
+    for (int q = 0; q < ADJ_NV; ++q) acc[q].run();
     const long long c = (long long)z * g.nxy + s.xy;
     T a[VX], b[VX], d[VX];
 #pragma unroll
@@ -111,8 +113,8 @@ __global__ void __launch_bounds__(MTX* MTY) k_tdgl_adj(Geo g, Bc<T> bc, const T*
     store_n<T, VX>(lam_out + g.n + c, b);
     store_n<T, VX>(lam_out + 2 * g.n + c, d);
   };
-  const TileSched ts{&S->sched_next, &S->sched_done};
-  for (long long t = sched_take(ts, &tile_slot); t < mc.ntiles; t = sched_take(ts, &tile_slot)) {
+  const TileSched ts{&S->sched_next, &S->sched_done, mc.ntiles};
+  for (long long t = sched_first(ts, &tile_slot); t < mc.ntiles; t = sched_next(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(g, t, mc);
 #pragma unroll
     for (int q = 0; q < ADJ_NV; ++q) acc[q] = Acc<T>();

@@ -29,7 +29,7 @@ using CgPipe = Pipe<T, typename FieldOf<T, EPS>::type, MTX, MTY, VX, EPS ? 4 : 2
 // only): the correction x is still 0, so the deferred update writes alpha
 // p_old without staging or reading x (2 words read, 3 written per cell).
 template <typename T, bool EPS, bool MG, int VX, bool DIRECT = false, bool FIRST = false, bool SECOND = false>
-__global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g, Bc<T> bc, const T* __restrict__ eps,
+__global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? 3 : 2) k_cg_p(Geo g, Bc<T> bc, const T* __restrict__ eps,
                                                   const T* __restrict__ invd, const T* __restrict__ r, T* p0,
                                                   T* p1, T* __restrict__ q, T* __restrict__ x, double* part,
                                                   Scalars* S, MarchCfg mc) {
@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g
     return Out{first ? o[0] : (xz ? alpha * h[1] : o[0] + alpha * h[1]), pc, qv};
   };
   auto post = [&](int z, const Out (&ov)[VX]) {
+    apq.run();
     const long long c = (long long)z * g.nxy + s.xy;
     T xs[VX], ps[VX], qs[VX];
 #pragma unroll
@@ -121,8 +122,8 @@ __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_cg_p(Geo g
     apq.add(st.c, qv);
     return Out{first ? o[0] : (xz ? alpha * sr.c.v[1] : o[0] + alpha * sr.c.v[1]), st.c, qv};
   };
-  const TileSched ts{&S->sched_next, &S->sched_done};
-  for (long long t = sched_take(ts, &tile_slot); t < mc.ntiles; t = sched_take(ts, &tile_slot)) {
+  const TileSched ts{&S->sched_next, &S->sched_done, mc.ntiles};
+  for (long long t = sched_first(ts, &tile_slot); t < mc.ntiles; t = sched_next(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(g, t, mc);
     apq = Acc<T>();
     if constexpr (DIRECT && FIRST) {
@@ -209,6 +210,8 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_cg_r(Geo g, Bc<T> bc, const T*
 #pragma unroll
     for (int k = 0; k < NV; ++k) one(i * NV + k, rs[k], qs[k]);
     reinterpret_cast<V*>(r)[i] = rv;
+    arr.run();
+    arz.run();
     if (++cnt == 16) {
       arr.flush();
       arz.flush();

@@ -122,11 +122,15 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Dot-product accumulators.  FP64 fields: plain FMA accumulation.  FP32
-// fields: the compensated dot product "Dot2" of Ogita, Rump & Oishi (SIAM J.
-// Sci. Comput. 26, 2005) -- the exact product by TwoProduct (one FMA) and a
-// TwoSum of the running sum, with the error terms collected in a second
-// float -- flushed into an FP64 total after every short run of cells, so the
-// FP64 unit sees a handful of adds per column instead of one per cell.
+// fields: a short run of products (the cells of one vector, closed by run())
+// is summed by plain FMAs; the run totals are summed with TwoSum (Knuth), the
+// error terms collected in a second float ("cascaded" summation: the
+// compensated sum of Ogita, Rump & Oishi, SIAM J. Sci. Comput. 26, 2005,
+// applied to runs instead of single products); flush() moves the pair into an
+// FP64 total, so the FP64 unit sees a handful of adds per tile.  A run of k
+// products carries a relative error of about k u (u = 2^-24) of its absolute
+// sum, so with k = 4 the dot keeps close to FP32 working accuracy of the
+// absolute sum instead of the growth with the length of a plain FP32 sum.
 template <typename T>
 struct Acc;
 
@@ -134,29 +138,32 @@ template <>
 struct Acc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ void run() {}
   __device__ __forceinline__ void flush() {}
   __device__ __forceinline__ double value() const { return s; }
 };
 
 template <>
 struct Acc<float> {
-  float hi = 0.f, lo = 0.f;
+  float part = 0.f;               // the current run
+  float hi = 0.f, lo = 0.f;       // compensated sum of the closed runs
   double tot = 0.0;
-  __device__ __forceinline__ void add(float a, float b) {
-    float p = a * b;
-    float pe = fmaf(a, b, -p);            // a*b = p + pe exactly
-    float s = __fadd_rn(hi, p);
-    float z = __fsub_rn(s, hi);
-    float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, z)), __fsub_rn(p, z));  // hi + p = s + se
+  __device__ __forceinline__ void add(float a, float b) { part = fmaf(a, b, part); }
+  __device__ __forceinline__ void run() {
+    const float s = __fadd_rn(hi, part);
+    const float z = __fsub_rn(s, hi);
+    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, z)), __fsub_rn(part, z));  // hi + part = s + se
     hi = s;
-    lo = __fadd_rn(lo, __fadd_rn(pe, se));
+    lo = __fadd_rn(lo, se);
+    part = 0.f;
   }
   __device__ __forceinline__ void flush() {
+    run();
     tot += (double)hi + (double)lo;
     hi = 0.f;
     lo = 0.f;
   }
-  __device__ __forceinline__ double value() const { return tot + (double)hi + (double)lo; }
+  __device__ __forceinline__ double value() const { return tot + (double)hi + (double)lo + (double)part; }
 };
 
 // Block-reduce NV values, publish the block's partials, and tell whether this

@@ -69,9 +69,12 @@ __global__ void __launch_bounds__(MTX* MTY) k_diag(Geo g, Bc<T> bc, const T* __r
     }
     return T(0);
   };
-  auto post = [&](int, const T (&)[VX]) {};
-  const TileSched ts{&S->sched_next, &S->sched_done};
-  for (long long t = sched_take(ts, &tile_slot); t < mc.ntiles; t = sched_take(ts, &tile_slot)) {
+  auto post = [&](int, const T (&)[VX]) {
+#pragma unroll
+    for (int q = 0; q < DIAG_NV; ++q) acc[q].run();
+  };
+  const TileSched ts{&S->sched_next, &S->sched_done, mc.ntiles};
+  for (long long t = sched_first(ts, &tile_slot); t < mc.ntiles; t = sched_next(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(g, t, mc);
 #pragma unroll
     for (int q = 0; q < DIAG_NV; ++q) acc[q] = Acc<T>();

@@ -185,11 +185,16 @@ struct Pipe {
   static constexpr size_t bytes() { return (size_t)NS * STAGE * sizeof(T) + field_bytes(); }
 };
 
-// Dynamic tile scheduler: thread 0 takes the next tile from an atomic
-// counter; the last block to run out resets the counter for the next launch.
+// Tile scheduler.  A grid with a block per tile (the small multigrid levels)
+// takes tile blockIdx.x and touches no counter.  Otherwise tiles are handed
+// out dynamically: thread 0 takes the next tile from an atomic counter, and
+// the last block to run out resets the counter for the next launch.
 struct TileSched {
   unsigned long long* next;
   unsigned* done;
+  bool fixed;                      // a block per tile: tile blockIdx.x, no counter
+  __device__ __forceinline__ TileSched(unsigned long long* n, unsigned* d, long long ntiles)
+      : next(n), done(d), fixed((long long)gridDim.x >= ntiles) {}
 };
 
 __device__ __forceinline__ long long sched_take(const TileSched& ts, long long* slot) {
@@ -199,7 +204,17 @@ __device__ __forceinline__ long long sched_take(const TileSched& ts, long long* 
   return *slot;
 }
 
+__device__ __forceinline__ long long sched_first(const TileSched& ts, long long* slot) {
+  return ts.fixed ? (long long)blockIdx.x : sched_take(ts, slot);
+}
+
+// the next tile; past every tile (so the caller's loop ends) in the fixed form
+__device__ __forceinline__ long long sched_next(const TileSched& ts, long long* slot) {
+  return ts.fixed ? (1LL << 62) : sched_take(ts, slot);
+}
+
 __device__ __forceinline__ void sched_finish(const TileSched& ts) {
+  if (ts.fixed) return;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     __threadfence();
     if (atomicAdd(ts.done, 1u) == gridDim.x - 1) {

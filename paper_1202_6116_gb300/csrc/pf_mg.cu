@@ -141,7 +141,7 @@ using MgPipeD = Pipe<T, void, MTX, MTY, VX, E ? 2 : 1, E ? 2 : 1, MG_D>;
 // w1 diag^-1 A f there; on the planes next to a z face and their neighbour
 // planes e1 is formed per neighbour with its own diagonal.
 template <typename T, int VX, bool EPS>
-__global__ void __launch_bounds__(MTX* MTY) k_mg_pre(MgView<T> L, Scalars* S) {
+__global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? 4 : 2) k_mg_pre(MgView<T> L, Scalars* S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   if (S->done) return;
@@ -209,8 +209,8 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_pre(MgView<T> L, Scalars* S) {
     }
   };
   auto post = [&](int z, const T (&ov)[VX]) { store_n<T, VX>(L.e + (long long)z * L.g.nxy + s.xy, ov); };
-  const TileSched ts{&S->sched_next, &S->sched_done};
-  for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
+  const TileSched ts{&S->sched_next, &S->sched_done, L.mc.ntiles};
+  for (long long t = sched_first(ts, &tile_slot); t < L.mc.ntiles; t = sched_next(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
     march_direct<T, T, MTX, MTY, VX, NH, 0, MG_D>(L.g, s, smem, hsrc, osrc, emit, post);
   }
@@ -277,8 +277,8 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Sc
       for (int j = 0; j < cnt; ++j) dst[j] = v[j] * scale;
     }
   };
-  const TileSched ts{&S->sched_next, &S->sched_done};
-  for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
+  const TileSched ts{&S->sched_next, &S->sched_done, L.mc.ntiles};
+  for (long long t = sched_first(ts, &tile_slot); t < L.mc.ntiles; t = sched_next(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
     march_direct<T, T, MTX, MTY, VX, NH, 1, MG_D>(L.g, s, smem, hsrc, osrc, emit, post);
   }
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Sc
 // stencil field is e + e_c(parent), the parents staged with the fine planes
 // and combined with e at each of the seven cells.
 template <typename T, int VX, bool EPS>
-__global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_mg_post1(MgView<T> L, MgView<T> C, Scalars* S) {
+__global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? 3 : 2) k_mg_post1(MgView<T> L, MgView<T> C, Scalars* S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   if (S->done) return;
@@ -335,8 +335,8 @@ __global__ void __launch_bounds__(MTX* MTY, sizeof(T) == 4 ? 3 : 2) k_mg_post1(M
     }
   };
   auto post = [&](int z, const T (&ov)[VX]) { store_n<T, VX>(L.et + (long long)z * L.g.nxy + s.xy, ov); };
-  const TileSched ts{&S->sched_next, &S->sched_done};
-  for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
+  const TileSched ts{&S->sched_next, &S->sched_done, L.mc.ntiles};
+  for (long long t = sched_first(ts, &tile_slot); t < L.mc.ntiles; t = sched_next(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
     march_direct<T, T, MTX, MTY, VX, NH, NO, MG_D, 1>(L.g, s, smem, hsrc, osrc, emit, post, par);
   }
@@ -377,9 +377,12 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_post2(MgView<T> L, double* part
     if (LAST) arz.add(o[0], e);
     return e;
   };
-  auto post = [&](int z, const T (&ov)[VX]) { store_n<T, VX>(L.e + (long long)z * L.g.nxy + s.xy, ov); };
-  const TileSched ts{&S->sched_next, &S->sched_done};
-  for (long long t = sched_take(ts, &tile_slot); t < L.mc.ntiles; t = sched_take(ts, &tile_slot)) {
+  auto post = [&](int z, const T (&ov)[VX]) {
+    if (LAST) arz.run();
+    store_n<T, VX>(L.e + (long long)z * L.g.nxy + s.xy, ov);
+  };
+  const TileSched ts{&S->sched_next, &S->sched_done, L.mc.ntiles};
+  for (long long t = sched_first(ts, &tile_slot); t < L.mc.ntiles; t = sched_next(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
     arz = Acc<T>();
     march_direct<T, T, MTX, MTY, VX, NH, NO, MG_D>(L.g, s, smem, hsrc, osrc, emit, post);
@@ -569,11 +572,23 @@ __device__ __forceinline__ void tail_cols(const MgView<T>& L, Body body) {
   }
 }
 
+// 1/diag at plane z of a column (eps = 1); iint: the interior value.
+template <typename T>
+__device__ __forceinline__ T col_inv(const MgView<T>& L, const TailCol& o, int z, T iint) {
+  const int nz = L.g.nz;
+  if (L.g.periodic_z || (z > 0 && z < nz - 1)) return iint;
+  int cz = 2;
+  if (z == 0) cz += 2 * o.dlo - 1;
+  if (z == nz - 1) cz += 2 * o.dhi - 1;
+  return T(1) / (T(2) * L.ax + T(2) * L.ay + T(cz) * L.az);
+}
+
 // (A v) at plane z of a column and 1/diag there: the same operator, face
 // order and diagonal as the sweep kernels (per-direction 1/h^2; with eps the
-// harmonic-mean face weights and the precomputed 1/diag).
+// harmonic-mean face weights and the precomputed 1/diag; iint: the interior
+// 1/diag with eps = 1, so only the face planes divide).
 template <typename T>
-__device__ __forceinline__ T col_apply(const MgView<T>& L, const T* v, const TailCol& o, int z, T& inv) {
+__device__ __forceinline__ T col_apply(const MgView<T>& L, const T* v, const TailCol& o, int z, T& inv, T iint) {
   const int nz = L.g.nz, nxy = (int)L.g.nxy;
   const int c = z * nxy + o.xy;
   const T vc = v[c];
@@ -595,12 +610,11 @@ __device__ __forceinline__ T col_apply(const MgView<T>& L, const T* v, const Tai
   const T sx = (vc - v[c + o.dxm]) + (vc - v[c + o.dxp]);
   const T sy = (vc - v[c + o.dym]) + (vc - v[c + o.dyp]);
   T sz = T(0);
-  int cz = 2;
   if (zm >= 0) sz += vc - v[zm];
-  else { cz += 2 * o.dlo - 1; if (o.dlo) sz += T(2) * vc; }
+  else if (o.dlo) sz += T(2) * vc;
   if (zp >= 0) sz += vc - v[zp];
-  else { cz += 2 * o.dhi - 1; if (o.dhi) sz += T(2) * vc; }
-  inv = T(1) / (T(2) * L.ax + T(2) * L.ay + T(cz) * L.az);
+  else if (o.dhi) sz += T(2) * vc;
+  inv = col_inv(L, o, z, iint);
   return L.ax * sx + L.ay * sy + L.az * sz;
 }
 
@@ -635,11 +649,11 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int sing
     const MgView<T>& C = t.lv[k + 1];
     T *f = F(k), *e = E(k), *et = ET(k);
     const int nxy = (int)L.g.nxy, nz = L.g.nz;
+    const T iint = mg_inv_int(L);
     tail_cols(L, [&](const TailCol& o, int, int, int z0, int z1) {
       for (int z = z0; z < z1; ++z) {
-        T inv;
-        col_apply(L, f, o, z, inv);                       // only the diagonal is needed here
         const int c = z * nxy + o.xy;
+        const T inv = L.eps ? L.invd[c] : col_inv(L, o, z, iint);
         et[c] = om1 * inv * f[c];
       }
     });
@@ -647,7 +661,7 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int sing
     tail_cols(L, [&](const TailCol& o, int, int, int z0, int z1) {
       for (int z = z0; z < z1; ++z) {
         T inv;
-        const T Ae = col_apply(L, et, o, z, inv);
+        const T Ae = col_apply(L, et, o, z, inv, iint);
         const int c = z * nxy + o.xy;
         e[c] = et[c] + om2 * inv * (f[c] - Ae);
       }
@@ -658,7 +672,7 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int sing
     tail_cols(L, [&](const TailCol& o, int, int, int z0, int z1) {
       for (int z = z0; z < z1; ++z) {
         T inv;
-        const T Ae = col_apply(L, e, o, z, inv);
+        const T Ae = col_apply(L, e, o, z, inv, iint);
         const int c = z * nxy + o.xy;
         et[c] = f[c] - Ae;
       }
@@ -687,6 +701,7 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int sing
     T *f = F(k), *e = E(k), *et = ET(k);
     const T* ec = E(k + 1);
     const int nxy = (int)L.g.nxy, nz = L.g.nz;
+    const T iint = mg_inv_int(L);
     tail_cols(L, [&](const TailCol& o, int x, int y, int z0, int z1) {
       const int pxy = (y >> (L.fy - 1)) * C.g.nx + (x >> (L.fx - 1));
       for (int z = z0; z < z1; ++z) e[z * nxy + o.xy] += ec[(z >> (L.fz - 1)) * (int)C.g.nxy + pxy];
@@ -695,7 +710,7 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int sing
     tail_cols(L, [&](const TailCol& o, int, int, int z0, int z1) {
       for (int z = z0; z < z1; ++z) {
         T inv;
-        const T Ae = col_apply(L, e, o, z, inv);
+        const T Ae = col_apply(L, e, o, z, inv, iint);
         const int c = z * nxy + o.xy;
         et[c] = e[c] + om2 * inv * (f[c] - Ae);
       }
@@ -705,7 +720,7 @@ __global__ void __launch_bounds__(MG_MAX_COARSE) k_mg_tail(MgTail<T> t, int sing
     tail_cols(L, [&](const TailCol& o, int, int, int z0, int z1) {
       for (int z = z0; z < z1; ++z) {
         T inv;
-        const T Ae = col_apply(L, et, o, z, inv);
+        const T Ae = col_apply(L, et, o, z, inv, iint);
         const int c = z * nxy + o.xy;
         eo[c] = et[c] + om1 * inv * (f[c] - Ae);
       }

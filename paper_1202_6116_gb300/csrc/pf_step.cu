@@ -129,10 +129,15 @@ __global__ void __launch_bounds__(MTX* MTY) k_rhs(Geo g, Bc<T> bc, const T* __re
     return rv;
   };
   auto post = [&](int z, const T (&ov)[VX]) {
-    if (!MEAN) store_n<T, VX>(r + (long long)z * g.nxy + s.xy, ov);
+    abb.run();
+    if (!MEAN) {
+      arr.run();
+      arz.run();
+      store_n<T, VX>(r + (long long)z * g.nxy + s.xy, ov);
+    }
   };
-  const TileSched ts{&S->sched_next, &S->sched_done};
-  for (long long t = sched_take(ts, &tile_slot); t < mc.ntiles; t = sched_take(ts, &tile_slot)) {
+  const TileSched ts{&S->sched_next, &S->sched_done, mc.ntiles};
+  for (long long t = sched_first(ts, &tile_slot); t < mc.ntiles; t = sched_next(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(g, t, mc);
     abb = Acc<T>();
     arr = Acc<T>();
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_rhs(Geo g, Bc<T> bc, const T* __re
 
 template <typename T>
 struct Coef {
-  T a1, a11, a12, g, dtL;
+  T c1, c11, c12, g, dtL;        // c1 = 2 a1, c11 = 4 a11, c12 = 2 a12 (exact scalings)
   T amp;                         // thermal random force: sigma sqrt(dt) (0: off)
   unsigned long long seed;
   long long* step;               // device step counter (steps since pf_bind)
@@ -202,20 +207,7 @@ struct P6 {
   T x, y, z, lx, ly, lz;
 };
 
-// VX bf16 remainders <-> floats (8-byte accesses for a 4-cell vector).
-template <int VX>
-__device__ __forceinline__ void load_bf16(const unsigned short* p, float (&o)[VX]) {
-  if constexpr (VX == 4) {
-    const uint2 u = *reinterpret_cast<const uint2*>(p);
-    o[0] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(u.x & 0xffffu)));
-    o[1] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(u.x >> 16)));
-    o[2] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(u.y & 0xffffu)));
-    o[3] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(u.y >> 16)));
-  } else {
-#pragma unroll
-    for (int i = 0; i < VX; ++i) o[i] = __bfloat162float(__ushort_as_bfloat16(p[i]));
-  }
-}
+// VX floats -> bf16 remainders (one 8-byte store for a 4-cell vector).
 template <int VX>
 __device__ __forceinline__ void store_bf16(unsigned short* p, const float (&v)[VX]) {
   unsigned short b[VX];
@@ -228,6 +220,34 @@ __device__ __forceinline__ void store_bf16(unsigned short* p, const float (&v)[V
 #pragma unroll
     for (int i = 0; i < VX; ++i) p[i] = b[i];
   }
+}
+
+// VX bf16 values kept packed in registers (two per 32-bit word) and widened
+// one at a time: a bf16 is the upper half of the float with the same value.
+template <int VX>
+struct Bf16x {
+  unsigned w[(VX + 1) / 2];
+};
+template <int VX>
+__device__ __forceinline__ Bf16x<VX> load_bf16x(const unsigned short* p) {
+  Bf16x<VX> r;
+  if constexpr (VX == 4) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    r.w[0] = u.x;
+    r.w[1] = u.y;
+  } else if constexpr (VX == 2) {
+    r.w[0] = *reinterpret_cast<const unsigned*>(p);
+  } else {
+#pragma unroll
+    for (int i = 0; i < (VX + 1) / 2; ++i) r.w[i] = 0u;
+#pragma unroll
+    for (int i = 0; i < VX; ++i) r.w[i >> 1] |= (unsigned)p[i] << ((i & 1) * 16);
+  }
+  return r;
+}
+template <int VX>
+__device__ __forceinline__ float bf16x_at(const Bf16x<VX>& r, int i) {
+  return __uint_as_float(((r.w[i >> 1] >> ((i & 1) * 16)) & 0xffffu) << 16);
 }
 
 // a + b = s + e exactly (TwoSum, Knuth): no condition on the magnitudes.
@@ -252,7 +272,14 @@ __global__ void __launch_bounds__(MTX* MTY, 2) k_tdgl(Geo g, Bc<T> bc, const T* 
   const T* hsrc[4] = {P, P + g.n, P + 2 * g.n, phi};
   const T* osrc[1] = {nullptr};
   TileGeo<MTX, MTY, VX> s;
-  T lov[3][VX];                      // remainders of the own vector (COMP), loaded with its first cell
+  // remainders of the own vector (COMP), packed: those of plane z are loaded
+  // while plane z - 1 is stored, so their latency hides behind a plane of work
+  Bf16x<VX> lraw[3];
+  auto load_lo = [&](int z) {
+    const long long c0 = (long long)z * g.nxy + s.xy;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) lraw[i] = load_bf16x<VX>(Plo + i * g.n + c0);
+  };
   auto emit = [&](int xy, int z, const Stencil7<Raw<T, 4>>& st, const T (&)[1], bool) -> Out {
     // E = -grad phi from face values (mean inside, V at an electrode, phi_cell at an open face)
     const T fc = st.c.v[3];
@@ -270,8 +297,7 @@ __global__ void __launch_bounds__(MTX* MTY, 2) k_tdgl(Geo g, Bc<T> bc, const T* 
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int j = (i + 1) % 3, l = (i + 2) % 3;
-      const T hi = T(2) * k.a1 * p[i] + T(4) * k.a11 * p[i] * p[i] * p[i] +
-                   T(2) * k.a12 * p[i] * (p[j] * p[j] + p[l] * p[l]);
+      const T hi = k.c1 * p[i] + k.c11 * p[i] * p[i] * p[i] + k.c12 * p[i] * (p[j] * p[j] + p[l] * p[l]);
       T lap = T(0);
       lap += st.xm.v[i] - p[i];
       lap += st.xp.v[i] - p[i];
@@ -286,16 +312,10 @@ __global__ void __launch_bounds__(MTX* MTY, 2) k_tdgl(Geo g, Bc<T> bc, const T* 
     if constexpr (NOISE && !CORR) gauss3<T>((unsigned long long)z * g.nxy + xy, nstep, k.seed, gz);
     if constexpr (COMP) {
       const int iv = xy - s.xy;                     // index inside the own vector
-      if (iv == 0) {
-        const long long c0 = (long long)z * g.nxy + s.xy;
-        load_bf16<VX>(Plo + c0, lov[0]);
-        load_bf16<VX>(Plo + g.n + c0, lov[1]);
-        load_bf16<VX>(Plo + 2 * g.n + c0, lov[2]);
-      }
       T hv[3], lv[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        T d = lov[i][iv] + inc[i];
+        T d = bf16x_at(lraw[i], iv) + inc[i];
         if constexpr (NOISE) d += k.amp * gz[i];
         two_sum(p[i], d, hv[i], lv[i]);
       }
@@ -312,6 +332,9 @@ __global__ void __launch_bounds__(MTX* MTY, 2) k_tdgl(Geo g, Bc<T> bc, const T* 
   };
   auto post = [&](int z, const Out (&ov)[VX]) {
     const long long c = (long long)z * g.nxy + s.xy;
+    if constexpr (COMP) {
+      if (z + 1 < s.z1) load_lo(z + 1);          // the next plane's remainders (the own cells of plane z are done)
+    }
     T a[VX], b[VX], d[VX];
     if (z >= g.zair) {                 // air layers carry no polarization
 #pragma unroll
@@ -373,9 +396,12 @@ __global__ void __launch_bounds__(MTX* MTY, 2) k_tdgl(Geo g, Bc<T> bc, const T* 
     store_n<T, VX>(Pn + g.n + c, b);
     store_n<T, VX>(Pn + 2 * g.n + c, d);
   };
-  const TileSched ts{&S->sched_next, &S->sched_done};
-  for (long long t = sched_take(ts, &tile_slot); t < mc.ntiles; t = sched_take(ts, &tile_slot)) {
+  const TileSched ts{&S->sched_next, &S->sched_done, mc.ntiles};
+  for (long long t = sched_first(ts, &tile_slot); t < mc.ntiles; t = sched_next(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(g, t, mc);
+    if constexpr (COMP) {
+      if (s.act) load_lo(s.z0);
+    }
     march_direct<T, Out, MTX, MTY, VX, 4, 0, STEP_D>(g, s, smem, hsrc, osrc, emit, post);
   }
   // sched_finish, with the step counter advanced by the last block to finish
@@ -475,7 +501,8 @@ static void tdgl_v(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P
 template <typename T>
 void launch_tdgl(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, T* Pn, const double* coef,
                  int corr, const Noise& nz) {
-  Coef<T> k{T(coef[0]), T(coef[1]), T(coef[2]), T(coef[3]), T(coef[4]), T(nz.amp), nz.seed, nz.step, nz.advance};
+  Coef<T> k{T(2) * T(coef[0]), T(4) * T(coef[1]), T(2) * T(coef[2]), T(coef[3]), T(coef[4]), T(nz.amp), nz.seed,
+            nz.step, nz.advance};
   const bool noise = nz.amp != 0.0;
   if (corr) {
     if (noise) tdgl_v<T, true, true>(L, g, d, P, Pn, k);
