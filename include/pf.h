@@ -391,7 +391,13 @@ typedef struct {
   int32_t tz;                /* z planes per tile (z-block depth), 1 .. 64 */
   int32_t blocks_per_sm;     /* resident blocks per SM the grid is sized for
                                 (0: as many as fit); tiles are handed out dynamically */
-  int32_t reserved;          /* must be zero */
+  int32_t mg_whole;          /* multigrid sweeps: 0 (default) runs the pre-smoother, the
+                                prolongation sweep and the coarse levels' second post-sweep
+                                of a level of >= 2^25 cells (2^23 with eps) whose z faces
+                                are not periodic as two launches, the interior planes with
+                                the face code compiled out and the two face slabs of 2
+                                planes; 1 runs every sweep as one launch.  Results are
+                                identical either way. */
 } pf_tiling;
 
 /* Current tiling (the default picks vx = 16 bytes when nx allows it and the

@@ -255,6 +255,7 @@ struct pf_ctx {
   double noise_sigma = 0.0;       // thermal random force (pf_set_noise)
   unsigned long long noise_seed = 0;
   int tile_bps = 0;               // blocks per SM requested by pf_set_tiling (0: as many as fit)
+  int mg_whole = 0;               // 1: no multigrid sweep is split into interior and face launches
   cudaStream_t cap_stream = nullptr;
   bool async_open = false;        // pf_step_async work enqueued since the last pf_step_wait
   int64_t async_steps = 0;        // steps of that work
@@ -436,6 +437,7 @@ pf::MgView<T> mg_view(pf_ctx* ctx, size_t k) {
     v.invd = (const T*)(ctx->ws + (k == 0 ? ctx->lay.invd : l.invd));
   }
   v.mc = l.mc;
+  v.split = !ctx->mg_whole && pf::mg_split_level(l.n(), l.nz, ctx->prm.periodic_z, ctx->prm.has_eps) ? 1 : 0;
   return v;
 }
 
@@ -493,10 +495,12 @@ void vcycle(pf_ctx* ctx, int j) {
     const pf::MgView<T> lv = mg_view<T>(ctx, k), cv = mg_view<T>(ctx, k + 1);
     const double N = (double)lv.g.n;
     before_launch(ctx);
-    pf::launch_mg_pre<T>(ctx->L, lv, S);
+    int nk = pf::launch_mg_pre<T>(ctx->L, lv, S);
     after_launch(ctx, mg_fam(F_MG_PRE, k), (2 + 2 * e) * N * w, 2, j);
-    pf::launch_mg_rr<T>(ctx->L, lv, cv, S);
+    ctx->launches += nk - 1;
+    nk = pf::launch_mg_rr<T>(ctx->L, lv, cv, S);
     after_launch(ctx, mg_fam(F_MG_RR, k), (2 + e + 1.0 / (lv.fx * lv.fy * lv.fz)) * N * w, 2, j);
+    ctx->launches += nk - 1;
   }
   if (k0 + 1 < nl) {
     pf::MgTail<T> t{};
@@ -522,10 +526,12 @@ void vcycle(pf_ctx* ctx, int j) {
     const pf::MgView<T> lv = mg_view<T>(ctx, k), cv = mg_view<T>(ctx, k + 1);
     const double N = (double)lv.g.n;
     before_launch(ctx);
-    pf::launch_mg_post1<T>(ctx->L, lv, cv, S);
+    int nk = pf::launch_mg_post1<T>(ctx->L, lv, cv, S);
     after_launch(ctx, mg_fam(F_MG_POST1, k), (3 + 2 * e + 1.0 / (lv.fx * lv.fy * lv.fz)) * N * w, 2, j);
-    pf::launch_mg_post2<T>(ctx->L, lv, k == 0, part, S);
+    ctx->launches += nk - 1;
+    nk = pf::launch_mg_post2<T>(ctx->L, lv, k == 0, part, S);
     after_launch(ctx, mg_fam(F_MG_POST2, k), (3 + 2 * e) * N * w, 2, j);
+    ctx->launches += nk - 1;
   }
 }
 
@@ -725,10 +731,22 @@ bool refresh_step(const pf_ctx* ctx) {
 }
 
 // Kernels of one step outside the Krylov loops, and per Krylov iteration.
+// Kernels of one V-cycle: four per level above the tail (two for a split
+// level's pre and post1, and for its post2 below the finest), plus the tail or
+// the coarse solve.
+int64_t vcycle_kernels(const pf_ctx* ctx) {
+  const size_t k0 = mg_tail_start(ctx->lay, ctx->prm.precision == PF_FP32 ? 4 : 8);
+  int64_t n = 1;
+  for (size_t k = 0; k < k0; ++k) {
+    const MgLevelHost& l = ctx->lay.mg[k];
+    const bool split = !ctx->mg_whole && pf::mg_split_level(l.n(), l.nz, ctx->prm.periodic_z, ctx->prm.has_eps);
+    n += 4 + (split ? (k == 0 ? 2 : 3) : 0);
+  }
+  return n;
+}
+
 void step_kernel_counts(const pf_ctx* ctx, int refresh, int64_t* fixed, int64_t* per_iter) {
-  const int64_t vc = ctx->prm.solver == PF_PCG_MG
-                         ? 4 * (int64_t)mg_tail_start(ctx->lay, ctx->prm.precision == PF_FP32 ? 4 : 8) + 1
-                         : 0;
+  const int64_t vc = ctx->prm.solver == PF_PCG_MG ? vcycle_kernels(ctx) : 0;
   const bool heun = ctx->prm.integrator == PF_HEUN;
   const int64_t per_solve = (ctx->singular ? 2 : 0) + 2 + vc + (plain_extrap(ctx) ? 1 : 0);
   *per_iter = 2 + vc;
@@ -1481,7 +1499,7 @@ pf_status pf_get_tiling(const pf_ctx* ctx, pf_tiling* out) {
   out->vx = ctx->L.march.vx;
   out->tz = ctx->L.march.tz;
   out->blocks_per_sm = ctx->tile_bps;
-  out->reserved = 0;
+  out->mg_whole = ctx->mg_whole;
   return PF_OK;
 }
 
@@ -1495,7 +1513,7 @@ pf_status pf_set_tiling(pf_ctx* ctx, const pf_tiling* t) {
   if (t->vx > 1 && ctx->prm.nx % t->vx != 0) return ctx->fail(PF_ERR_ARG, "nx is not a multiple of vx = %d", t->vx);
   if (t->tz < 1 || t->tz > 64) return ctx->fail(PF_ERR_ARG, "tz must be in 1 .. 64");
   if (t->blocks_per_sm < 0 || t->blocks_per_sm > 64) return ctx->fail(PF_ERR_ARG, "blocks_per_sm must be in 0 .. 64");
-  if (t->reserved != 0) return ctx->fail(PF_ERR_ARG, "reserved must be zero");
+  if (t->mg_whole != 0 && t->mg_whole != 1) return ctx->fail(PF_ERR_ARG, "mg_whole must be 0 or 1");
   const Geo& g = ctx->geo;
   const int occ = pf::march_blocks_per_sm(fp32, ctx->prm.has_eps);
   const int bps = t->blocks_per_sm > 0 ? std::min(t->blocks_per_sm, occ) : occ;
@@ -1509,6 +1527,7 @@ pf_status pf_set_tiling(pf_ctx* ctx, const pf_tiling* t) {
   drop_graphs(ctx);
   ctx->L.march = m;
   ctx->tile_bps = t->blocks_per_sm;
+  ctx->mg_whole = t->mg_whole;
   ctx->gen += 1;
   return PF_OK;
 }

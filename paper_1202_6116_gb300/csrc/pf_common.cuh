@@ -20,11 +20,16 @@ constexpr int FLAT_THREADS = 256;
 
 // Tiling of a plane-march launch: tiles of (MTX * vx) x MTY columns times tz
 // planes; vx = cells per thread (16 bytes, or 1 when nx is not a multiple).
+// Tile z-index iz covers planes [zlo + iz (tz + zskip), that + tz), clipped
+// at nz - zcut; all three are 0 for a launch over the whole z range (a launch
+// over the interior planes sets zlo = zcut = b; one over the two face slabs
+// of b planes sets tz = b, zskip = nz - 2 b).
 struct MarchCfg {
   int tiles_x, tiles_y, tz;
   long long ntiles;
   int grid;
   int vx;
+  int zlo, zcut, zskip;
 };
 
 struct Geo {

@@ -18,6 +18,21 @@ constexpr int MG_MAX_COARSE = 1024;   // cells of the coarsest multigrid level (
 constexpr int MG_TAIL_CELLS = 4096;   // levels at most this large run in the one-block V-cycle tail
 constexpr int MG_TAIL_LEVELS = 16;
 constexpr int MG_TAIL_SMEM = 192 * 1024;   // shared-memory limit of the tail's level arrays (bytes)
+// A multigrid sweep over a large level whose z faces are not periodic runs as
+// two launches: the interior planes [b, nz - b), compiled without the face
+// code (fewer registers, more resident blocks), and the two face slabs of b
+// planes (the pre-smoother's face code also covers the planes next to a face,
+// hence b = 2).  Split: the pre-smoother, the prolongation sweep and the second
+// post-sweep below the finest level (the finest one also reduces r.z).  The
+// second launch costs about 10 us, which a level pays back from about 2^25
+// cells (measured: a 2^27-cell level gains, a 2^24-cell one loses), or from
+// 2^23 with a permittivity field, whose face code costs more registers.
+constexpr int MG_SPLIT_B = 2;
+constexpr long long MG_SPLIT_CELLS = 1LL << 25;
+constexpr long long MG_SPLIT_CELLS_EPS = 1LL << 23;
+inline bool mg_split_level(long long n, int nz, int periodic_z, int eps) {
+  return !periodic_z && nz >= 2 * MG_SPLIT_B + 2 && n >= (eps ? MG_SPLIT_CELLS_EPS : MG_SPLIT_CELLS);
+}
 
 struct LaunchCfg {
   int grid;            // simple per-cell kernels (TX x TY blocks over tiles)
@@ -72,6 +87,7 @@ struct MgView {
   const T* eps;       // cell permittivity of this level (nullptr: eps = 1)
   const T* invd;      // 1/diag of this level's operator (with eps only)
   MarchCfg mc;
+  int split;          // 1: its split sweeps run as interior + face-slab launches (mg_split_level)
 };
 
 // The small levels of the V-cycle (lv[0] .. lv[nl - 1], the last one the
@@ -244,17 +260,17 @@ void set_global_error(const char* what, const char* detail = nullptr);
 
 // Multigrid V-cycle pieces (pf_mg.cu).
 template <typename T>
-void launch_mg_pre(const LaunchCfg& L, const MgView<T>& lv, Scalars* S);
+int launch_mg_pre(const LaunchCfg& L, const MgView<T>& lv, Scalars* S);
 template <typename T>
-void launch_mg_rr(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S);
+int launch_mg_rr(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S);
 template <typename T>
 void launch_mg_coarse(const LaunchCfg& L, const MgView<T>& cv, int singular, Scalars* S);
 template <typename T>
 void launch_mg_tail(const LaunchCfg& L, const MgTail<T>& t, int singular, Scalars* S);
 template <typename T>
-void launch_mg_post1(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S);
+int launch_mg_post1(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S);
 template <typename T>
-void launch_mg_post2(const LaunchCfg& L, const MgView<T>& lv, int last, double* part, Scalars* S);
+int launch_mg_post2(const LaunchCfg& L, const MgView<T>& lv, int last, double* part, Scalars* S);
 template <typename T>
 int mg_blocks_per_sm();
 // Permittivity of a coarse level (the mean of the fine children, into ceps)

@@ -52,8 +52,8 @@ __device__ __forceinline__ TileGeo<TXT, TYT, VX> tile_geo(const Geo& g, long lon
   const int iy = r % mc.tiles_y;
   const int iz = r / mc.tiles_y;
   const int x0 = ix * BX, y0 = iy * TYT;
-  s.z0 = iz * mc.tz;
-  s.z1 = min(s.z0 + mc.tz, g.nz);
+  s.z0 = mc.zlo + iz * (mc.tz + mc.zskip);
+  s.z1 = min(s.z0 + mc.tz, g.nz - mc.zcut);
   s.w = min(BX, g.nx - x0);
   s.h = min(TYT, g.ny - y0);
   s.tx = threadIdx.x;
@@ -350,7 +350,7 @@ struct Raw {
 // smem: Pipe<...>::bytes() bytes, 16-byte aligned.  Every thread of the block
 // must call this (it synchronises).
 template <typename T, typename F, typename Out, int TXT, int TYT, int VX, int NH, int NO, int D, int NP = 0,
-          class Val, class Emit, class Post>
+          bool INTR = false, class Val, class Emit, class Post>
 __device__ __forceinline__ void march(const Geo& g, const TileGeo<TXT, TYT, VX>& s, unsigned char* smem,
                                       const T* const (&hsrc)[NH], const T* const (&osrc)[NO > 0 ? NO : 1],
                                       Val val, Emit emit, Post post, ParentSrc<T> par = ParentSrc<T>{}) {
@@ -488,7 +488,7 @@ __device__ __forceinline__ void march(const Geo& g, const TileGeo<TXT, TYT, VX>&
         }
         post(z, outv);
       };
-      if (zb < 0 || za < 0) emit_all(true);
+      if (!INTR && (zb < 0 || za < 0)) emit_all(true);
       else emit_all(false);
     }
 #pragma unroll
@@ -510,9 +510,11 @@ __device__ __forceinline__ void march(const Geo& g, const TileGeo<TXT, TYT, VX>&
 // post and bt as in march.  With NP = 1 the staged coarse-grid parents come as
 // field NH of the stencil (the parent of each of the seven cells); a vector's
 // parents are stored compactly (VX / fx values), read with one access and
-// expanded in registers.
-template <typename T, typename Out, int TXT, int TYT, int VX, int NH, int NO, int D, int NP = 0, class Emit,
-          class Post>
+// expanded in registers.  INTR (both walks): the launch covers interior planes
+// only (every plane has both z neighbours), so only the bt = false form of the
+// functors is compiled -- the boundary code then costs no registers.
+template <typename T, typename Out, int TXT, int TYT, int VX, int NH, int NO, int D, int NP = 0, bool INTR = false,
+          class Emit, class Post>
 __device__ __forceinline__ void march_direct(const Geo& g, const TileGeo<TXT, TYT, VX>& s, unsigned char* smem,
                                              const T* const (&hsrc)[NH], const T* const (&osrc)[NO > 0 ? NO : 1],
                                              Emit emit, Post post, ParentSrc<T> par = ParentSrc<T>{}) {
@@ -618,7 +620,7 @@ __device__ __forceinline__ void march_direct(const Geo& g, const TileGeo<TXT, TY
         }
         post(z, outv);
       };
-      if (zb < 0 || za < 0) emit_all(true);
+      if (!INTR && (zb < 0 || za < 0)) emit_all(true);
       else emit_all(false);
     }
 #pragma unroll

@@ -140,8 +140,8 @@ using MgPipeD = Pipe<T, void, MTX, MTY, VX, E ? 2 : 1, E ? 2 : 1, MG_D>;
 // A e1).  Away from the z faces the diagonal is one constant, so A e1 =
 // w1 diag^-1 A f there; on the planes next to a z face and their neighbour
 // planes e1 is formed per neighbour with its own diagonal.
-template <typename T, int VX, bool EPS>
-__global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? 4 : 2) k_mg_pre(MgView<T> L, Scalars* S) {
+template <typename T, int VX, bool EPS, bool INT = false>
+__global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? (INT ? 5 : 4) : 2) k_mg_pre(MgView<T> L, Scalars* S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   if (S->done) return;
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? 4 : 2) k_
       const T Ae1 = apply_aniso_eps(e1, dlo, dhi, L.ax, L.ay, L.az, bt);
       return e1.c.v + om2 * sr.c.v[2] * (f.c - Ae1);
     } else {
-      const bool near = zfaces && (z == 1 || z == nz - 2);
+      const bool near = !INT && zfaces && (z == 1 || z == nz - 2);
       if (!bt && !near) {
         const T Ae1 = w1 * apply_aniso(f, 0, 0, L.ax, L.ay, L.az, false);
         return w1 * f.c + om2 * inv_int * (f.c - Ae1);
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? 4 : 2) k_
   const TileSched ts{&S->sched_next, &S->sched_done, L.mc.ntiles};
   for (long long t = sched_first(ts, &tile_slot); t < L.mc.ntiles; t = sched_next(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
-    march_direct<T, T, MTX, MTY, VX, NH, 0, MG_D>(L.g, s, smem, hsrc, osrc, emit, post);
+    march_direct<T, T, MTX, MTY, VX, NH, 0, MG_D, 0, INT>(L.g, s, smem, hsrc, osrc, emit, post);
   }
   sched_finish(ts);
 }
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Sc
 // Prolongation + correction fused into the first post-smoothing sweep: the
 // stencil field is e + e_c(parent), the parents staged with the fine planes
 // and combined with e at each of the seven cells.
-template <typename T, int VX, bool EPS>
+template <typename T, int VX, bool EPS, bool INT = false>
 __global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? 3 : 2) k_mg_post1(MgView<T> L, MgView<T> C, Scalars* S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
@@ -338,15 +338,15 @@ __global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? 3 : 2) k_
   const TileSched ts{&S->sched_next, &S->sched_done, L.mc.ntiles};
   for (long long t = sched_first(ts, &tile_slot); t < L.mc.ntiles; t = sched_next(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
-    march_direct<T, T, MTX, MTY, VX, NH, NO, MG_D, 1>(L.g, s, smem, hsrc, osrc, emit, post, par);
+    march_direct<T, T, MTX, MTY, VX, NH, NO, MG_D, 1, INT>(L.g, s, smem, hsrc, osrc, emit, post, par);
   }
   sched_finish(ts);
 }
 
 // Last post-smoothing sweep.  On the finest level (LAST) it also forms
 // r.z (f = r, e = z): the last block sets beta = (r.z)_new / (r.z)_old.
-template <typename T, bool LAST, int VX, bool EPS>
-__global__ void __launch_bounds__(MTX* MTY) k_mg_post2(MgView<T> L, double* part, Scalars* S) {
+template <typename T, bool LAST, int VX, bool EPS, bool INT = false>
+__global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? (INT ? 5 : (LAST ? 3 : 4)) : 2) k_mg_post2(MgView<T> L, double* part, Scalars* S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   if (S->done) return;
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_post2(MgView<T> L, double* part
   for (long long t = sched_first(ts, &tile_slot); t < L.mc.ntiles; t = sched_next(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
     arz = Acc<T>();
-    march_direct<T, T, MTX, MTY, VX, NH, NO, MG_D>(L.g, s, smem, hsrc, osrc, emit, post);
+    march_direct<T, T, MTX, MTY, VX, NH, NO, MG_D, 0, INT>(L.g, s, smem, hsrc, osrc, emit, post);
     if (LAST) {
       double v[1] = {arz.value()};
       tile_partials<1, MTX * MTY>(v, part, t);
@@ -755,66 +755,124 @@ static int mg_grid(K kernel, size_t bytes, long long ntiles, int& res) {
   return (int)std::min<long long>(ntiles, std::min(res, MAX_GRID));
 }
 
-template <typename T, int VX, bool E>
-static void pre_v(const LaunchCfg& L, const MgView<T>& lv, Scalars* S) {
+// A level split by mg_split_level: the view of its interior planes (tiles of
+// the level's depth over [b, nz - b)) and of its two face slabs of b planes.
+template <typename T>
+static bool split_views(const MgView<T>& lv, MgView<T>& vi, MgView<T>& vb) {
+  if (!lv.split) return false;
+  constexpr int b = MG_SPLIT_B;
+  const long long cols = (long long)lv.mc.tiles_x * lv.mc.tiles_y;
+  vi = lv;
+  vi.mc.zlo = b;
+  vi.mc.zcut = b;
+  vi.mc.zskip = 0;
+  vi.mc.ntiles = cols * ((lv.g.nz - 2 * b + lv.mc.tz - 1) / lv.mc.tz);
+  vb = lv;
+  vb.mc.tz = b;
+  vb.mc.zlo = 0;
+  vb.mc.zcut = 0;
+  vb.mc.zskip = lv.g.nz - 2 * b;
+  vb.mc.ntiles = cols * 2;
+  return true;
+}
+
+template <typename T, int VX, bool E, bool I>
+static void pre_l(const LaunchCfg& L, const MgView<T>& lv, Scalars* S) {
   static bool f = false;
   static int res = 0;
   const size_t bytes = MgPipeD0<T, VX, E>::bytes();
-  smem_once(k_mg_pre<T, VX, E>, bytes, f);
-  const int grid = mg_grid(k_mg_pre<T, VX, E>, bytes, lv.mc.ntiles, res);
-  k_mg_pre<T, VX, E><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, S);
+  smem_once(k_mg_pre<T, VX, E, I>, bytes, f);
+  const int grid = mg_grid(k_mg_pre<T, VX, E, I>, bytes, lv.mc.ntiles, res);
+  k_mg_pre<T, VX, E, I><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, S);
 }
 template <typename T, int VX, bool E>
-static void rr_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
+static int pre_v(const LaunchCfg& L, const MgView<T>& lv, Scalars* S) {
+  MgView<T> vi, vb;
+  if (!split_views(lv, vi, vb)) {
+    pre_l<T, VX, E, false>(L, lv, S);
+    return 1;
+  }
+  pre_l<T, VX, E, true>(L, vi, S);
+  pre_l<T, VX, E, false>(L, vb, S);
+  return 2;
+}
+// (the residual's face code costs it no registers: never split)
+template <typename T, int VX, bool E>
+static int rr_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
   static bool f = false;
   static int res = 0;
   const size_t bytes = MgPipeR<T, VX, E>::bytes();
   smem_once(k_mg_rr<T, VX, E>, bytes, f);
   const int grid = mg_grid(k_mg_rr<T, VX, E>, bytes, lv.mc.ntiles, res);
   k_mg_rr<T, VX, E><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, cv, S);
+  return 1;
 }
-template <typename T, int VX, bool E>
-static void post1_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
+template <typename T, int VX, bool E, bool I>
+static void post1_l(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
   static bool f = false;
   static int res = 0;
   const size_t bytes = MgPipeP<T, VX, E>::bytes();
-  smem_once(k_mg_post1<T, VX, E>, bytes, f);
-  const int grid = mg_grid(k_mg_post1<T, VX, E>, bytes, lv.mc.ntiles, res);
-  k_mg_post1<T, VX, E><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, cv, S);
+  smem_once(k_mg_post1<T, VX, E, I>, bytes, f);
+  const int grid = mg_grid(k_mg_post1<T, VX, E, I>, bytes, lv.mc.ntiles, res);
+  k_mg_post1<T, VX, E, I><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, cv, S);
 }
-template <typename T, bool LAST, int VX, bool E>
-static void post2_v(const LaunchCfg& L, const MgView<T>& lv, double* part, Scalars* S) {
+template <typename T, int VX, bool E>
+static int post1_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
+  MgView<T> vi, vb;
+  if (!split_views(lv, vi, vb)) {
+    post1_l<T, VX, E, false>(L, lv, cv, S);
+    return 1;
+  }
+  post1_l<T, VX, E, true>(L, vi, cv, S);
+  post1_l<T, VX, E, false>(L, vb, cv, S);
+  return 2;
+}
+template <typename T, bool LAST, int VX, bool E, bool I>
+static void post2_l(const LaunchCfg& L, const MgView<T>& lv, double* part, Scalars* S) {
   static bool f = false;
   static int res = 0;
   const size_t bytes = MgPipeD<T, VX, E>::bytes();
-  smem_once(k_mg_post2<T, LAST, VX, E>, bytes, f);
-  const int grid = mg_grid(k_mg_post2<T, LAST, VX, E>, bytes, lv.mc.ntiles, res);
-  k_mg_post2<T, LAST, VX, E><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, part, S);
+  smem_once(k_mg_post2<T, LAST, VX, E, I>, bytes, f);
+  const int grid = mg_grid(k_mg_post2<T, LAST, VX, E, I>, bytes, lv.mc.ntiles, res);
+  k_mg_post2<T, LAST, VX, E, I><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, part, S);
+}
+// The finest level's second post-sweep also reduces r.z over all its tiles,
+// so it is never split.
+template <typename T, bool LAST, int VX, bool E>
+static int post2_v(const LaunchCfg& L, const MgView<T>& lv, double* part, Scalars* S) {
+  MgView<T> vi, vb;
+  if (LAST || !split_views(lv, vi, vb)) {
+    post2_l<T, LAST, VX, E, false>(L, lv, part, S);
+    return 1;
+  }
+  post2_l<T, LAST, VX, E, true>(L, vi, part, S);
+  post2_l<T, LAST, VX, E, false>(L, vb, part, S);
+  return 2;
 }
 
 constexpr int vec_of(size_t bytes) { return (int)(16 / bytes); }
 
 template <typename T>
-void launch_mg_pre(const LaunchCfg& L, const MgView<T>& lv, Scalars* S) {
+int launch_mg_pre(const LaunchCfg& L, const MgView<T>& lv, Scalars* S) {
   constexpr int V = vec_of(sizeof(T));
   if (lv.eps) {
-    if (lv.mc.vx > 1) pre_v<T, V, true>(L, lv, S);
-    else pre_v<T, 1, true>(L, lv, S);
+    return lv.mc.vx > 1 ? pre_v<T, V, true>(L, lv, S)
+                        : pre_v<T, 1, true>(L, lv, S);
   } else {
-    if (lv.mc.vx > 1) pre_v<T, V, false>(L, lv, S);
-    else pre_v<T, 1, false>(L, lv, S);
+    return lv.mc.vx > 1 ? pre_v<T, V, false>(L, lv, S)
+                        : pre_v<T, 1, false>(L, lv, S);
   }
 }
 
 template <typename T>
-void launch_mg_rr(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
+int launch_mg_rr(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
   constexpr int V = vec_of(sizeof(T));
   if (lv.eps) {
-    if (lv.mc.vx > 1) rr_v<T, V, true>(L, lv, cv, S);
-    else rr_v<T, 1, true>(L, lv, cv, S);
+    return lv.mc.vx > 1 ? rr_v<T, V, true>(L, lv, cv, S)
+                        : rr_v<T, 1, true>(L, lv, cv, S);
   } else {
-    if (lv.mc.vx > 1) rr_v<T, V, false>(L, lv, cv, S);
-    else rr_v<T, 1, false>(L, lv, cv, S);
+    return lv.mc.vx > 1 ? rr_v<T, V, false>(L, lv, cv, S)
+                        : rr_v<T, 1, false>(L, lv, cv, S);
   }
 }
 
@@ -825,33 +883,32 @@ void launch_mg_coarse(const LaunchCfg& L, const MgView<T>& cv, int singular, Sca
 }
 
 template <typename T>
-void launch_mg_post1(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
+int launch_mg_post1(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
   constexpr int V = vec_of(sizeof(T));
   if (lv.eps) {
-    if (lv.mc.vx > 1) post1_v<T, V, true>(L, lv, cv, S);
-    else post1_v<T, 1, true>(L, lv, cv, S);
+    return lv.mc.vx > 1 ? post1_v<T, V, true>(L, lv, cv, S)
+                        : post1_v<T, 1, true>(L, lv, cv, S);
   } else {
-    if (lv.mc.vx > 1) post1_v<T, V, false>(L, lv, cv, S);
-    else post1_v<T, 1, false>(L, lv, cv, S);
+    return lv.mc.vx > 1 ? post1_v<T, V, false>(L, lv, cv, S)
+                        : post1_v<T, 1, false>(L, lv, cv, S);
   }
 }
 
 template <typename T, bool E>
-static void post2_e(const LaunchCfg& L, const MgView<T>& lv, int last, double* part, Scalars* S) {
+static int post2_e(const LaunchCfg& L, const MgView<T>& lv, int last, double* part, Scalars* S) {
   constexpr int V = vec_of(sizeof(T));
   if (last) {
-    if (lv.mc.vx > 1) post2_v<T, true, V, E>(L, lv, part, S);
-    else post2_v<T, true, 1, E>(L, lv, part, S);
+    return lv.mc.vx > 1 ? post2_v<T, true, V, E>(L, lv, part, S)
+                        : post2_v<T, true, 1, E>(L, lv, part, S);
   } else {
-    if (lv.mc.vx > 1) post2_v<T, false, V, E>(L, lv, part, S);
-    else post2_v<T, false, 1, E>(L, lv, part, S);
+    return lv.mc.vx > 1 ? post2_v<T, false, V, E>(L, lv, part, S)
+                        : post2_v<T, false, 1, E>(L, lv, part, S);
   }
 }
 
 template <typename T>
-void launch_mg_post2(const LaunchCfg& L, const MgView<T>& lv, int last, double* part, Scalars* S) {
-  if (lv.eps) post2_e<T, true>(L, lv, last, part, S);
-  else post2_e<T, false>(L, lv, last, part, S);
+int launch_mg_post2(const LaunchCfg& L, const MgView<T>& lv, int last, double* part, Scalars* S) {
+  return lv.eps ? post2_e<T, true>(L, lv, last, part, S) : post2_e<T, false>(L, lv, last, part, S);
 }
 
 // ------------------------------------------------ permittivity of the levels
@@ -928,12 +985,12 @@ int mg_blocks_per_sm() {
 }
 
 #define PF_MG_INSTANTIATE(T)                                                           \
-  template void launch_mg_pre<T>(const LaunchCfg&, const MgView<T>&, Scalars*);                  \
-  template void launch_mg_rr<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*); \
+  template int launch_mg_pre<T>(const LaunchCfg&, const MgView<T>&, Scalars*);                   \
+  template int launch_mg_rr<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*);  \
   template void launch_mg_coarse<T>(const LaunchCfg&, const MgView<T>&, int, Scalars*);          \
   template void launch_mg_tail<T>(const LaunchCfg&, const MgTail<T>&, int, Scalars*);            \
-  template void launch_mg_post1<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*); \
-  template void launch_mg_post2<T>(const LaunchCfg&, const MgView<T>&, int, double*, Scalars*);        \
+  template int launch_mg_post1<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*); \
+  template int launch_mg_post2<T>(const LaunchCfg&, const MgView<T>&, int, double*, Scalars*);         \
   template void launch_mg_eps_level<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, T*, T*);  \
   template int mg_blocks_per_sm<T>();
 

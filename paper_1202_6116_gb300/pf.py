@@ -63,7 +63,7 @@ class pf_kernel_stat(C.Structure):
 
 
 class pf_tiling(C.Structure):
-    _fields_ = [("vx", C.c_int32), ("tz", C.c_int32), ("blocks_per_sm", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("vx", C.c_int32), ("tz", C.c_int32), ("blocks_per_sm", C.c_int32), ("mg_whole", C.c_int32)]
 
 
 class PfError(RuntimeError):
@@ -291,8 +291,8 @@ def pf_get_tiling(ctx) -> pf_tiling:
     return t
 
 
-def pf_set_tiling(ctx, vx, tz, blocks_per_sm=0):
-    t = pf_tiling(int(vx), int(tz), int(blocks_per_sm), 0)
+def pf_set_tiling(ctx, vx, tz, blocks_per_sm=0, mg_whole=0):
+    t = pf_tiling(int(vx), int(tz), int(blocks_per_sm), int(mg_whole))
     return check(lib().pf_set_tiling(ctx, C.byref(t)), ctx)
 
 
