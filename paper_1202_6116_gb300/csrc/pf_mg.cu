@@ -449,9 +449,52 @@ __device__ __forceinline__ double warps_sum(double v, int nw, double* red) {
 // permittivity field makes the coarse operator's diagonal vary by orders of
 // magnitude.  With no electrode the level is singular: the right-hand side and
 // the solution are projected to zero mean.
+// A coarsest level that is one z column (1 x 1 x nz: the in-plane faces join a
+// cell to itself and drop out) with non-periodic z is tridiagonal: solved
+// directly by the Thomas algorithm (forward elimination, back substitution)
+// in FP64 by one thread, with scratch for 2 nz values.  Jacobi-PCG on such a
+// column (a film whose z axis stops coarsening, as under air layers) needed up
+// to nz iterations of three block reductions each.
+template <typename T>
+__device__ __forceinline__ void coarse_column_solve(const MgView<T>& C, const T* cf, T* ce, double* scratch) {
+  const int n = C.g.nz;
+  const double az = C.az;
+  double* cpr = scratch;                        // c'_z
+  double* dpr = scratch + n;                    // d'_z
+  auto w = [&](int z, int nb) -> double {       // face weight between cells z and nb
+    if (!C.eps) return 1.0;
+    const double ec = (double)C.eps[z], en = (double)C.eps[nb];
+    return 2.0 * ec * en / (ec + en);
+  };
+  double prev_c = 0.0, prev_d = 0.0;
+  for (int z = 0; z < n; ++z) {
+    const double wm = z > 0 ? w(z, z - 1) : 0.0, wp = z < n - 1 ? w(z, z + 1) : 0.0;
+    const double wd = C.eps ? (double)C.eps[z] : 1.0;
+    double diag = az * (wm + wp);
+    if (z == 0 && C.tlo[0]) diag += az * 2.0 * wd;
+    if (z == n - 1 && C.thi[0]) diag += az * 2.0 * wd;
+    const double lower = -az * wm, upper = -az * wp;
+    const double m = diag - lower * prev_c;
+    prev_c = upper / m;
+    prev_d = ((double)cf[z] - lower * prev_d) / m;
+    cpr[z] = prev_c;
+    dpr[z] = prev_d;
+  }
+  double x = 0.0;
+  for (int z = n - 1; z >= 0; --z) {
+    x = dpr[z] - cpr[z] * x;
+    ce[z] = (T)x;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void mg_coarse_solve(const MgView<T>& C, const T* cf, T* ce, int singular, double* ps,
                                                 double* red) {
+  if (C.g.nx == 1 && C.g.ny == 1 && !C.g.periodic_z && !singular && 2 * C.g.nz <= MG_MAX_COARSE &&
+      (C.tlo[0] || C.thi[0])) {
+    if (threadIdx.x == 0) coarse_column_solve(C, cf, ce, ps);
+    return;
+  }
   const int n = (int)C.g.n, tid = threadIdx.x;
   const int nw = (n + 31) >> 5;
   if (tid >= nw * 32) return;
@@ -552,14 +595,32 @@ struct TailCol {
   int dlo, dhi;             // electrode masks of the column's z faces
 };
 
+// Quotient of small non-negative ints (a < 2^22) by d >= 1 through a float
+// reciprocal formed once per level: the rounded product is at most one off,
+// and one compare on each side corrects it.  The column walks divide by the
+// level's sizes at every item of every phase; an integer division there cost
+// more than the arithmetic of the cell it located.
+struct SmallDiv {
+  int d;
+  float r;
+  __device__ __forceinline__ explicit SmallDiv(int d_) : d(d_), r(1.0f / (float)d_) {}
+  __device__ __forceinline__ int operator()(int a) const {
+    int q = (int)((float)a * r);
+    if (q * d > a) --q;
+    else if ((q + 1) * d <= a) ++q;
+    return q;
+  }
+};
+
 template <typename T, class Body>
 __device__ __forceinline__ void tail_cols(const MgView<T>& L, Body body) {
   const int nx = L.g.nx, ny = L.g.ny, nxy = (int)L.g.nxy, nz = L.g.nz;
   const int nch = nxy >= (int)blockDim.x ? 1 : min(nz, (int)blockDim.x / nxy);   // z chunks per column
+  const SmallDiv by_nxy(nxy), by_nch(nch), by_nx(nx);
   for (int item = threadIdx.x; item < nxy * nch; item += blockDim.x) {
-    const int col = item % nxy, ch = item / nxy;
-    const int z0 = (int)((long long)ch * nz / nch), z1 = (int)((long long)(ch + 1) * nz / nch);
-    const int y = col / nx, x = col - y * nx;
+    const int ch = nch > 1 ? by_nxy(item) : 0, col = item - ch * nxy;
+    const int z0 = nch > 1 ? by_nch(ch * nz) : 0, z1 = nch > 1 ? by_nch((ch + 1) * nz) : nz;
+    const int y = by_nx(col), x = col - y * nx;
     TailCol o;
     o.xy = col;
     o.dxm = x == 0 ? nx - 1 : -1;
