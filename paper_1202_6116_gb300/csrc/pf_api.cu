@@ -495,11 +495,19 @@ void vcycle(pf_ctx* ctx, int j) {
     const pf::MgView<T> lv = mg_view<T>(ctx, k), cv = mg_view<T>(ctx, k + 1);
     const double N = (double)lv.g.n;
     before_launch(ctx);
-    int nk = pf::launch_mg_pre<T>(ctx->L, lv, S);
+    const double rest = 1.0 / (lv.fx * lv.fy * lv.fz);
+    int nk = pf::launch_mg_prr<T>(ctx->L, lv, cv, S);
+    if (nk > 0) {     // fused interior: f read once, e and the coarse rhs written; face slabs as before
+      const double Nf = 2.0 * pf::MG_SPLIT_B * (double)lv.g.nxy;
+      after_launch(ctx, mg_fam(F_MG_PRE, k), ((2 + rest) * (N - Nf) + (4 + rest) * Nf) * w, 2, j);
+      ctx->launches += nk - 1;
+      continue;
+    }
+    nk = pf::launch_mg_pre<T>(ctx->L, lv, S);
     after_launch(ctx, mg_fam(F_MG_PRE, k), (2 + 2 * e) * N * w, 2, j);
     ctx->launches += nk - 1;
     nk = pf::launch_mg_rr<T>(ctx->L, lv, cv, S);
-    after_launch(ctx, mg_fam(F_MG_RR, k), (2 + e + 1.0 / (lv.fx * lv.fy * lv.fz)) * N * w, 2, j);
+    after_launch(ctx, mg_fam(F_MG_RR, k), (2 + e + rest) * N * w, 2, j);
     ctx->launches += nk - 1;
   }
   if (k0 + 1 < nl) {

@@ -263,6 +263,11 @@ template <typename T>
 int launch_mg_pre(const LaunchCfg& L, const MgView<T>& lv, Scalars* S);
 template <typename T>
 int launch_mg_rr(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S);
+// Pre-smoother and residual of a split FP32 level as one fused pass over its
+// interior planes (plus the face slabs' own kernels); returns the launches, 0
+// when the level does not qualify (then nothing was launched).
+template <typename T>
+int launch_mg_prr(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S);
 template <typename T>
 void launch_mg_coarse(const LaunchCfg& L, const MgView<T>& cv, int singular, Scalars* S);
 template <typename T>

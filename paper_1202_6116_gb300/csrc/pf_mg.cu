@@ -81,6 +81,33 @@ __device__ __forceinline__ T apply_aniso(const Stencil7<T>& s, int dlo, int dhi,
   return ax * sx + ay * sy + az * sz;
 }
 
+// The interior 7-point operator (eps = 1) and the two pre-sweeps from zero,
+// every operation rounded as written (no contraction into FMAs): the kernels
+// that form them on the same cell -- the pre-smoother, the residual and their
+// fused form on a split level -- then agree bit for bit.
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+
+template <typename T>
+__device__ __forceinline__ T apply_int(T c, T xm, T xp, T ym, T yp, T zm, T zp, T ax, T ay, T az) {
+  const T sx = rn_add(rn_sub(c, xm), rn_sub(c, xp));
+  const T sy = rn_add(rn_sub(c, ym), rn_sub(c, yp));
+  const T sz = rn_add(rn_sub(c, zm), rn_sub(c, zp));
+  return rn_add(rn_add(rn_mul(ax, sx), rn_mul(ay, sy)), rn_mul(az, sz));
+}
+
+// e = e1 + w2 D^-1 (f - A e1), e1 = w1 D^-1 f, with D constant (w1 = omega1 / d,
+// w2d = omega2 / d): A e1 = w1 A f.
+template <typename T>
+__device__ __forceinline__ T pre_int(T c, T xm, T xp, T ym, T yp, T zm, T zp, T ax, T ay, T az, T w1, T w2d) {
+  const T Ae1 = rn_mul(w1, apply_int(c, xm, xp, ym, yp, zm, zp, ax, ay, az));
+  return rn_add(rn_mul(w1, c), rn_mul(w2d, rn_sub(c, Ae1)));
+}
+
 template <typename T>
 __device__ __forceinline__ T mg_inv_bt(const MgView<T>& L, int xy, int z, T inv_int, const bool bt) {
   return bt ? mg_inv(L, xy, z, inv_int) : inv_int;
@@ -147,7 +174,7 @@ __global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? (INT ? 5 
   if (S->done) return;
   constexpr int NH = EPS ? 3 : 1;          // f (, eps, 1/diag)
   const T om1 = mg_omega1<T>(), om2 = mg_omega2<T>(), inv_int = mg_inv_int(L);
-  const T w1 = om1 * inv_int;
+  const T w1 = rn_mul(om1, inv_int), w2d = rn_mul(om2, inv_int);
   const T* hsrc[NH];
   hsrc[0] = L.f;
   if constexpr (EPS) {
@@ -176,10 +203,7 @@ __global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? (INT ? 5 
       return e1.c.v + om2 * sr.c.v[2] * (f.c - Ae1);
     } else {
       const bool near = !INT && zfaces && (z == 1 || z == nz - 2);
-      if (!bt && !near) {
-        const T Ae1 = w1 * apply_aniso(f, 0, 0, L.ax, L.ay, L.az, false);
-        return w1 * f.c + om2 * inv_int * (f.c - Ae1);
-      }
+      if (!bt && !near) return pre_int(f.c, f.xm, f.xp, f.ym, f.yp, f.zm, f.zp, L.ax, L.ay, L.az, w1, w2d);
       Stencil7<T> e1;
       const T ic = mg_inv(L, xy, z, inv_int);
       e1.c = om1 * ic * f.c;
@@ -241,8 +265,15 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Sc
     const bool B = bt;
     const int dlo = (B && sr.zb < 0) ? (int)L.tlo[xy] : 0;
     const int dhi = (B && sr.za < 0) ? (int)L.thi[xy] : 0;
-    if constexpr (EPS) return o[0] - apply_aniso_eps(pick_eps(sr, 0, 1), dlo, dhi, L.ax, L.ay, L.az, bt);
-    else return o[0] - apply_aniso(pick(sr, 0), dlo, dhi, L.ax, L.ay, L.az, bt);
+    if constexpr (EPS) {
+      return o[0] - apply_aniso_eps(pick_eps(sr, 0, 1), dlo, dhi, L.ax, L.ay, L.az, bt);
+    } else {
+      if (!bt) {
+        const Stencil7<T> e = pick(sr, 0);
+        return rn_sub(o[0], apply_int(e.c, e.xm, e.xp, e.ym, e.yp, e.zm, e.zp, L.ax, L.ay, L.az));
+      }
+      return o[0] - apply_aniso(pick(sr, 0), dlo, dhi, L.ax, L.ay, L.az, bt);
+    }
   };
   auto post = [&](int z, const T (&rv)[VX]) {
 #pragma unroll
@@ -281,6 +312,179 @@ __global__ void __launch_bounds__(MTX* MTY) k_mg_rr(MgView<T> L, MgView<T> C, Sc
   for (long long t = sched_first(ts, &tile_slot); t < L.mc.ntiles; t = sched_next(ts, &tile_slot)) {
     s = tile_geo<MTX, MTY, VX>(L.g, t, L.mc);
     march_direct<T, T, MTX, MTY, VX, NH, 1, MG_D>(L.g, s, smem, hsrc, osrc, emit, post);
+  }
+  sched_finish(ts);
+}
+
+// Pre-smoother, residual and restriction fused, on the interior planes of a
+// split FP32 level without eps whose tiles are whole (nx a multiple of 64, ny
+// of 16): one pass over f instead of f -> e, then e and f again.  The residual
+// at a cell needs e at its six neighbours, and e at a cell needs f at its own
+// six, so a tile stages f with a two-cell ring (periodic wrap resolved in the
+// source rows and columns) and forms e on its columns and on the one-cell ring
+// around them, one plane ahead of the residual.  e of the plane just below or
+// above the tile is formed too (own columns), except on the planes next to a z
+// face, which belong to the face slabs: there it is the face-slab
+// pre-smoother's output, read back (that launch runs first; the face-slab
+// residual runs after this one).  The arithmetic per cell is pre_int and
+// apply_int, as in k_mg_pre and k_mg_rr, so the results are bit-identical.
+// One barrier per plane: the e plane a tile writes at plane u (buffer u mod 2)
+// was last read for the residual of plane u - 2, and stage u + 4 mod 5 last
+// held plane u - 1; both reads end before the barrier of plane u.
+constexpr int PRR_D = 2;                   // planes of cp.async look-ahead
+constexpr int PRR_NS = PRR_D + 3;          // f planes w, w + 1, w + 2 in use, PRR_D in flight
+constexpr int PRR_RS = 72;                 // a staged row: x0 - 4 .. x0 + 67 (x0 at 4: 16-byte aligned)
+constexpr int PRR_RH = 20;                 // staged rows: y0 - 2 .. y0 + 17
+constexpr int PRR_EH = 18;                 // e plane rows: y0 - 1 .. y0 + 16 (columns as staged)
+constexpr int PRR_STAGE = PRR_RS * PRR_RH;
+constexpr int PRR_EPLANE = PRR_RS * PRR_EH;
+constexpr size_t prr_smem_bytes() { return (size_t)(PRR_NS * PRR_STAGE + 2 * PRR_EPLANE) * sizeof(float); }
+
+__global__ void __launch_bounds__(MTX* MTY, 4) k_mg_prr(MgView<float> L, MgView<float> C, Scalars* S) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long tile_slot;
+  static_assert(MTX == 16 && MTY == 16, "tiles of 64 x 16 columns, four cells a thread");
+  if (S->done) return;
+  float* const stg = reinterpret_cast<float*>(smem);
+  float* const eb = stg + PRR_NS * PRR_STAGE;
+  const int nx = L.g.nx, ny = L.g.ny, nz = L.g.nz;
+  const long long nxy = L.g.nxy;
+  const float om1 = mg_omega1<float>(), om2 = mg_omega2<float>(), inv_int = mg_inv_int(L);
+  const float w1 = rn_mul(om1, inv_int), w2d = rn_mul(om2, inv_int);
+  const float ax = L.ax, ay = L.ay, az = L.az;
+  const float scale = 1.0f / float(L.fx * L.fy * L.fz);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * MTX;
+  const int c0 = 4 + 4 * tx;               // column of the own vector in a stage or e plane
+  const int so = (ty + 2) * PRR_RS + c0;   // own vector in a stage
+  const int eo = (ty + 1) * PRR_RS + c0;   // own vector in an e plane
+  // ring cell of this thread (threads 0 .. 159): stage row, e-plane row, column
+  int rr = -1, re = -1, rc = -1;
+  if (tid < 64) { rr = 1; re = 0; rc = 4 + tid; }
+  else if (tid < 128) { rr = 18; re = 17; rc = 4 + tid - 64; }
+  else if (tid < 144) { rr = 2 + tid - 128; re = 1 + tid - 128; rc = 3; }
+  else if (tid < 160) { rr = 2 + tid - 144; re = 1 + tid - 144; rc = 68; }
+  auto load4 = [](const float* p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  };
+  const TileSched ts{&S->sched_next, &S->sched_done, L.mc.ntiles};
+  for (long long t = sched_first(ts, &tile_slot); t < L.mc.ntiles; t = sched_next(ts, &tile_slot)) {
+    const TileGeo<MTX, MTY, 4> s = tile_geo<MTX, MTY, 4>(L.g, t, L.mc);
+    const int x0 = s.x - 4 * tx, y0 = s.y - ty, z0 = s.z0, nt = s.z1 - s.z0;
+    // f plane w (z = z0 - 2 + w) into stage w mod PRR_NS: 20 rows of 16
+    // vectors, and the ring columns x0 - 2, x0 - 1, x0 + 64, x0 + 65
+    auto issue = [&](int w) {
+      if (w <= nt + 3) {
+        float* st = stg + (w % PRR_NS) * PRR_STAGE;
+        const float* src = L.f + (long long)(z0 - 2 + w) * nxy;
+        for (int i = tid; i < PRR_RH * 16; i += MTX * MTY) {
+          const int r = i >> 4, v = i & 15;
+          int y = y0 - 2 + r;
+          y += y < 0 ? ny : 0;
+          y -= y >= ny ? ny : 0;
+          cp_async<16>(st + r * PRR_RS + 4 + 4 * v, src + (long long)y * nx + x0 + 4 * v);
+        }
+        for (int i = tid; i < PRR_RH * 4; i += MTX * MTY) {
+          const int r = i >> 2, k = i & 3;
+          int y = y0 - 2 + r;
+          y += y < 0 ? ny : 0;
+          y -= y >= ny ? ny : 0;
+          int x = k < 2 ? x0 - 2 + k : x0 + 62 + k;
+          x += x < 0 ? nx : 0;
+          x -= x >= nx ? nx : 0;
+          cp_async<4>(st + r * PRR_RS + (k < 2 ? 2 + k : 66 + k), src + (long long)y * nx + x);
+        }
+      }
+      cp_commit();
+    };
+    // e at a staged cell from the f planes below, at and above it
+    auto e_at = [&](const float* sm, const float* sc, const float* sp, int off) -> float {
+      const float* q = sc + off;
+      return pre_int(q[0], q[-1], q[1], q[-PRR_RS], q[PRR_RS], sm[off], sp[off], ax, ay, az, w1, w2d);
+    };
+    float em2[4], em1[4], e0[4], racc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) em2[i] = em1[i] = e0[i] = racc[i] = 0.f;
+    for (int w = 0; w < PRR_D + 2; ++w) issue(w);
+    for (int u = 0; u <= nt + 1; ++u) {
+      cp_wait<PRR_D - 1>();                // f planes u .. u + 2 of this thread have landed
+      __syncthreads();                     // ... and of every thread
+      issue(u + PRR_D + 2);
+      const float* sm = stg + (u % PRR_NS) * PRR_STAGE;
+      const float* sc = stg + ((u + 1) % PRR_NS) * PRR_STAGE;
+      const float* sp = stg + ((u + 2) % PRR_NS) * PRR_STAGE;
+      float* ebu = eb + (u & 1) * PRR_EPLANE;
+      const int z = z0 - 1 + u;
+      // e of plane z on the own vector
+      if (z == 1 || z == nz - 2) {
+        load4(L.e + (long long)z * nxy + s.xy, e0);
+      } else {
+        float fc[4], fm[4], fp[4], fym[4], fyp[4];
+        load4(sc + so, fc);
+        load4(sm + so, fm);
+        load4(sp + so, fp);
+        load4(sc + so - PRR_RS, fym);
+        load4(sc + so + PRR_RS, fyp);
+        const float fl = sc[so - 1], fr = sc[so + 4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          e0[i] = pre_int(fc[i], i == 0 ? fl : fc[i - 1], i == 3 ? fr : fc[i + 1], fym[i], fyp[i], fm[i], fp[i], ax,
+                          ay, az, w1, w2d);
+      }
+      // planes whose residual this tile forms: e on the own vector and the ring
+      if (u >= 1 && u <= nt) {
+        *reinterpret_cast<float4*>(ebu + eo) = make_float4(e0[0], e0[1], e0[2], e0[3]);
+        if (rc >= 0) ebu[re * PRR_RS + rc] = e_at(sm, sc, sp, rr * PRR_RS + rc);
+      }
+      // residual of plane z - 1 (its e plane is complete since this plane's barrier)
+      if (u >= 2) {
+        const float* ebm = eb + ((u - 1) & 1) * PRR_EPLANE;
+        float ec[4], eym[4], eyp[4], fv[4], rv[4];
+        load4(ebm + eo, ec);
+        load4(ebm + eo - PRR_RS, eym);
+        load4(ebm + eo + PRR_RS, eyp);
+        load4(sm + so, fv);                // f of plane z - 1 is f plane u
+        const float el = ebm[eo - 1], er = ebm[eo + 4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          rv[i] = rn_sub(fv[i], apply_int(ec[i], i == 0 ? el : ec[i - 1], i == 3 ? er : ec[i + 1], eym[i], eyp[i],
+                                          em2[i], e0[i], ax, ay, az));
+        const int zr = z - 1;
+        *reinterpret_cast<float4*>(L.e + (long long)zr * nxy + s.xy) = make_float4(ec[0], ec[1], ec[2], ec[3]);
+        // restriction: 2 planes in registers, 2 rows by lane ^ 16, 2 columns in the vector
+#pragma unroll
+        for (int i = 0; i < 4; ++i) racc[i] += rv[i];
+        if ((zr & (L.fz - 1)) == L.fz - 1) {
+          float v[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            v[i] = racc[i];
+            racc[i] = 0.f;
+          }
+          if (L.fy == 2) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 16);
+          }
+          int cnt = 4;
+          if (L.fx == 2) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) v[j] = v[2 * j] + v[2 * j + 1];
+            cnt = 2;
+          }
+          if (L.fy == 1 || (s.y & 1) == 0) {
+            float* dst = C.f + (long long)(zr >> (L.fz - 1)) * C.g.nxy + (long long)(s.y >> (L.fy - 1)) * C.g.nx +
+                         (s.x >> (L.fx - 1));
+            for (int j = 0; j < cnt; ++j) dst[j] = v[j] * scale;
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        em2[i] = em1[i];
+        em1[i] = e0[i];
+      }
+    }
+    cp_wait<0>();
   }
   sched_finish(ts);
 }
@@ -868,6 +1072,29 @@ static int rr_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Sc
   k_mg_rr<T, VX, E><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, cv, S);
   return 1;
 }
+// The fused pre-smoother + residual on a split FP32 level without eps and with
+// whole tiles: face-slab pre-smoother, fused interior, face-slab residual
+// (3 launches, as the split pre-smoother plus the residual).  0: not eligible.
+template <typename T>
+static int prr_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
+  if constexpr (sizeof(T) != 4) {
+    return 0;
+  } else {
+    MgView<T> vi, vb;
+    if (lv.eps || lv.mc.vx != 4 || lv.g.nx % (MTX * 4) != 0 || lv.g.ny % MTY != 0 || !split_views(lv, vi, vb))
+      return 0;
+    static bool f = false;
+    static int res = 0;
+    const size_t bytes = prr_smem_bytes();
+    smem_once(k_mg_prr, bytes, f);
+    pre_l<T, 4, false, false>(L, vb, S);
+    const int grid = mg_grid(k_mg_prr, bytes, vi.mc.ntiles, res);
+    k_mg_prr<<<grid, dim3(MTX, MTY), bytes, L.stream>>>(vi, cv, S);
+    rr_v<T, 4, false>(L, vb, cv, S);
+    return 3;
+  }
+}
+
 template <typename T, int VX, bool E, bool I>
 static void post1_l(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
   static bool f = false;
@@ -923,6 +1150,11 @@ int launch_mg_pre(const LaunchCfg& L, const MgView<T>& lv, Scalars* S) {
     return lv.mc.vx > 1 ? pre_v<T, V, false>(L, lv, S)
                         : pre_v<T, 1, false>(L, lv, S);
   }
+}
+
+template <typename T>
+int launch_mg_prr(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
+  return prr_v<T>(L, lv, cv, S);
 }
 
 template <typename T>
@@ -1048,6 +1280,7 @@ int mg_blocks_per_sm() {
 #define PF_MG_INSTANTIATE(T)                                                           \
   template int launch_mg_pre<T>(const LaunchCfg&, const MgView<T>&, Scalars*);                   \
   template int launch_mg_rr<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*);  \
+  template int launch_mg_prr<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*); \
   template void launch_mg_coarse<T>(const LaunchCfg&, const MgView<T>&, int, Scalars*);          \
   template void launch_mg_tail<T>(const LaunchCfg&, const MgTail<T>&, int, Scalars*);            \
   template int launch_mg_post1<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*); \

@@ -44,15 +44,16 @@ template <typename T, bool EPS, int VX, int X = 0>
 using StepPipe = Pipe<T, void, MTX, MTY, VX, (EPS ? 5 : 4) + X, EPS ? 1 : 0, STEP_D>;
 
 // Face values of P along the face normal (reading of the boundary kinds).
+// Between two interior cells the face values (P_c + P_n)/2 of a component
+// cancel their P_c: the pair of faces normal to x adds (P_x+ - P_x-)/2, which
+// is formed directly (fewer operations and no rounding of P_c + P_n).
 template <typename T, int NH>
 __device__ __forceinline__ T divergence(const Stencil7<Raw<T, NH>>& s, int dlo, int dhi) {
   const T h = T(0.5);
-  const T pxc = s.c.v[0], pyc = s.c.v[1], pzc = s.c.v[2];
-  T div = T(0);
-  div += -(h * (pxc + s.xm.v[0]));
-  div += h * (pxc + s.xp.v[0]);
-  div += -(h * (pyc + s.ym.v[1]));
-  div += h * (pyc + s.yp.v[1]);
+  const T pzc = s.c.v[2];
+  T div = h * (s.xp.v[0] - s.xm.v[0]);
+  div += h * (s.yp.v[1] - s.ym.v[1]);
+  if (s.zb >= 0 && s.za >= 0) return div + h * (s.zp.v[2] - s.zm.v[2]);
   if (s.zb >= 0) div += -(h * (pzc + s.zm.v[2]));
   else if (dlo) div += -pzc;
   if (s.za >= 0) div += h * (pzc + s.zp.v[2]);
@@ -284,8 +285,8 @@ __global__ void __launch_bounds__(MTX* MTY, 2) k_tdgl(Geo g, Bc<T> bc, const T* 
     // E = -grad phi from face values (mean inside, V at an electrode, phi_cell at an open face)
     const T fc = st.c.v[3];
     T E[3];
-    E[0] = -(h * (fc + st.xp.v[3]) - h * (fc + st.xm.v[3])) * ih;
-    E[1] = -(h * (fc + st.yp.v[3]) - h * (fc + st.ym.v[3])) * ih;
+    E[0] = -(h * (st.xp.v[3] - st.xm.v[3])) * ih;      // the face values' phi_c cancels
+    E[1] = -(h * (st.yp.v[3] - st.ym.v[3])) * ih;
     T flo, fhi;
     if (st.zb >= 0) flo = h * (fc + st.zm.v[3]);
     else flo = bc.tlo[xy] ? bc.vlo[xy] : fc;
