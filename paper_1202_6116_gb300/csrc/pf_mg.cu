@@ -82,22 +82,25 @@ __device__ __forceinline__ T apply_aniso(const Stencil7<T>& s, int dlo, int dhi,
 }
 
 // The interior 7-point operator (eps = 1) and the two pre-sweeps from zero,
-// every operation rounded as written (no contraction into FMAs): the kernels
-// that form them on the same cell -- the pre-smoother, the residual and their
-// fused form on a split level -- then agree bit for bit.
+// every operation rounded as written, with the fused multiply-adds spelled
+// out (no contraction left to the compiler): the kernels that form them on
+// the same cell -- the pre-smoother, the residual and their fused form on a
+// split level -- then agree bit for bit.
 __device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 template <typename T>
 __device__ __forceinline__ T apply_int(T c, T xm, T xp, T ym, T yp, T zm, T zp, T ax, T ay, T az) {
   const T sx = rn_add(rn_sub(c, xm), rn_sub(c, xp));
   const T sy = rn_add(rn_sub(c, ym), rn_sub(c, yp));
   const T sz = rn_add(rn_sub(c, zm), rn_sub(c, zp));
-  return rn_add(rn_add(rn_mul(ax, sx), rn_mul(ay, sy)), rn_mul(az, sz));
+  return rn_fma(ax, sx, rn_fma(ay, sy, rn_mul(az, sz)));
 }
 
 // e = e1 + w2 D^-1 (f - A e1), e1 = w1 D^-1 f, with D constant (w1 = omega1 / d,
@@ -105,7 +108,7 @@ __device__ __forceinline__ T apply_int(T c, T xm, T xp, T ym, T yp, T zm, T zp, 
 template <typename T>
 __device__ __forceinline__ T pre_int(T c, T xm, T xp, T ym, T yp, T zm, T zp, T ax, T ay, T az, T w1, T w2d) {
   const T Ae1 = rn_mul(w1, apply_int(c, xm, xp, ym, yp, zm, zp, ax, ay, az));
-  return rn_add(rn_mul(w1, c), rn_mul(w2d, rn_sub(c, Ae1)));
+  return rn_fma(w2d, rn_sub(c, Ae1), rn_mul(w1, c));
 }
 
 template <typename T>
@@ -344,6 +347,7 @@ __global__ void __launch_bounds__(MTX* MTY, 4) k_mg_prr(MgView<float> L, MgView<
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   static_assert(MTX == 16 && MTY == 16, "tiles of 64 x 16 columns, four cells a thread");
+  static_assert(PRR_RH * 16 <= 2 * MTX * MTY && PRR_RH * 4 <= MTX * MTY, "a plane's copies: two vectors and one ring cell a thread");
   if (S->done) return;
   float* const stg = reinterpret_cast<float*>(smem);
   float* const eb = stg + PRR_NS * PRR_STAGE;
@@ -371,29 +375,38 @@ __global__ void __launch_bounds__(MTX* MTY, 4) k_mg_prr(MgView<float> L, MgView<
   for (long long t = sched_first(ts, &tile_slot); t < L.mc.ntiles; t = sched_next(ts, &tile_slot)) {
     const TileGeo<MTX, MTY, 4> s = tile_geo<MTX, MTY, 4>(L.g, t, L.mc);
     const int x0 = s.x - 4 * tx, y0 = s.y - ty, z0 = s.z0, nt = s.z1 - s.z0;
-    // f plane w (z = z0 - 2 + w) into stage w mod PRR_NS: 20 rows of 16
-    // vectors, and the ring columns x0 - 2, x0 - 1, x0 + 64, x0 + 65
+    // A staged f plane is 20 rows of 16 vectors (320 copies) plus the ring
+    // columns x0 - 2, x0 - 1, x0 + 64, x0 + 65 (80 copies): this thread's share
+    // (vectors tid and tid + 256, ring cell tid), located once per tile.
+    auto row_of = [&](int r) {
+      int y = y0 - 2 + r;
+      y += y < 0 ? ny : 0;
+      y -= y >= ny ? ny : 0;
+      return y * nx;
+    };
+    const int sv0 = (tid >> 4) * PRR_RS + 4 + 4 * (tid & 15), gv0 = row_of(tid >> 4) + x0 + 4 * (tid & 15);
+    const int i1 = tid + MTX * MTY;
+    const bool has1 = i1 < PRR_RH * 16;
+    const int sv1 = has1 ? (i1 >> 4) * PRR_RS + 4 + 4 * (i1 & 15) : 0;
+    const int gv1 = has1 ? row_of(i1 >> 4) + x0 + 4 * (i1 & 15) : 0;
+    const bool hasr = tid < PRR_RH * 4;
+    int svr = 0, gvr = 0;
+    if (hasr) {
+      const int r = tid >> 2, k = tid & 3;
+      int x = k < 2 ? x0 - 2 + k : x0 + 62 + k;
+      x += x < 0 ? nx : 0;
+      x -= x >= nx ? nx : 0;
+      svr = r * PRR_RS + (k < 2 ? 2 + k : 66 + k);
+      gvr = row_of(r) + x;
+    }
+    // f plane w (z = z0 - 2 + w) into stage w mod PRR_NS
     auto issue = [&](int w) {
       if (w <= nt + 3) {
         float* st = stg + (w % PRR_NS) * PRR_STAGE;
         const float* src = L.f + (long long)(z0 - 2 + w) * nxy;
-        for (int i = tid; i < PRR_RH * 16; i += MTX * MTY) {
-          const int r = i >> 4, v = i & 15;
-          int y = y0 - 2 + r;
-          y += y < 0 ? ny : 0;
-          y -= y >= ny ? ny : 0;
-          cp_async<16>(st + r * PRR_RS + 4 + 4 * v, src + (long long)y * nx + x0 + 4 * v);
-        }
-        for (int i = tid; i < PRR_RH * 4; i += MTX * MTY) {
-          const int r = i >> 2, k = i & 3;
-          int y = y0 - 2 + r;
-          y += y < 0 ? ny : 0;
-          y -= y >= ny ? ny : 0;
-          int x = k < 2 ? x0 - 2 + k : x0 + 62 + k;
-          x += x < 0 ? nx : 0;
-          x -= x >= nx ? nx : 0;
-          cp_async<4>(st + r * PRR_RS + (k < 2 ? 2 + k : 66 + k), src + (long long)y * nx + x);
-        }
+        cp_async<16>(st + sv0, src + gv0);
+        if (has1) cp_async<16>(st + sv1, src + gv1);
+        if (hasr) cp_async<4>(st + svr, src + gvr);
       }
       cp_commit();
     };
@@ -425,7 +438,10 @@ __global__ void __launch_bounds__(MTX* MTY, 4) k_mg_prr(MgView<float> L, MgView<
         load4(sp + so, fp);
         load4(sc + so - PRR_RS, fym);
         load4(sc + so + PRR_RS, fyp);
-        const float fl = sc[so - 1], fr = sc[so + 4];
+        // x neighbours at the vector ends: the next lanes' vectors, or the ring at the tile edge
+        float fl = __shfl_up_sync(0xffffffffu, fc[3], 1), fr = __shfl_down_sync(0xffffffffu, fc[0], 1);
+        if (tx == 0) fl = sc[so - 1];
+        if (tx == MTX - 1) fr = sc[so + 4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
           e0[i] = pre_int(fc[i], i == 0 ? fl : fc[i - 1], i == 3 ? fr : fc[i + 1], fym[i], fyp[i], fm[i], fp[i], ax,
@@ -444,7 +460,9 @@ __global__ void __launch_bounds__(MTX* MTY, 4) k_mg_prr(MgView<float> L, MgView<
         load4(ebm + eo - PRR_RS, eym);
         load4(ebm + eo + PRR_RS, eyp);
         load4(sm + so, fv);                // f of plane z - 1 is f plane u
-        const float el = ebm[eo - 1], er = ebm[eo + 4];
+        float el = __shfl_up_sync(0xffffffffu, ec[3], 1), er = __shfl_down_sync(0xffffffffu, ec[0], 1);
+        if (tx == 0) el = ebm[eo - 1];
+        if (tx == MTX - 1) er = ebm[eo + 4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
           rv[i] = rn_sub(fv[i], apply_int(ec[i], i == 0 ? el : ec[i - 1], i == 3 ? er : ec[i + 1], eym[i], eyp[i],
