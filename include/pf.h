@@ -74,7 +74,7 @@ typedef struct {
   double g;                  /* gradient coefficient G11, Eq. dF_grad/dP */
   double L;                  /* mobility multiplying -dF/dP in Eq. TDGL */
   double dt;                 /* time step */
-  int32_t precision;         /* PF_FP64 or PF_FP32 (FP32 fields, FP64-accurate dots) */
+  int32_t precision;         /* PF_FP64 or PF_FP32 (FP32 fields; dots compensated, reduced in FP64) */
   int32_t solver;            /* PF_PCG_JACOBI or PF_PCG_MG */
   double poisson_rtol;       /* stop when ||b - A phi||_2 / ||b||_2 < rtol (recursive residual) */
   int32_t poisson_maxit;     /* iteration cap per solve (>= 1) */
