@@ -301,24 +301,26 @@ namespace {
 
 enum Fam {
   F_RHS_MEAN, F_RHS, F_CG_P, F_CG_R, F_FINISH, F_SUB_MEAN, F_TDGL, F_INVDIAG, F_TDGL_ADJ, F_DIAG, F_EXTRAP,
-  F_MG_PRE, F_MG_RR, F_MG_COARSE, F_MG_POST1, F_MG_POST2, F_COUNT
+  F_MG_PRE, F_MG_RR, F_MG_COARSE, F_MG_POST1, F_MG_POST2, F_MG_PRR, F_MG_PP, F_COUNT
 };
 const char* const FAM_NAMES[F_COUNT] = {"rhs_mean", "rhs",      "cg_p",     "cg_r",     "cg_finish",
                                         "sub_mean", "tdgl",     "invdiag",  "tdgl_adj", "diag",     "extrap",
-                                        "mg_pre",   "mg_rr",    "mg_bottom", "mg_post1", "mg_post2"};
+                                        "mg_pre",   "mg_rr",    "mg_bottom", "mg_post1", "mg_post2", "mg_prr",
+                                        "mg_pp"};
+constexpr int MG_KINDS = F_COUNT - F_MG_PRE;
 
-// Multigrid families are kept per level: family id F_COUNT + level * 5 + kind.
-int mg_fam(int kind, size_t level) { return F_COUNT + (int)level * 5 + (kind - F_MG_PRE); }
+// Multigrid families are kept per level: family id F_COUNT + level * MG_KINDS + kind.
+int mg_fam(int kind, size_t level) { return F_COUNT + (int)level * MG_KINDS + (kind - F_MG_PRE); }
 
 void prof_reset(pf_ctx* ctx) {
-  const int total = F_COUNT + 5 * pf::MG_MAX_LEVELS;
+  const int total = F_COUNT + MG_KINDS * pf::MG_MAX_LEVELS;
   ctx->stats.assign(total, pf_kernel_stat{});
   for (int f = 0; f < total; ++f) {
     if (f < F_COUNT)
       std::snprintf(ctx->stats[f].name, sizeof(ctx->stats[f].name), "%s", FAM_NAMES[f]);
     else
-      std::snprintf(ctx->stats[f].name, sizeof(ctx->stats[f].name), "%s.L%d", FAM_NAMES[F_MG_PRE + (f - F_COUNT) % 5],
-                    (f - F_COUNT) / 5);
+      std::snprintf(ctx->stats[f].name, sizeof(ctx->stats[f].name), "%s.L%d",
+                    FAM_NAMES[F_MG_PRE + (f - F_COUNT) % MG_KINDS], (f - F_COUNT) / MG_KINDS);
   }
   ctx->recs.clear();
   ctx->have_base = false;
@@ -491,19 +493,29 @@ void vcycle(pf_ctx* ctx, int j) {
   pf::Scalars* S = (pf::Scalars*)(ctx->ws + ctx->lay.S);
   double* part = (double*)(ctx->ws + ctx->lay.part);
   const double e = ctx->prm.has_eps ? 1.0 : 0.0;   // eps read with the field, 1/diag with f
+  // Fused post-sweeps on the finest level keep the pre-smoothed correction out
+  // of z (in z_tmp) and put e' in q, which is dead between the residual update
+  // and the next search direction.
+  const bool fused_post = k0 > 0 && pf::mg_fused_post<T>(mg_view<T>(ctx, 0));
+  auto view = [&](size_t k) {
+    pf::MgView<T> v = mg_view<T>(ctx, k);
+    if (k == 0 && fused_post) v.e = v.et;
+    return v;
+  };
   for (size_t k = 0; k < k0; ++k) {
-    const pf::MgView<T> lv = mg_view<T>(ctx, k), cv = mg_view<T>(ctx, k + 1);
+    const pf::MgView<T> lv = view(k), cv = view(k + 1);
     const double N = (double)lv.g.n;
     before_launch(ctx);
     const double rest = 1.0 / (lv.fx * lv.fy * lv.fz);
-    int nk = pf::launch_mg_prr<T>(ctx->L, lv, cv, S);
-    if (nk > 0) {     // fused interior: f read once, e and the coarse rhs written; face slabs as before
-      const double Nf = 2.0 * pf::MG_SPLIT_B * (double)lv.g.nxy;
-      after_launch(ctx, mg_fam(F_MG_PRE, k), ((2 + rest) * (N - Nf) + (4 + rest) * Nf) * w, 2, j);
-      ctx->launches += nk - 1;
-      continue;
-    }
-    nk = pf::launch_mg_pre<T>(ctx->L, lv, S);
+    const double Nf = 2.0 * pf::MG_SPLIT_B * (double)lv.g.nxy;   // cells of the face slabs of a split level
+    // fused interior (f read once, e and the coarse rhs written) between the face slabs' own launches
+    const int nf = pf::launch_mg_prr<T>(ctx->L, lv, cv, S, [&](int part_no) {
+      if (part_no == 0) after_launch(ctx, mg_fam(F_MG_PRE, k), 2 * Nf * w, 2, j);
+      else if (part_no == 1) after_launch(ctx, mg_fam(F_MG_PRR, k), (2 + rest) * (N - Nf) * w, 2, j);
+      else after_launch(ctx, mg_fam(F_MG_RR, k), (2 + rest) * Nf * w, 2, j);
+    });
+    if (nf > 0) continue;
+    int nk = pf::launch_mg_pre<T>(ctx->L, lv, S);
     after_launch(ctx, mg_fam(F_MG_PRE, k), (2 + 2 * e) * N * w, 2, j);
     ctx->launches += nk - 1;
     nk = pf::launch_mg_rr<T>(ctx->L, lv, cv, S);
@@ -531,9 +543,20 @@ void vcycle(pf_ctx* ctx, int j) {
     after_launch(ctx, mg_fam(F_MG_COARSE, nl - 1), 2.0 * (double)cv.g.n * w, 2, j);
   }
   for (size_t k = k0; k-- > 0;) {
-    const pf::MgView<T> lv = mg_view<T>(ctx, k), cv = mg_view<T>(ctx, k + 1);
+    const pf::MgView<T> lv = view(k), cv = view(k + 1);
     const double N = (double)lv.g.n;
     before_launch(ctx);
+    if (k == 0 && fused_post) {
+      T* const z = mg_view<T>(ctx, 0).e;
+      const double Nf = 2.0 * pf::MG_SPLIT_B * (double)lv.g.nxy, rest = 1.0 / (lv.fx * lv.fy * lv.fz);
+      // face slabs' first sweep, fused interior (e, e_c and f read, the result written), face slabs' second sweep
+      pf::launch_mg_pp<T>(ctx->L, lv, cv, (T*)(ctx->ws + ctx->lay.q), z, part, S, [&](int part_no) {
+        if (part_no == 0) after_launch(ctx, mg_fam(F_MG_POST1, k), (3 + rest) * Nf * w, 2, j);
+        else if (part_no == 1) after_launch(ctx, mg_fam(F_MG_PP, k), (3 + rest) * (N - Nf) * w, 2, j);
+        else after_launch(ctx, mg_fam(F_MG_POST2, k), 3 * Nf * w, 2, j);
+      });
+      continue;
+    }
     int nk = pf::launch_mg_post1<T>(ctx->L, lv, cv, S);
     after_launch(ctx, mg_fam(F_MG_POST1, k), (3 + 2 * e + 1.0 / (lv.fx * lv.fy * lv.fz)) * N * w, 2, j);
     ctx->launches += nk - 1;

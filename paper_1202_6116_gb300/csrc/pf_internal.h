@@ -1,6 +1,8 @@
 // Internal interface between the C ABI (pf_api.cu) and the kernel launchers.
 #pragma once
 
+#include <functional>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -266,8 +268,22 @@ int launch_mg_rr(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, S
 // Pre-smoother and residual of a split FP32 level as one fused pass over its
 // interior planes (plus the face slabs' own kernels); returns the launches, 0
 // when the level does not qualify (then nothing was launched).
+// mark(i) is called after the i-th of its launches (0 .. 2; the profiler's marks).
 template <typename T>
-int launch_mg_prr(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S);
+int launch_mg_prr(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S,
+                  const std::function<void(int)>& mark);
+// Whether the finest level's post-sweeps run fused (launch_mg_pp); then the
+// V-cycle keeps the pre-smoothed correction out of z (in z_tmp) and uses ep
+// (the CG's q, dead between the residual update and the next search
+// direction) for e'.
+template <typename T>
+bool mg_fused_post(const MgView<T>& lv);
+// Prolongation sweep + second post-sweep of the finest level, fused on its
+// interior (lv.e: the pre-smoothed correction, ep: e', z: the result; r.z and
+// beta as k_mg_post2); returns the launches, 0 when not eligible.
+template <typename T>
+int launch_mg_pp(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, T* ep, T* z, double* part,
+                 Scalars* S, const std::function<void(int)>& mark);
 template <typename T>
 void launch_mg_coarse(const LaunchCfg& L, const MgView<T>& cv, int singular, Scalars* S);
 template <typename T>

@@ -507,6 +507,214 @@ __global__ void __launch_bounds__(MTX* MTY, 4) k_mg_prr(MgView<float> L, MgView<
   sched_finish(ts);
 }
 
+// Prolongation sweep and second post-sweep fused, on the interior planes of the
+// split finest level (FP32, eps = 1, whole tiles, every coarsening factor 2).
+// Three fields are kept apart: the pre-smoothed correction L.e (read), e' in
+// L.et and the result zout -- reading e with a ring while writing the result
+// in place would race with the neighbouring tiles.
+//   e' = u + w2 D^-1 (f - A u),  u = e + P e_c      (k_mg_post1)
+//   e'' = e' + w1 D^-1 (f - A e')                   (k_mg_post2, with r.z)
+// in one pass: e, e_c and f read, e'' written, instead of writing e' and
+// reading it and f again.  The second sweep needs e' at six neighbours and e'
+// needs u at six, so a tile stages e and f with a two-cell ring and the coarse
+// parents of that box, and forms e' on its columns and the one-cell ring, one
+// plane ahead of e''.  e' of the plane below or above the tile is formed too,
+// except next to a face slab (planes 1 and nz - 2), where it is the face-slab
+// prolongation sweep's output (that launch runs first); e' of planes 2 and
+// nz - 3 is written for the face-slab second sweep (which runs after this one
+// and sums the r.z tile partials of both launches: this one's first).
+constexpr int PP_NS = 5;                   // staged planes: w, w + 1, w + 2 in use, two in flight
+constexpr int PP_CW = 40, PP_CH = 10;      // coarse box: x0/2 - 4 .. x0/2 + 35, y0/2 - 1 .. y0/2 + 8
+constexpr int PP_STAGE = 2 * PRR_STAGE + PP_CW * PP_CH;   // e, f, parents
+constexpr size_t pp_smem_bytes() { return (size_t)(PP_NS * PP_STAGE + 2 * PRR_EPLANE) * sizeof(float); }
+
+__global__ void __launch_bounds__(MTX* MTY, 2) k_mg_pp(MgView<float> L, MgView<float> C, float* zout,
+                                                       double* part, Scalars* S) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long tile_slot;
+  static_assert(MTX == 16 && MTY == 16, "tiles of 64 x 16 columns, four cells a thread");
+  static_assert(PP_CW * PP_CH / 4 <= MTX * MTY, "one coarse vector a thread");
+  if (S->done) return;
+  float* const stg = reinterpret_cast<float*>(smem);
+  float* const eb = stg + PP_NS * PP_STAGE;
+  const int nx = L.g.nx, ny = L.g.ny, nz = L.g.nz, cnx = C.g.nx, cny = C.g.ny;
+  const long long nxy = L.g.nxy, cnxy = C.g.nxy;
+  const float inv_int = mg_inv_int(L);
+  const float w2d = rn_mul(mg_omega2<float>(), inv_int), w1d = rn_mul(mg_omega1<float>(), inv_int);
+  const float ax = L.ax, ay = L.ay, az = L.az;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * MTX;
+  const int c0 = 4 + 4 * tx;
+  const int so = (ty + 2) * PRR_RS + c0;   // own vector in a staged field plane
+  const int eo = (ty + 1) * PRR_RS + c0;   // own vector in an e' plane
+  int rr = -1, re = -1, rc = -1;           // ring cell of threads 0 .. 159
+  if (tid < 64) { rr = 1; re = 0; rc = 4 + tid; }
+  else if (tid < 128) { rr = 18; re = 17; rc = 4 + tid - 64; }
+  else if (tid < 144) { rr = 2 + tid - 128; re = 1 + tid - 128; rc = 3; }
+  else if (tid < 160) { rr = 2 + tid - 144; re = 1 + tid - 144; rc = 68; }
+  auto load4 = [](const float* p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  };
+  Acc<float> arz;
+  const TileSched ts{&S->sched_next, &S->sched_done, L.mc.ntiles};
+  for (long long t = sched_first(ts, &tile_slot); t < L.mc.ntiles; t = sched_next(ts, &tile_slot)) {
+    const TileGeo<MTX, MTY, 4> s = tile_geo<MTX, MTY, 4>(L.g, t, L.mc);
+    const int x0 = s.x - 4 * tx, y0 = s.y - ty, z0 = s.z0, nt = s.z1 - s.z0;
+    auto row_of = [&](int r) {
+      int y = y0 - 2 + r;
+      y += y < 0 ? ny : 0;
+      y -= y >= ny ? ny : 0;
+      return y * nx;
+    };
+    // this thread's copies of a staged plane: e and f vectors tid, tid + 256
+    // (of 320), ring cell tid (of 80), and coarse vector tid (of 100)
+    const int sv0 = (tid >> 4) * PRR_RS + 4 + 4 * (tid & 15), gv0 = row_of(tid >> 4) + x0 + 4 * (tid & 15);
+    const int i1 = tid + MTX * MTY;
+    const bool has1 = i1 < PRR_RH * 16;
+    const int sv1 = has1 ? (i1 >> 4) * PRR_RS + 4 + 4 * (i1 & 15) : 0;
+    const int gv1 = has1 ? row_of(i1 >> 4) + x0 + 4 * (i1 & 15) : 0;
+    const bool hasr = tid < PRR_RH * 4;
+    int svr = 0, gvr = 0;
+    if (hasr) {
+      const int r = tid >> 2, k = tid & 3;
+      int x = k < 2 ? x0 - 2 + k : x0 + 62 + k;
+      x += x < 0 ? nx : 0;
+      x -= x >= nx ? nx : 0;
+      svr = r * PRR_RS + (k < 2 ? 2 + k : 66 + k);
+      gvr = row_of(r) + x;
+    }
+    const bool hasc = tid < PP_CW * PP_CH / 4;
+    int svc = 0, gvc = 0;
+    if (hasc) {
+      const int r = tid / (PP_CW / 4), v = tid % (PP_CW / 4);
+      int y = y0 / 2 - 1 + r;
+      y += y < 0 ? cny : 0;
+      y -= y >= cny ? cny : 0;
+      int x = x0 / 2 - 4 + 4 * v;          // whole 16-byte vectors: x0 / 2 is a multiple of 32
+      x += x < 0 ? cnx : 0;
+      x -= x >= cnx ? cnx : 0;
+      svc = r * PP_CW + 4 * v;
+      gvc = y * cnx + x;
+    }
+    // e, f and the parents of plane w (z = z0 - 2 + w) into stage w mod PP_NS
+    auto issue = [&](int w) {
+      if (w <= nt + 3) {
+        const int z = z0 - 2 + w;
+        float* st = stg + (w % PP_NS) * PP_STAGE;
+        const float* se = L.e + (long long)z * nxy;
+        const float* sf = L.f + (long long)z * nxy;
+        cp_async<16>(st + sv0, se + gv0);
+        cp_async<16>(st + PRR_STAGE + sv0, sf + gv0);
+        if (has1) {
+          cp_async<16>(st + sv1, se + gv1);
+          cp_async<16>(st + PRR_STAGE + sv1, sf + gv1);
+        }
+        if (hasr) {
+          cp_async<4>(st + svr, se + gvr);
+          cp_async<4>(st + PRR_STAGE + svr, sf + gvr);
+        }
+        if (hasc) cp_async<16>(st + 2 * PRR_STAGE + svc, C.e + (long long)(z >> 1) * cnxy + gvc);
+      }
+      cp_commit();
+    };
+    // u = e + P e_c at staged cell (r, c) of a stage: the parent of column c is
+    // coarse column 2 + c / 2 of the box, of row r the coarse row r / 2
+    auto u_at = [&](const float* st, int r, int c) -> float {
+      return st[r * PRR_RS + c] + st[2 * PRR_STAGE + (r >> 1) * PP_CW + 2 + (c >> 1)];
+    };
+    // e' at staged cell (r, c) from the stages of the planes below, at and above it
+    auto ep_at = [&](const float* sm, const float* sc, const float* sp, int r, int c) -> float {
+      const float uc = u_at(sc, r, c);
+      const float Au = apply_int(uc, u_at(sc, r, c - 1), u_at(sc, r, c + 1), u_at(sc, r - 1, c), u_at(sc, r + 1, c),
+                                 u_at(sm, r, c), u_at(sp, r, c), ax, ay, az);
+      return rn_fma(w2d, rn_sub(sc[PRR_STAGE + r * PRR_RS + c], Au), uc);
+    };
+    float em2[4], e0[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) em2[i] = e0[i] = 0.f;
+    float em1[4] = {0.f, 0.f, 0.f, 0.f};
+    arz = Acc<float>();
+    for (int w = 0; w < 4; ++w) issue(w);
+    for (int u = 0; u <= nt + 1; ++u) {
+      cp_wait<1>();                        // planes u .. u + 2 of this thread have landed
+      __syncthreads();                     // ... and of every thread
+      issue(u + 4);
+      const float* sm = stg + (u % PP_NS) * PP_STAGE;
+      const float* sc = stg + ((u + 1) % PP_NS) * PP_STAGE;
+      const float* sp = stg + ((u + 2) % PP_NS) * PP_STAGE;
+      float* ebu = eb + (u & 1) * PRR_EPLANE;
+      const int z = z0 - 1 + u;
+      if (z == 1 || z == nz - 2) {
+        load4(L.et + (long long)z * nxy + s.xy, e0);
+      } else {
+        // e' on the own vector: u = e + parent on the vector, its rows above and
+        // below, the planes below and above, and the two cells beside it
+        const int r = ty + 2, pc = 4 + 2 * tx;          // parent columns of the vector: pc, pc + 1
+        const float* pb = sc + 2 * PRR_STAGE;
+        float ec[4], eym[4], eyp[4], ezm[4], ezp[4], fc[4];
+        load4(sc + so, ec);
+        load4(sc + so - PRR_RS, eym);
+        load4(sc + so + PRR_RS, eyp);
+        load4(sm + so, ezm);
+        load4(sp + so, ezp);
+        load4(sc + PRR_STAGE + so, fc);
+        auto par2 = [](const float* q) { return *reinterpret_cast<const float2*>(q); };
+        const float2 pC = par2(pb + (r >> 1) * PP_CW + pc), pYM = par2(pb + ((r - 1) >> 1) * PP_CW + pc),
+                     pYP = par2(pb + ((r + 1) >> 1) * PP_CW + pc),
+                     pZM = par2(sm + 2 * PRR_STAGE + (r >> 1) * PP_CW + pc),
+                     pZP = par2(sp + 2 * PRR_STAGE + (r >> 1) * PP_CW + pc);
+        const float uL = sc[so - 1] + pb[(r >> 1) * PP_CW + pc - 1];
+        const float uR = sc[so + 4] + pb[(r >> 1) * PP_CW + pc + 2];
+        float uc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) uc[i] = ec[i] + (i < 2 ? pC.x : pC.y);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float ym = eym[i] + (i < 2 ? pYM.x : pYM.y), yp = eyp[i] + (i < 2 ? pYP.x : pYP.y);
+          const float zm = ezm[i] + (i < 2 ? pZM.x : pZM.y), zp = ezp[i] + (i < 2 ? pZP.x : pZP.y);
+          const float Au = apply_int(uc[i], i == 0 ? uL : uc[i - 1], i == 3 ? uR : uc[i + 1], ym, yp, zm, zp, ax, ay, az);
+          e0[i] = rn_fma(w2d, rn_sub(fc[i], Au), uc[i]);
+        }
+      }
+      if (u >= 1 && u <= nt) {
+        *reinterpret_cast<float4*>(ebu + eo) = make_float4(e0[0], e0[1], e0[2], e0[3]);
+        if (rc >= 0) ebu[re * PRR_RS + rc] = ep_at(sm, sc, sp, rr, rc);
+        if (z == 2 || z == nz - 3)         // handed to the face-slab second sweep
+          *reinterpret_cast<float4*>(L.et + (long long)z * nxy + s.xy) = make_float4(e0[0], e0[1], e0[2], e0[3]);
+      }
+      if (u >= 2) {                        // e'' of plane z - 1
+        const float* ebm = eb + ((u - 1) & 1) * PRR_EPLANE;
+        float ec[4], eym[4], eyp[4], fv[4], ev[4];
+        load4(ebm + eo, ec);
+        load4(ebm + eo - PRR_RS, eym);
+        load4(ebm + eo + PRR_RS, eyp);
+        load4(sm + PRR_STAGE + so, fv);    // f of plane z - 1: stage u
+        float el = __shfl_up_sync(0xffffffffu, ec[3], 1), er = __shfl_down_sync(0xffffffffu, ec[0], 1);
+        if (tx == 0) el = ebm[eo - 1];
+        if (tx == MTX - 1) er = ebm[eo + 4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float Ae = apply_int(ec[i], i == 0 ? el : ec[i - 1], i == 3 ? er : ec[i + 1], eym[i], eyp[i], em2[i],
+                                     e0[i], ax, ay, az);
+          ev[i] = rn_fma(w1d, rn_sub(fv[i], Ae), ec[i]);
+          arz.add(fv[i], ev[i]);
+        }
+        arz.run();
+        *reinterpret_cast<float4*>(zout + (long long)(z - 1) * nxy + s.xy) = make_float4(ev[0], ev[1], ev[2], ev[3]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        em2[i] = em1[i];
+        em1[i] = e0[i];
+      }
+    }
+    cp_wait<0>();
+    double v[1] = {arz.value()};
+    tile_partials<1, MTX * MTY>(v, part, t);
+  }
+  sched_finish(ts);
+}
+
 // Prolongation + correction fused into the first post-smoothing sweep: the
 // stencil field is e + e_c(parent), the parents staged with the fine planes
 // and combined with e at each of the seven cells.
@@ -568,7 +776,11 @@ __global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? 3 : 2) k_
 // Last post-smoothing sweep.  On the finest level (LAST) it also forms
 // r.z (f = r, e = z): the last block sets beta = (r.z)_new / (r.z)_old.
 template <typename T, bool LAST, int VX, bool EPS, bool INT = false>
-__global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? (INT ? 5 : (LAST ? 3 : 4)) : 2) k_mg_post2(MgView<T> L, double* part, Scalars* S) {
+__global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? (INT ? 5 : (LAST ? 3 : 4)) : 2) k_mg_post2(MgView<T> L, double* part, Scalars* S,
+                                                                                                long long pofs,
+                                                                                                long long ptot) {
+  // pofs, ptot (finest level): this launch's tile partials go to part[pofs + t]; the
+  // last block sums part[0 .. ptot) (a fused interior launch wrote the first pofs)
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
   if (S->done) return;
@@ -610,14 +822,14 @@ __global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? (INT ? 5 
     march_direct<T, T, MTX, MTY, VX, NH, NO, MG_D, 0, INT>(L.g, s, smem, hsrc, osrc, emit, post);
     if (LAST) {
       double v[1] = {arz.value()};
-      tile_partials<1, MTX * MTY>(v, part, t);
+      tile_partials<1, MTX * MTY>(v, part + pofs, t);
     }
   }
   sched_finish(ts);
   if (!LAST) return;
   if (last_block<MTX * MTY>(&S->ticket)) {
     double out[1];
-    gather_partials<1, MTX * MTY>(part, L.mc.ntiles, out);
+    gather_partials<1, MTX * MTY>(part, ptot, out);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       const double rz = out[0];
       if (!isfinite(rz)) {
@@ -1094,7 +1306,8 @@ static int rr_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Sc
 // whole tiles: face-slab pre-smoother, fused interior, face-slab residual
 // (3 launches, as the split pre-smoother plus the residual).  0: not eligible.
 template <typename T>
-static int prr_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
+static int prr_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S,
+                 const std::function<void(int)>& mark) {
   if constexpr (sizeof(T) != 4) {
     return 0;
   } else {
@@ -1106,11 +1319,24 @@ static int prr_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, S
     const size_t bytes = prr_smem_bytes();
     smem_once(k_mg_prr, bytes, f);
     pre_l<T, 4, false, false>(L, vb, S);
+    mark(0);
     const int grid = mg_grid(k_mg_prr, bytes, vi.mc.ntiles, res);
     k_mg_prr<<<grid, dim3(MTX, MTY), bytes, L.stream>>>(vi, cv, S);
+    mark(1);
     rr_v<T, 4, false>(L, vb, cv, S);
+    mark(2);
     return 3;
   }
+}
+
+// The finest level's prolongation sweep and second post-sweep as face-slab
+// prolongation sweep, fused interior, face-slab second sweep (3 launches, as
+// the split prolongation sweep plus the unsplit second sweep); lv.e holds the
+// pre-smoothed correction, ep receives e', z the result.  0: not eligible.
+template <typename T>
+static bool pp_ok(const MgView<T>& lv) {
+  return sizeof(T) == 4 && lv.split && !lv.eps && lv.mc.vx == 4 && lv.g.nx % (MTX * 4) == 0 && lv.g.ny % MTY == 0 &&
+         lv.fx == 2 && lv.fy == 2 && lv.fz == 2;
 }
 
 template <typename T, int VX, bool E, bool I>
@@ -1134,13 +1360,15 @@ static int post1_v(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv,
   return 2;
 }
 template <typename T, bool LAST, int VX, bool E, bool I>
-static void post2_l(const LaunchCfg& L, const MgView<T>& lv, double* part, Scalars* S) {
+static void post2_l(const LaunchCfg& L, const MgView<T>& lv, double* part, Scalars* S, long long pofs = 0,
+                    long long ptot = -1) {
   static bool f = false;
   static int res = 0;
   const size_t bytes = MgPipeD<T, VX, E>::bytes();
   smem_once(k_mg_post2<T, LAST, VX, E, I>, bytes, f);
   const int grid = mg_grid(k_mg_post2<T, LAST, VX, E, I>, bytes, lv.mc.ntiles, res);
-  k_mg_post2<T, LAST, VX, E, I><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, part, S);
+  k_mg_post2<T, LAST, VX, E, I><<<grid, dim3(MTX, MTY), bytes, L.stream>>>(lv, part, S, pofs,
+                                                                          ptot < 0 ? lv.mc.ntiles : ptot);
 }
 // The finest level's second post-sweep also reduces r.z over all its tiles,
 // so it is never split.
@@ -1171,8 +1399,9 @@ int launch_mg_pre(const LaunchCfg& L, const MgView<T>& lv, Scalars* S) {
 }
 
 template <typename T>
-int launch_mg_prr(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S) {
-  return prr_v<T>(L, lv, cv, S);
+int launch_mg_prr(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, Scalars* S,
+                  const std::function<void(int)>& mark) {
+  return prr_v<T>(L, lv, cv, S, mark);
 }
 
 template <typename T>
@@ -1214,6 +1443,41 @@ static int post2_e(const LaunchCfg& L, const MgView<T>& lv, int last, double* pa
   } else {
     return lv.mc.vx > 1 ? post2_v<T, false, V, E>(L, lv, part, S)
                         : post2_v<T, false, 1, E>(L, lv, part, S);
+  }
+}
+
+template <typename T>
+bool mg_fused_post(const MgView<T>& lv) {
+  return pp_ok(lv);
+}
+
+template <typename T>
+int launch_mg_pp(const LaunchCfg& L, const MgView<T>& lv, const MgView<T>& cv, T* ep, T* z, double* part,
+                 Scalars* S, const std::function<void(int)>& mark) {
+  if constexpr (sizeof(T) != 4) {
+    return 0;
+  } else {
+    MgView<T> vi, vb;
+    if (!pp_ok(lv) || !split_views(lv, vi, vb)) return 0;
+    MgView<T> v1 = vb;                     // face slabs: e -> e'
+    v1.et = ep;
+    post1_l<T, 4, false, false>(L, v1, cv, S);
+    mark(0);
+    static bool f = false;
+    static int res = 0;
+    const size_t bytes = pp_smem_bytes();
+    smem_once(k_mg_pp, bytes, f);
+    MgView<T> vp = vi;                     // interior: e (and e' of the face-adjacent planes) -> z
+    vp.et = ep;
+    const int grid = mg_grid(k_mg_pp, bytes, vi.mc.ntiles, res);
+    k_mg_pp<<<grid, dim3(MTX, MTY), bytes, L.stream>>>(vp, cv, z, part, S);
+    mark(1);
+    MgView<T> v2 = vb;                     // face slabs: e' -> z, then r.z over both launches' tiles
+    v2.et = ep;
+    v2.e = z;
+    post2_l<T, true, 4, false, false>(L, v2, part, S, vi.mc.ntiles, vi.mc.ntiles + vb.mc.ntiles);
+    mark(2);
+    return 3;
   }
 }
 
@@ -1298,7 +1562,11 @@ int mg_blocks_per_sm() {
 #define PF_MG_INSTANTIATE(T)                                                           \
   template int launch_mg_pre<T>(const LaunchCfg&, const MgView<T>&, Scalars*);                   \
   template int launch_mg_rr<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*);  \
-  template int launch_mg_prr<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*); \
+  template int launch_mg_prr<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*,   \
+                                 const std::function<void(int)>&);                               \
+  template bool mg_fused_post<T>(const MgView<T>&);                                              \
+  template int launch_mg_pp<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, T*, T*, double*, Scalars*, \
+                                const std::function<void(int)>&);                                             \
   template void launch_mg_coarse<T>(const LaunchCfg&, const MgView<T>&, int, Scalars*);          \
   template void launch_mg_tail<T>(const LaunchCfg&, const MgTail<T>&, int, Scalars*);            \
   template int launch_mg_post1<T>(const LaunchCfg&, const MgView<T>&, const MgView<T>&, Scalars*); \

@@ -38,16 +38,43 @@ def _pair(w, steps):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_split_sweeps_match_whole_sweeps_tip(precision):
-    # 512 x 512 x 128 = 2^25 cells: the finest level splits (pre, post1), the next does not
+    # 512 x 512 x 128 = 2^25 cells: the finest level splits, the next does not.  In
+    # FP32 the finest level's pre-smoother + residual and its two post-sweeps also
+    # run fused; the post-sweeps' r.z is then summed over the interior and the face
+    # slabs' tiles in another order and rounded in another grouping, so FP32 is
+    # compared within the solve tolerance, FP64 (nothing fused) bit for bit.
     w = W.film_tip_fp32(512, 512, 128, seed=3).with_(solver="mg", maxit=500, precision=precision,
                                                       rtol=1e-7 if precision == "fp32" else 1e-10)
     (a, ia), (b, ib) = _pair(w, 4)
-    assert torch.equal(a.P, b.P) and torch.equal(a.phi, b.phi)
-    assert ia["total_iters"] == ib["total_iters"] and ia["solves"] == ib["solves"] == 4
+    if precision == "fp64":
+        assert torch.equal(a.P, b.P) and torch.equal(a.phi, b.phi)
+        assert ia["total_iters"] == ib["total_iters"]
+    else:
+        for x, y in ((a.P, b.P), (a.phi, b.phi)):
+            scale = float(y.abs().max())
+            assert float((x - y).abs().max()) <= 1e-5 * scale
+        assert abs(ia["total_iters"] - ib["total_iters"]) <= 4
+    assert ia["solves"] == ib["solves"] == 4
     extra = ia["kernel_launches"] - ib["kernel_launches"]
     assert extra > 0 and extra % 2 == 0          # two more launches per V-cycle
     a.close()
     b.close()
+
+
+def test_fused_finest_level_matches_oracle_grade_solve():
+    """The fused finest-level passes (FP32 tip film, 2^25 cells) solve the
+    potential to the requested tolerance: the true residual of the solved
+    potential, formed in FP64 on the device, stays within a small factor of it."""
+    w = W.film_tip_fp32(512, 512, 128, seed=3).with_(solver="mg", maxit=500)
+    f = Film(w)
+    st, info = f.step(6)
+    assert st == pf.PF_OK and info["nonconverged"] == 0
+    Pprev = f.P.clone()                  # the state the next step's solve is for
+    st, info = f.step(1)
+    assert st == pf.PF_OK and info["last_relres"] < w.rtol
+    stored, bnorm, comp = f.true_residual(Pprev)
+    assert comp / bnorm < 10 * w.rtol
+    f.close()
 
 
 def test_split_sweeps_match_whole_sweeps_open_air():
