@@ -396,8 +396,13 @@ typedef struct {
                                 of a level of >= 2^25 cells (2^23 with eps) whose z faces
                                 are not periodic as two launches, the interior planes with
                                 the face code compiled out and the two face slabs of 2
-                                planes; 1 runs every sweep as one launch.  Results are
-                                identical either way. */
+                                planes; in FP32 without eps the finest level's interior
+                                then also fuses pre-smoother + residual + restriction, and
+                                prolongation sweep + second post-sweep.  1 runs every sweep
+                                as one launch over the whole level.  Results are identical
+                                either way, except that the fused post-sweeps sum r.z in
+                                another order (FP32 results agree within the solve
+                                tolerance). */
 } pf_tiling;
 
 /* Current tiling (the default picks vx = 16 bytes when nx allows it and the
