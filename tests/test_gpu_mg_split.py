@@ -77,6 +77,21 @@ def test_fused_finest_level_matches_oracle_grade_solve():
     f.close()
 
 
+@pytest.mark.parametrize("shape", [(528, 512, 128), (512, 512, 129)])
+def test_split_fallbacks_match_whole_sweeps(shape):
+    """Shapes the fused finest-level passes do not take whole: nx not a multiple
+    of the 64-column tile (split sweeps only), and an odd nz (no z coarsening on
+    the finest level: the fused pre-smoother + residual restricts plane by plane,
+    the post-sweeps stay unfused).  Bit for bit against whole-level sweeps."""
+    w = W.film_tip_fp32(*shape, seed=4).with_(solver="mg", maxit=500)
+    (a, ia), (b, ib) = _pair(w, 3)
+    assert torch.equal(a.P, b.P) and torch.equal(a.phi, b.phi)
+    assert ia["total_iters"] == ib["total_iters"]
+    assert ia["kernel_launches"] > ib["kernel_launches"]
+    a.close()
+    b.close()
+
+
 def test_split_sweeps_match_whole_sweeps_open_air():
     # permittivity field, open top face, 512 x 512 x 37 > 2^23 cells: the eps sweeps split
     w = W.film_open_air(512, 512, 37, seed=5).with_(solver="mg", maxit=500)
