@@ -523,12 +523,13 @@ __global__ void __launch_bounds__(MTX* MTY, 4) k_mg_prr(MgView<float> L, MgView<
 // prolongation sweep's output (that launch runs first); e' of planes 2 and
 // nz - 3 is written for the face-slab second sweep (which runs after this one
 // and sums the r.z tile partials of both launches: this one's first).
-constexpr int PP_NS = 5;                   // staged planes: w, w + 1, w + 2 in use, two in flight
+constexpr int PP_D = 1;                    // planes of cp.async look-ahead
+constexpr int PP_NS = PP_D + 3;            // staged planes: w, w + 1, w + 2 in use, PP_D in flight
 constexpr int PP_CW = 40, PP_CH = 10;      // coarse box: x0/2 - 4 .. x0/2 + 35, y0/2 - 1 .. y0/2 + 8
 constexpr int PP_STAGE = 2 * PRR_STAGE + PP_CW * PP_CH;   // e, f, parents
 constexpr size_t pp_smem_bytes() { return (size_t)(PP_NS * PP_STAGE + 2 * PRR_EPLANE) * sizeof(float); }
 
-__global__ void __launch_bounds__(MTX* MTY, 2) k_mg_pp(MgView<float> L, MgView<float> C, float* zout,
+__global__ void __launch_bounds__(MTX* MTY, 3) k_mg_pp(MgView<float> L, MgView<float> C, float* zout,
                                                        double* part, Scalars* S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long tile_slot;
@@ -634,11 +635,11 @@ __global__ void __launch_bounds__(MTX* MTY, 2) k_mg_pp(MgView<float> L, MgView<f
     for (int i = 0; i < 4; ++i) em2[i] = e0[i] = 0.f;
     float em1[4] = {0.f, 0.f, 0.f, 0.f};
     arz = Acc<float>();
-    for (int w = 0; w < 4; ++w) issue(w);
+    for (int w = 0; w < PP_D + 2; ++w) issue(w);
     for (int u = 0; u <= nt + 1; ++u) {
-      cp_wait<1>();                        // planes u .. u + 2 of this thread have landed
+      cp_wait<PP_D - 1>();                 // planes u .. u + 2 of this thread have landed
       __syncthreads();                     // ... and of every thread
-      issue(u + 4);
+      issue(u + PP_D + 2);
       const float* sm = stg + (u % PP_NS) * PP_STAGE;
       const float* sc = stg + ((u + 1) % PP_NS) * PP_STAGE;
       const float* sp = stg + ((u + 2) % PP_NS) * PP_STAGE;
