@@ -1555,6 +1555,7 @@ pf_status pf_set_tiling(pf_ctx* ctx, const pf_tiling* t) {
   m.tz = std::min(t->tz, g.nz);
   m.ntiles = (long long)m.tiles_x * m.tiles_y * ((g.nz + m.tz - 1) / m.tz);
   m.grid = (int)std::min<long long>(m.ntiles, std::min<long long>(pf::MAX_GRID, (long long)bps * ctx->nsm));
+  m.bps = t->blocks_per_sm;
   drop_graphs(ctx);
   ctx->L.march = m;
   ctx->tile_bps = t->blocks_per_sm;

@@ -30,6 +30,8 @@ struct MarchCfg {
   int grid;
   int vx;
   int zlo, zcut, zskip;
+  int bps;           // resident blocks per SM asked for (0: as many as fit; kernels
+                     // with their own occupancy size their grid by it)
 };
 
 struct Geo {

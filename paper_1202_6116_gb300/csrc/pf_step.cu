@@ -61,6 +61,51 @@ __device__ __forceinline__ T divergence(const Stencil7<Raw<T, NH>>& s, int dlo, 
   return div;
 }
 
+// The last block to finish sums the tiles' partials in tile order and starts
+// the solve: ||b||^2, ||r||^2 and r.z of the warm residual, the convergence
+// test of the start (or, MEAN, the mean of b).  Called by every thread.
+template <int NV, bool MEAN, bool COMP>
+__device__ __forceinline__ void rhs_close(const Geo& g, double* part, Scalars* S, long long ntiles,
+                                          cudaGraphConditionalHandle cond, int use_cond) {
+  if (!last_block<MTX * MTY>(&S->ticket)) return;
+  double out[NV];
+  gather_partials<NV, MTX * MTY>(part, ntiles, out);
+  if (threadIdx.x != 0 || threadIdx.y != 0) return;
+  if (MEAN) {
+    S->mean_b = out[0] / (double)g.n;
+    S->ticket = 0;
+    return;
+  }
+  const double bb = out[0], rr = out[NV > 1 ? 1 : 0], rz = out[NV > 2 ? 2 : 0];
+  S->bb = bb;
+  S->rr = rr;
+  S->rz = rz;
+  S->iter = 0;
+  S->first = 1;
+  S->pending = 0;
+  S->xzero = COMP ? 1 : 0;            // a compensated start's correction begins at 0, unwritten
+  S->status = 0;
+  S->alpha = 0.0;
+  S->beta = 0.0;
+  if (!isfinite(bb) || !isfinite(rr)) {
+    S->nonfinite = 1;
+    S->zero_x = 0;
+    S->done = 1;
+    S->last_rel = rr;
+  } else if (bb == 0.0) {
+    S->zero_x = 1;
+    S->done = 1;
+    S->last_rel = 0.0;
+  } else {
+    const double rel = sqrt(rr) / sqrt(bb);
+    S->zero_x = 0;
+    S->last_rel = rel;
+    S->done = (rel < S->rtol) ? 1 : 0;
+  }
+  S->ticket = 0;
+  if (use_cond) cudaGraphSetConditional(cond, S->done ? 0u : 1u);
+}
+
 // COMP: the start is the compensated pair phi + s (r0 = b - A phi - A s).
 template <typename T, bool EPS, bool MEAN, int VX, bool COMP = false>
 __global__ void __launch_bounds__(MTX* MTY) k_rhs(Geo g, Bc<T> bc, const T* __restrict__ P, const T* __restrict__ phi,
@@ -149,43 +194,224 @@ __global__ void __launch_bounds__(MTX* MTY) k_rhs(Geo g, Bc<T> bc, const T* __re
     tile_partials<NV, MTX * MTY>(vv, part, t);
   }
   sched_finish(ts);
-  if (!last_block<MTX * MTY>(&S->ticket)) return;
-  double out[NV];
-  gather_partials<NV, MTX * MTY>(part, mc.ntiles, out);
-  if (threadIdx.x != 0 || threadIdx.y != 0) return;
-  if (MEAN) {
-    S->mean_b = out[0] / (double)g.n;
-    S->ticket = 0;
-    return;
+  rhs_close<NV, MEAN, COMP>(g, part, S, mc.ntiles, cond, use_cond);
+}
+
+// k_rhs for a compensated FP32 start with eps = 1 on whole tiles of 64 x 16
+// columns (nx a multiple of 64, ny of 16): the same outputs, sums and tile
+// order, with each field staged with only the neighbours its term reads --
+// phi and its remainder with the x and y halo of the 7-point operator, P_y
+// with its halo rows, P_x with its halo columns, P_z at the own cells (its
+// z neighbours come down the own column).  A stage is 23 680 bytes instead
+// of the general march's 25 920, and there are fewer copies to issue.  The
+// copies of plane v + 3 are issued after plane v's barrier, into the stage
+// plane v - 1 had (every thread has finished it by then): plane v is read
+// in-plane, plane v + 1 at the own cells, planes v + 2 and v + 3 are in
+// flight.  Four stages, two blocks of 256 threads per SM.  (Three stages --
+// one plane in flight, three blocks per SM -- ran 6 % slower on the
+// 1024 x 1024 x 128 film: fewer bytes in flight per SM.)
+constexpr int RW_RS = 72;                  // phi / lo / P_x rows: x0 - 4 .. x0 + 67 (x0 at column 4)
+constexpr int RW_PHI = 0;                  // stage offsets (floats): phi, rows y0 - 1 .. y0 + 16
+constexpr int RW_LO = RW_PHI + 18 * RW_RS; // remainder of the start, as phi
+constexpr int RW_PY = RW_LO + 18 * RW_RS;  // P_y, rows y0 - 1 .. y0 + 16, columns x0 .. x0 + 63
+constexpr int RW_PX = RW_PY + 18 * 64;     // P_x, rows y0 .. y0 + 15, as phi's columns
+constexpr int RW_PZ = RW_PX + 16 * RW_RS;  // P_z, rows y0 .. y0 + 15, columns x0 .. x0 + 63
+constexpr int RW_STAGE = RW_PZ + 16 * 64;
+constexpr int RW_D = 2;                    // planes in flight beyond the two being read
+constexpr int RW_NS = RW_D + 2;
+constexpr size_t rhs_w_smem_bytes() { return (size_t)RW_NS * RW_STAGE * sizeof(float); }
+static_assert(RW_LO % 4 == 0 && RW_PY % 4 == 0 && RW_PX % 4 == 0 && RW_PZ % 4 == 0 && RW_STAGE % 4 == 0,
+              "16-byte aligned stage regions");
+
+__global__ void __launch_bounds__(MTX* MTY, RW_D == 1 ? 3 : 2) k_rhs_w(Geo g, Bc<float> bc, const float* __restrict__ P,
+                                                      const float* __restrict__ phi, const float* __restrict__ lo,
+                                                      float* __restrict__ r, double* part, Scalars* S, MarchCfg mc,
+                                                      cudaGraphConditionalHandle cond, int use_cond) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long tile_slot;
+  static_assert(MTX == 16 && MTY == 16, "tiles of 64 x 16 columns, four cells a thread");
+  float* const stg = reinterpret_cast<float*>(smem);
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const long long nxy = g.nxy;
+  const float* const Px = P;
+  const float* const Py = P + g.n;
+  const float* const Pz = P + 2 * g.n;
+  const float mb = float(S->mean_b);
+  const float inv6 = 1.0f / (6.0f * float(g.ih2));
+  const float ih = float(g.ih), ih2 = float(g.ih2);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * MTX;
+  // own vector in each region of a stage
+  const int o_phi = (ty + 1) * RW_RS + 4 + 4 * tx, o_py = (ty + 1) * 64 + 4 * tx;
+  const int o_px = ty * RW_RS + 4 + 4 * tx, o_pz = ty * 64 + 4 * tx;
+  auto load4 = [](const float* p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  };
+  // z of virtual plane v of a tile starting at z0 (v = 0: the plane below,
+  // nt + 1: the plane above), -1 past a non-periodic face
+  auto plane_of = [&](int z0, int v) {
+    int z = z0 - 1 + v;
+    if (z < 0) z = g.periodic_z ? z + nz : -1;
+    else if (z >= nz) z = g.periodic_z ? z - nz : -1;
+    return z;
+  };
+  Acc<float> abb, arr, arz;
+  const TileSched ts{&S->sched_next, &S->sched_done, mc.ntiles};
+  for (long long t = sched_first(ts, &tile_slot); t < mc.ntiles; t = sched_next(ts, &tile_slot)) {
+    const TileGeo<MTX, MTY, 4> s = tile_geo<MTX, MTY, 4>(g, t, mc);
+    const int x0 = s.x - 4 * tx, y0 = s.y - ty, z0 = s.z0, nt = s.z1 - s.z0;
+    // The halo copies of a plane: 96 vectors (phi, lo and P_y, the rows
+    // y0 - 1 and y0 + 16) by threads 0 .. 95, 96 cells (phi, lo and P_x, the
+    // columns x0 - 1 and x0 + 64) by threads 96 .. 191; periodic x/y wrap in
+    // the source.
+    const float* hsrc = nullptr;
+    int hdst = -1;
+    bool hvec = false;
+    if (tid < 96) {
+      const int f = tid >> 5, bot = (tid >> 4) & 1, c = tid & 15;
+      const int y = bot ? (y0 + 16 == ny ? 0 : y0 + 16) : (y0 == 0 ? ny - 1 : y0 - 1);
+      hsrc = (f == 0 ? phi : f == 1 ? lo : Py) + (long long)y * nx + x0 + 4 * c;
+      hdst = f == 2 ? RW_PY + bot * 17 * 64 + 4 * c : (f == 0 ? RW_PHI : RW_LO) + bot * 17 * RW_RS + 4 + 4 * c;
+      hvec = true;
+    } else if (tid < 192) {
+      const int j = tid - 96, f = j >> 5, rgt = (j >> 4) & 1, row = j & 15;
+      const int x = rgt ? (x0 + 64 == nx ? 0 : x0 + 64) : (x0 == 0 ? nx - 1 : x0 - 1);
+      hsrc = (f == 0 ? phi : f == 1 ? lo : Px) + (long long)(y0 + row) * nx + x;
+      hdst = (f == 2 ? RW_PX + row * RW_RS : (f == 0 ? RW_PHI : RW_LO) + (row + 1) * RW_RS) + (rgt ? 68 : 3);
+    }
+    auto issue = [&](int v) {
+      const int z = v <= nt + 1 ? plane_of(z0, v) : -1;
+      if (z >= 0) {
+        float* st = stg + (v % RW_NS) * RW_STAGE;
+        const long long zo = (long long)z * nxy, go = zo + s.xy;
+        cp_async<16>(st + RW_PHI + o_phi, phi + go);
+        cp_async<16>(st + RW_LO + o_phi, lo + go);
+        cp_async<16>(st + RW_PZ + o_pz, Pz + go);
+        if (v >= 1 && v <= nt) {
+          cp_async<16>(st + RW_PY + o_py, Py + go);
+          cp_async<16>(st + RW_PX + o_px, Px + go);
+          if (hvec) cp_async<16>(st + hdst, hsrc + zo);
+          else if (hdst >= 0) cp_async<4>(st + hdst, hsrc + zo);
+        }
+      }
+      cp_commit();
+    };
+    abb = Acc<float>();
+    arr = Acc<float>();
+    arz = Acc<float>();
+    // z carry of the own column: P_z, phi, lo at plane v - 1 (plane v is read
+    // from its stage, plane v + 1 at the own cells of the next one)
+    float zm[3][4];
+    for (int w = 0; w < RW_NS; ++w) issue(w);
+    for (int v = 1; v <= nt; ++v) {
+      cp_wait<RW_D - 1>();                 // planes <= v + 1 of this thread have landed
+      __syncthreads();                     // ... of every thread, and plane v - 1 is no longer read
+      const int zb = plane_of(z0, v - 1), za = plane_of(z0, v + 1);
+      if (v == 1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) zm[0][i] = zm[1][i] = zm[2][i] = 0.f;
+        if (zb >= 0) {                     // stage 0: the plane below
+          load4(stg + RW_PZ + o_pz, zm[0]);
+          load4(stg + RW_PHI + o_phi, zm[1]);
+          load4(stg + RW_LO + o_phi, zm[2]);
+        }
+      }
+      issue(v + RW_D + 1);                 // into the stage of plane v - 1 (plane 0 read just above)
+      const float* sc = stg + (v % RW_NS) * RW_STAGE;
+      const float* sa = stg + ((v + 1) % RW_NS) * RW_STAGE;
+      const int z = z0 + v - 1;
+      // own vector of the field at stage offset off, planes v and v + 1 (0 past a face)
+      auto own = [&](int off, float (&c)[4], float (&p)[4]) {
+        load4(sc + off, c);
+        if (za >= 0) load4(sa + off, p);
+        else p[0] = p[1] = p[2] = p[3] = 0.f;
+      };
+      auto xends = [&](const float (&c)[4], int off, float& l, float& rr) {
+        l = __shfl_up_sync(0xffffffffu, c[3], 1);
+        rr = __shfl_down_sync(0xffffffffu, c[0], 1);
+        if (tx == 0) l = sc[off - 1];
+        if (tx == MTX - 1) rr = sc[off + 4];
+      };
+      auto plane = [&](const bool bt) {
+        // electrode faces of cell i (read again where needed: fewer live registers)
+        auto dlo = [&](int i) { return (bt && zb < 0) ? (int)bc.tlo[s.xy + i] : 0; };
+        auto dhi = [&](int i) { return (bt && za < 0) ? (int)bc.thi[s.xy + i] : 0; };
+        // b = -div P + Dirichlet terms (the general kernel's face rules)
+        float rv[4], bv[4];
+        {
+          float pzc[4], pzp[4], px[4], pym[4], pyp[4], l, rr;
+          own(RW_PZ + o_pz, pzc, pzp);
+          load4(sc + RW_PX + o_px, px);
+          load4(sc + RW_PY + o_py - 64, pym);
+          load4(sc + RW_PY + o_py + 64, pyp);
+          xends(px, RW_PX + o_px, l, rr);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            Stencil7<Raw<float, 3>> sp;
+            sp.c.v[2] = pzc[i];
+            sp.xm.v[0] = i == 0 ? l : px[i - 1];
+            sp.xp.v[0] = i == 3 ? rr : px[i + 1];
+            sp.ym.v[1] = pym[i];
+            sp.yp.v[1] = pyp[i];
+            sp.zm.v[2] = zm[0][i];
+            sp.zp.v[2] = pzp[i];
+            sp.zb = bt ? zb : 0;
+            sp.za = bt ? za : 0;
+            const int dl = dlo(i), dh = dhi(i);
+            float dir = 0.f;
+            if (dl) dir += 2.f * bc.vlo[s.xy + i];
+            if (dh) dir += 2.f * bc.vhi[s.xy + i];
+            bv[i] = -divergence(sp, dl, dh) * ih + dir * ih2 - mb;
+            rv[i] = bv[i];
+            zm[0][i] = pzc[i];
+          }
+        }
+        // r0 = b - A phi - A lo
+#pragma unroll
+        for (int k = 1; k < 3; ++k) {
+          const int off = (k == 1 ? RW_PHI : RW_LO) + o_phi;
+          float c[4], p[4], ym[4], yp[4], l, rr;
+          own(off, c, p);
+          load4(sc + off - RW_RS, ym);
+          load4(sc + off + RW_RS, yp);
+          xends(c, off, l, rr);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            Stencil7<float> q;
+            q.c = c[i];
+            q.xm = i == 0 ? l : c[i - 1];
+            q.xp = i == 3 ? rr : c[i + 1];
+            q.ym = ym[i];
+            q.yp = yp[i];
+            q.zm = zm[k][i];
+            q.zp = p[i];
+            q.zb = bt ? zb : 0;
+            q.za = bt ? za : 0;
+            rv[i] -= apply_bt(q, dlo(i), dhi(i), ih2, bt);
+            zm[k][i] = c[i];
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float inv = bt ? inv_diag_unit(g, bc, s.xy + i, z, inv6) : inv6;
+          abb.add(bv[i], bv[i]);
+          arr.add(rv[i], rv[i]);
+          arz.add(rv[i], rv[i] * inv);
+        }
+        abb.run();
+        arr.run();
+        arz.run();
+        *reinterpret_cast<float4*>(r + (long long)z * nxy + s.xy) = make_float4(rv[0], rv[1], rv[2], rv[3]);
+      };
+      if (zb < 0 || za < 0) plane(true);
+      else plane(false);
+    }
+    cp_wait<0>();
+    double vals[3] = {abb.value(), arr.value(), arz.value()};
+    tile_partials<3, MTX * MTY>(vals, part, t);
   }
-  const double bb = out[0], rr = out[NV > 1 ? 1 : 0], rz = out[NV > 2 ? 2 : 0];
-  S->bb = bb;
-  S->rr = rr;
-  S->rz = rz;
-  S->iter = 0;
-  S->first = 1;
-  S->pending = 0;
-  S->xzero = COMP ? 1 : 0;            // a compensated start's correction begins at 0, unwritten
-  S->status = 0;
-  S->alpha = 0.0;
-  S->beta = 0.0;
-  if (!isfinite(bb) || !isfinite(rr)) {
-    S->nonfinite = 1;
-    S->zero_x = 0;
-    S->done = 1;
-    S->last_rel = rr;
-  } else if (bb == 0.0) {
-    S->zero_x = 1;
-    S->done = 1;
-    S->last_rel = 0.0;
-  } else {
-    const double rel = sqrt(rr) / sqrt(bb);
-    S->zero_x = 0;
-    S->last_rel = rel;
-    S->done = (rel < S->rtol) ? 1 : 0;
-  }
-  S->ticket = 0;
-  if (use_cond) cudaGraphSetConditional(cond, S->done ? 0u : 1u);
+  sched_finish(ts);
+  rhs_close<3, false, true>(g, part, S, mc.ntiles, cond, use_cond);
 }
 
 template <typename T>
@@ -427,9 +653,40 @@ static void smem_attr(K kernel, size_t bytes, bool& done) {
   }
 }
 
+// k_rhs_w takes the start of an FP32 time series (compensated, eps = 1) when
+// the march's tiles are whole 64 x 16 tiles; its grid is sized by its own
+// occupancy (or the blocks per SM a tiling asked for, if fewer).
+static bool rhs_whole(const Geo& g, const MarchCfg& mc) { return mc.vx == 4 && g.nx % 64 == 0 && g.ny % MTY == 0; }
+
+static void rhs_w(const LaunchCfg& L, const Geo& g, const Dev<float>& d, const float* P, cudaGraphConditionalHandle cond,
+                  int use_cond) {
+  static bool f = false;
+  static int occ = 0, nsm = 0;
+  const size_t bytes = rhs_w_smem_bytes();
+  smem_attr(k_rhs_w, bytes, f);
+  if (occ == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      nsm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rhs_w, MTX * MTY, bytes) != cudaSuccess) occ = 1;
+    cudaGetLastError();
+    occ = std::max(occ, 1);
+  }
+  const int bps = L.march.bps > 0 ? std::min(L.march.bps, occ) : occ;
+  const int grid = (int)std::min<long long>(L.march.ntiles, std::min<long long>(MAX_GRID, (long long)bps * nsm));
+  k_rhs_w<<<grid, dim3(MTX, MTY), bytes, L.stream>>>(g, d.bc, P, d.cp.hi, d.cp.lo, d.r, d.part, d.S, L.march, cond,
+                                                     use_cond);
+}
+
 template <typename T, bool EPS, bool MEAN, int VX, bool COMP>
 static void rhs_t(const LaunchCfg& L, const Geo& g, const Dev<T>& d, const T* P, cudaGraphConditionalHandle cond,
                   int use_cond) {
+  if constexpr (std::is_same<T, float>::value && !EPS && !MEAN && VX == 4 && COMP) {
+    if (rhs_whole(g, L.march)) {
+      rhs_w(L, g, d, P, cond, use_cond);
+      return;
+    }
+  }
   static bool f = false;
   const size_t bytes = StepPipe<T, EPS, VX, COMP ? 1 : 0>::bytes();
   smem_attr(k_rhs<T, EPS, MEAN, VX, COMP>, bytes, f);
