@@ -207,9 +207,11 @@ __global__ void __launch_bounds__(MTX* MTY) k_rhs(Geo g, Bc<T> bc, const T* __re
 // copies of plane v + 3 are issued after plane v's barrier, into the stage
 // plane v - 1 had (every thread has finished it by then): plane v is read
 // in-plane, plane v + 1 at the own cells, planes v + 2 and v + 3 are in
-// flight.  Four stages, two blocks of 256 threads per SM.  (Three stages --
-// one plane in flight, three blocks per SM -- ran 6 % slower on the
-// 1024 x 1024 x 128 film: fewer bytes in flight per SM.)
+// flight.  Four stages, two blocks of 256 threads per SM.  On the
+// 1024 x 1024 x 128 film, against this form: three stages (one plane in
+// flight, three blocks per SM) 14 % slower, the copies issued before the
+// barrier (one plane in flight) 4 %, the own column's current plane read back
+// from its stage instead of carried 8 %.
 constexpr int RW_RS = 72;                  // phi / lo / P_x rows: x0 - 4 .. x0 + 67 (x0 at column 4)
 constexpr int RW_PHI = 0;                  // stage offsets (floats): phi, rows y0 - 1 .. y0 + 16
 constexpr int RW_LO = RW_PHI + 18 * RW_RS; // remainder of the start, as phi
@@ -299,9 +301,9 @@ __global__ void __launch_bounds__(MTX* MTY, RW_D == 1 ? 3 : 2) k_rhs_w(Geo g, Bc
     abb = Acc<float>();
     arr = Acc<float>();
     arz = Acc<float>();
-    // z carry of the own column: P_z, phi, lo at plane v - 1 (plane v is read
-    // from its stage, plane v + 1 at the own cells of the next one)
-    float zm[3][4];
+    // z carry of the own column: P_z, phi, lo at planes v - 1 and v (plane
+    // v + 1 is read at the own cells of its stage)
+    float zm[3][4], cc[3][4];
     for (int w = 0; w < RW_NS; ++w) issue(w);
     for (int v = 1; v <= nt; ++v) {
       cp_wait<RW_D - 1>();                 // planes <= v + 1 of this thread have landed
@@ -315,16 +317,23 @@ __global__ void __launch_bounds__(MTX* MTY, RW_D == 1 ? 3 : 2) k_rhs_w(Geo g, Bc
           load4(stg + RW_PHI + o_phi, zm[1]);
           load4(stg + RW_LO + o_phi, zm[2]);
         }
+        load4(stg + RW_STAGE + RW_PZ + o_pz, cc[0]);
+        load4(stg + RW_STAGE + RW_PHI + o_phi, cc[1]);
+        load4(stg + RW_STAGE + RW_LO + o_phi, cc[2]);
       }
       issue(v + RW_D + 1);                 // into the stage of plane v - 1 (plane 0 read just above)
       const float* sc = stg + (v % RW_NS) * RW_STAGE;
       const float* sa = stg + ((v + 1) % RW_NS) * RW_STAGE;
       const int z = z0 + v - 1;
-      // own vector of the field at stage offset off, planes v and v + 1 (0 past a face)
-      auto own = [&](int off, float (&c)[4], float (&p)[4]) {
-        load4(sc + off, c);
+      // own vector of carried field k at planes v (carried) and v + 1 (stage
+      // offset off; 0 past a face), which becomes the carried plane
+      auto own = [&](int off, int k, float (&c)[4], float (&p)[4]) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) c[i] = cc[k][i];
         if (za >= 0) load4(sa + off, p);
         else p[0] = p[1] = p[2] = p[3] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) cc[k][i] = p[i];
       };
       auto xends = [&](const float (&c)[4], int off, float& l, float& rr) {
         l = __shfl_up_sync(0xffffffffu, c[3], 1);
@@ -340,7 +349,7 @@ __global__ void __launch_bounds__(MTX* MTY, RW_D == 1 ? 3 : 2) k_rhs_w(Geo g, Bc
         float rv[4], bv[4];
         {
           float pzc[4], pzp[4], px[4], pym[4], pyp[4], l, rr;
-          own(RW_PZ + o_pz, pzc, pzp);
+          own(RW_PZ + o_pz, 0, pzc, pzp);
           load4(sc + RW_PX + o_px, px);
           load4(sc + RW_PY + o_py - 64, pym);
           load4(sc + RW_PY + o_py + 64, pyp);
@@ -371,7 +380,7 @@ __global__ void __launch_bounds__(MTX* MTY, RW_D == 1 ? 3 : 2) k_rhs_w(Geo g, Bc
         for (int k = 1; k < 3; ++k) {
           const int off = (k == 1 ? RW_PHI : RW_LO) + o_phi;
           float c[4], p[4], ym[4], yp[4], l, rr;
-          own(off, c, p);
+          own(off, k, c, p);
           load4(sc + off - RW_RS, ym);
           load4(sc + off + RW_RS, yp);
           xends(c, off, l, rr);
