@@ -29,6 +29,9 @@
 // come straight from the staged planes (march_direct).  Algorithmic traffic
 // per cell: k_rhs reads 4 words (5 with a compensated start) and writes 1;
 // k_tdgl reads 4 and writes 3 (compensated state: plus 3 half-words each way).
+// An FP32 time series on whole 64 x 16 tiles runs k_rhs_w and k_tdgl_w: the
+// same arithmetic on their own staging (each field with only the neighbours
+// its term reads, halo copies spread over the block).
 #include <cuda_bf16.h>
 
 #include "pf_internal.h"

@@ -1,9 +1,11 @@
-"""The Poisson right-hand side and warm residual of an FP32 time series on
-whole 64 x 16 tiles (k_rhs_w: each field staged with only the neighbours its
-term reads, three blocks per SM) against the FP64 oracle, and against the
-general plane march (vx = 1 tiling) on the same films: electrode masks and
-voltages on both z faces, a singular periodic box (zero-mean b), and tilings
-one plane deep, a whole film deep and with one block per SM."""
+"""The whole-tile kernels of an FP32 time series on 64 x 16 tiles -- the
+Poisson right-hand side and warm residual (k_rhs_w: each field staged with
+only the neighbours its term reads) and the compensated TDGL update
+(k_tdgl_w: the halo copies spread over the block) -- against the FP64 oracle,
+and against the general plane march (vx = 1 tiling) on the same films:
+electrode masks and voltages on both z faces, a singular periodic box
+(zero-mean b), and tilings one plane deep, a whole film deep and with one
+block per SM."""
 import numpy as np
 import pytest
 import torch
