@@ -308,7 +308,11 @@ def run_ours(args):
     Ph = film.P.detach().to("cpu").pin_memory()
     phih = film.phi.detach().to("cpu").pin_memory()
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
-    film.step(1)
+    # untimed warm-up through the same call: its steps alternate the two
+    # polarization buffers, whose one-step graphs are captured on first use
+    e2e_warm = 2
+    pf.pf_step_host(film.ctx, Ph, phih, e2e_warm)
+    torch.cuda.synchronize(dev)
     barrier()
     t0 = time.perf_counter()
     pf.pf_step_host(film.ctx, Ph, phih, e2e_steps)
@@ -317,7 +321,7 @@ def run_ours(args):
     e2e_ms, e2e_value = replica_throughput(1e3 * e2e_s, w.n * e2e_steps, world, dev)
     e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": 4 * w.n * w_bytes, "d2h_bytes_per_step": 4 * w.n * w_bytes,
-           "steps": e2e_steps}
+           "steps": e2e_steps, "warmup": e2e_warm}
 
     # roofline of the dominant kernel family (live CUDA-event times)
     work = [s for s in stats if s["launches"] > 0]
