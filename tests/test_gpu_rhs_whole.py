@@ -78,3 +78,17 @@ def test_whole_tiles_any_depth_and_grid(tiling):
     P, phi, _ = run(w)
     Pt, phit, _ = run(w, tiling=tiling)
     assert relerr(Pt, P) <= AGREE and relerr(phit, phi) <= AGREE
+
+
+@pytest.mark.parametrize("shape", [(64, 16, 1), (64, 16, 2), (128, 32, 3)])
+def test_whole_tiles_thin_films(shape):
+    """One tile column and row (the x and y halo wrap onto the tile itself),
+    one plane touching both z faces, two planes, three: against the oracle
+    and against the general march."""
+    nx, ny, nz = shape
+    w = mixed_workload(nx, ny, nz, 73, precision="fp32", steps=4, rtol=1e-7, amp=0.5)
+    Po, phio, _, _ = oracle_run(w.with_(precision="fp64"), rtol=1e-14)
+    P, phi, _ = run(w)
+    assert relerr(P, Po) <= FP32_TOL and relerr(phi, phio) <= 1e-3
+    Pg, phig, _ = run(w, tiling=(1, 4, 0))
+    assert relerr(P, Pg) <= AGREE and relerr(phi, phig) <= 10 * AGREE
