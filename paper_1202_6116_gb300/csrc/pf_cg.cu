@@ -14,6 +14,7 @@
 namespace pf {
 
 constexpr int CG_D = 2;   // planes of cp.async look-ahead in k_cg_p
+constexpr int CGD_D = 3;  // the same for its direct (multigrid) forms, whose stages are smaller
 
 template <typename T, bool EPS, int VX>
 using CgPipe = Pipe<T, typename FieldOf<T, EPS>::type, MTX, MTY, VX, EPS ? 4 : 2, 1, CG_D>;
@@ -138,14 +139,14 @@ __global__ void __launch_bounds__(MTX* MTY, (sizeof(T) == 4 && !EPS) ? 3 : 2) k_
         apq.add(st.c, qv);
         return Out{T(0), st.c, qv};
       };
-      march_direct<T, Out, MTX, MTY, VX, 1, 0, CG_D>(g, s, smem, hs1, os1, emit_f, post);
+      march_direct<T, Out, MTX, MTY, VX, 1, 0, CGD_D>(g, s, smem, hs1, os1, emit_f, post);
     } else if constexpr (DIRECT) {
       static_assert(MG && !EPS, "the direct form is the multigrid search direction with eps = 1");
       if constexpr (SECOND) {          // x is not read: stage z and p_old alone
         const T* const os0[1] = {nullptr};
-        march_direct<T, Out, MTX, MTY, VX, NH, 0, CG_D>(g, s, smem, hsrc, os0, emit_d, post);
+        march_direct<T, Out, MTX, MTY, VX, NH, 0, CGD_D>(g, s, smem, hsrc, os0, emit_d, post);
       } else {
-        march_direct<T, Out, MTX, MTY, VX, NH, 1, CG_D>(g, s, smem, hsrc, osrc, emit_d, post);
+        march_direct<T, Out, MTX, MTY, VX, NH, 1, CGD_D>(g, s, smem, hsrc, osrc, emit_d, post);
       }
     } else {
       march<T, F, Out, MTX, MTY, VX, NH, 1, CG_D>(g, s, smem, hsrc, osrc, val, emit, post);
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_cg_r(Geo g, Bc<T> bc, const T*
 template <typename T, bool EPS, bool MG, int VX, bool FIRST, bool SECOND>
 static void launch_cg_p_t(const LaunchCfg& L, const Geo& g, const Dev<T>& d) {
   constexpr bool DIRECT = MG && !EPS;
-  using PD = Pipe<T, void, MTX, MTY, VX, FIRST ? 1 : 2, (FIRST || SECOND) ? 0 : 1, CG_D>;
+  using PD = Pipe<T, void, MTX, MTY, VX, FIRST ? 1 : 2, (FIRST || SECOND) ? 0 : 1, CGD_D>;
   const size_t bytes = DIRECT ? PD::bytes() : CgPipe<T, EPS, VX>::bytes();
   static bool once = false;
   if (!once) {
